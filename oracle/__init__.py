@@ -1,0 +1,58 @@
+"""FP64 CPU oracle for alternating-update NNCP (test infrastructure only).
+
+This package is the plain, slow, obviously correct statement of what the GPU
+hot path computes.  It exists to check the CUDA library and nothing else: only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg
+of ``bench.py`` may import it.  The product path (``paper_1909_01149_gb300``)
+never imports, links or calls anything in here, and this package imports
+nothing from the product path.
+
+Everything is NumPy in float64.  The MTTKRP is computed by explicit
+matricization times an explicit Khatri-Rao product, with no dimension tree, so
+that a reader can check it against the definitions of the paper by eye.
+
+Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
+  unfold, khatri_rao, mttkrp ........ pinned (brute-force sums, CP closed form,
+                                      N=2 plain GEMM, two-stage 3-way equations)
+  gram_hadamard ..................... pinned (explicit K^T K)
+  nls_bpp ........................... pinned (scipy Lawson-Hanson NNLS,
+                                      brute-force passive-set enumeration, KKT)
+  nls_hals, nls_mu .................. pinned (objective non-increasing; HALS
+                                      column step is the exact 1-D minimiser;
+                                      HALS fixed point satisfies KKT)
+  nls_admm .......................... pinned (uncapped ADMM reaches the BPP
+                                      solution; capped form is deterministic)
+  nls_pgd ........................... pinned (objective non-increasing; fixed
+                                      point satisfies KKT)
+  normalize_columns ................. pinned (norms, reconstruction unchanged)
+  fit_identity ...................... pinned (explicit reconstruction residual)
+  nncp .............................. pinned (noiseless planted tensor -> zero
+                                      residual; monotone error for BPP/HALS)
+  cp_loss_grad ...................... pinned (central finite differences)
+"""
+
+from .nncp import (  # noqa: F401
+    unfold,
+    khatri_rao,
+    krp_except,
+    mttkrp,
+    mttkrp_bruteforce,
+    gram,
+    gram_hadamard,
+    nls_mu,
+    nls_hals,
+    nls_admm,
+    nls_bpp,
+    nls_bpp_row,
+    nls_pgd,
+    nls_objective,
+    normalize_columns,
+    cp_full,
+    fit_identity,
+    fit_explicit,
+    sqnorm,
+    nncp,
+    cp_loss,
+    cp_loss_grad,
+    choose_split,
+)

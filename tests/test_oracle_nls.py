@@ -1,0 +1,171 @@
+"""Pins for the oracle's NNLS updates (Sec. 4.3).
+
+BPP is checked against SciPy's Lawson-Hanson NNLS on an explicit A, b with
+A^T A = S and A^T b = m, against brute-force enumeration of every passive
+set, and against the KKT conditions.  HALS, MU, ADMM and PGD are checked by
+the properties the paper states or that fix them: monotone objective, the
+exact 1-D minimiser of each HALS column step, and convergence to the unique
+BPP solution when S is positive definite.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as o
+
+
+def _problem(rows, R, seed, m_rows=None):
+    """Random NNLS instance in Gram form: A (m x R), B (m x rows)."""
+    rng = np.random.default_rng(seed)
+    m_rows = m_rows or 3 * R
+    A = rng.random((m_rows, R))
+    B = rng.random((m_rows, rows)) - 0.3  # some rows have active constraints
+    S = A.T @ A
+    M = (A.T @ B).T  # rows x R
+    return A, B, S, M
+
+
+def _kkt(S, m, x):
+    y = S @ x - m
+    return x.min(), y.min(), np.abs(x * y).max()
+
+
+@pytest.mark.parametrize("R", [1, 3, 6, 12])
+def test_bpp_matches_lawson_hanson(R):
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    A, B, S, M = _problem(8, R, R)
+    X, _, ok = o.nls_bpp(S, M)
+    assert ok
+    for i in range(M.shape[0]):
+        ref, _ = scipy_opt.nnls(A, B[:, i])
+        np.testing.assert_allclose(X[i], ref, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("R", [2, 4, 6])
+def test_bpp_matches_passive_set_enumeration(R):
+    _, _, S, M = _problem(5, R, 40 + R)
+    X, _, _ = o.nls_bpp(S, M)
+    for i in range(M.shape[0]):
+        m = M[i]
+        found = []
+        for mask in itertools.product([False, True], repeat=R):
+            F = np.array(mask)
+            x = np.zeros(R)
+            if F.any():
+                x[F] = np.linalg.solve(S[np.ix_(F, F)], m[F])
+            y = S @ x - m
+            if x.min() >= -1e-12 and y[~F].min(initial=0) >= -1e-12:
+                found.append(np.maximum(x, 0))
+        assert found, "no KKT point found by enumeration"
+        for f in found:
+            np.testing.assert_allclose(X[i], f, rtol=1e-9, atol=1e-12)
+
+
+def test_bpp_kkt_and_warm_start_independence():
+    _, _, S, M = _problem(20, 10, 7)
+    X0, _, _ = o.nls_bpp(S, M)
+    rng = np.random.default_rng(1)
+    X1, _, _ = o.nls_bpp(S, M, rng.random(M.shape) - 0.5)
+    np.testing.assert_allclose(X0, X1, rtol=1e-10, atol=1e-13)
+    for i in range(M.shape[0]):
+        xmin, ymin, comp = _kkt(S, M[i], X0[i])
+        assert xmin >= 0 and ymin > -1e-10 and comp < 1e-10
+
+
+def test_bpp_row_zero_rhs():
+    S = np.eye(3) * 2
+    x, it, ok = o.nls_bpp_row(S, np.zeros(3))
+    assert ok and it == 0 and not x.any()
+
+
+@pytest.mark.parametrize("alg", ["mu", "hals", "admm", "pgd"])
+def test_objective_non_increasing(alg):
+    _, _, S, M = _problem(30, 8, 11)
+    M = np.abs(M)  # MU needs a non-negative numerator
+    H = np.random.default_rng(3).random(M.shape)
+    f0 = o.nls_objective(S, M, H)
+    fn = {"mu": o.nls_mu, "hals": o.nls_hals, "pgd": o.nls_pgd,
+          "admm": lambda S, M, H: o.nls_admm(S, M, H)}[alg]
+    for _ in range(20):
+        H = fn(S, M, H)
+        f1 = o.nls_objective(S, M, H)
+        if alg != "admm":  # ADMM is not a descent method step by step
+            assert f1 <= f0 + 1e-12 * abs(f0)
+        f0 = f1
+    assert (H >= 0).all()
+
+
+def test_hals_column_step_is_exact_minimiser():
+    _, _, S, M = _problem(6, 5, 13)
+    H = np.random.default_rng(4).random(M.shape)
+    R = S.shape[0]
+    # one column step in isolation: only column 0 changes
+    H1 = H.copy()
+    H1[:, 0] = np.maximum(0, H[:, 0] + (M[:, 0] - H @ S[:, 0]) / S[0, 0])
+    Hs = o.nls_hals(S, M, H)
+    np.testing.assert_allclose(Hs[:, 0], H1[:, 0], rtol=1e-14)
+    f1 = o.nls_objective(S, M, H1)
+    for delta in (1e-3, -1e-3, 0.1, -0.1):
+        Hp = H1.copy()
+        Hp[:, 0] = np.maximum(0, Hp[:, 0] + delta)
+        assert o.nls_objective(S, M, Hp) >= f1 - 1e-14
+    assert R == 5
+
+
+@pytest.mark.parametrize("alg", ["hals", "admm", "pgd"])
+def test_iterations_reach_bpp_solution(alg):
+    _, _, S, M = _problem(10, 6, 17)
+    X, _, _ = o.nls_bpp(S, M)
+    H = np.random.default_rng(5).random(M.shape)
+    if alg == "hals":
+        for _ in range(3000):
+            H = o.nls_hals(S, M, H)
+    elif alg == "pgd":
+        H = o.nls_pgd(S, M, H, steps=40000)
+    else:
+        H = o.nls_admm(S, M, H, max_inner=3000, tol=0.0)
+    np.testing.assert_allclose(H, X, rtol=1e-6, atol=1e-8)
+
+
+def test_mu_fixed_point_and_eps():
+    S = np.array([[2.0, 0.5], [0.5, 1.0]])
+    x = np.array([[0.3, 0.7]])
+    M = x @ S  # unconstrained optimum is x itself, strictly positive
+    np.testing.assert_allclose(o.nls_mu(S, M, x), x, rtol=1e-14)
+    # zero denominator is protected by eps and keeps zero entries at zero
+    z = o.nls_mu(S, M, np.zeros((1, 2)))
+    assert np.all(z == 0)
+
+
+def test_hals_skips_zero_diagonal():
+    S = np.array([[0.0, 0.0], [0.0, 1.0]])
+    M = np.array([[5.0, 2.0]])
+    H = np.array([[0.7, 0.1]])
+    out = o.nls_hals(S, M, H)
+    assert out[0, 0] == 0.7 and out[0, 1] == 2.0
+
+
+def test_admm_first_step_by_hand():
+    """One ADMM step from H = 0, U = 0 is the projected ridge solution with
+    rho = trace(S) / R."""
+    S = np.array([[4.0, 1.0], [1.0, 2.0]])
+    M = np.array([[1.0, -3.0]])
+    rho = 3.0
+    Htil = M @ np.linalg.inv(S + rho * np.eye(2))
+    H, U, k = o.nls_admm(S, M, np.zeros((1, 2)), max_inner=1,
+                         return_state=True)
+    np.testing.assert_allclose(H, np.maximum(Htil, 0), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(U, H - Htil, rtol=1e-14, atol=1e-15)
+    assert k == 1
+
+
+def test_normalize_columns():
+    rng = np.random.default_rng(9)
+    Hh = rng.random((7, 4))
+    Hh[:, 2] = 0.0
+    H, lam = o.normalize_columns(Hh)
+    np.testing.assert_allclose(np.linalg.norm(H[:, [0, 1, 3]], axis=0), 1.0)
+    assert lam[2] == 0 and not H[:, 2].any()
+    np.testing.assert_allclose(H * lam, Hh, rtol=1e-15)
