@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""NNCP benchmark: outer iterations per second of the C-ABI solve and the
+HBM throughput of its partial-MTTKRP kernel, on synthetic planted tensors.
+
+One step = one planc_nncp_solve call: ||X||^2, Grams of the initial factors,
+then `iters` outer iterations of (dimension-tree MTTKRP, Hadamard of Grams,
+NNLS update, normalisation, Gram) per mode and the error identity (all rows
+of the hot path).  value = outer iterations per second over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl planc|reference]
+                  [--config c2|c3|c1] [--alg hals|mu|admm|bpp|pgd]
+                  [--no-mixed] [--no-cpu-baseline]
+
+--impl reference times the FP64 NumPy oracle on the host cores (bounded
+samples of the same workload).  Under torchrun each rank runs its own replica
+of the workload (the path has no data-parallel exchange on one node).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    # 512^3 FP32, R = 32, planted + 5% noise, 50 outer iterations
+    "c2": dict(workload="nncp-dense-3way-512x512x512-fp32-R32", dims=(512, 512, 512), R=32,
+               dtype="f32", alg="hals", iters=50, noise=0.05, kind="planted"),
+    # 128x128x200x100 BF16 storage, R = 16, mouse-like, BPP, 30 iterations
+    "c3": dict(workload="nncp-dense-4way-128x128x200x100-bf16-R16", dims=(128, 128, 200, 100),
+               R=16, dtype="bf16", alg="bpp", iters=30, noise=None, kind="mouse"),
+    # 64^3 FP64, R = 8, HALS, 20 iterations
+    "c1": dict(workload="nncp-dense-3way-64x64x64-fp64-R8", dims=(64, 64, 64), R=8,
+               dtype="f64", alg="hals", iters=20, noise=0.01, kind="planted"),
+}
+METRIC = "NNCP outer iterations/s (+ partial-MTTKRP HBM GB/s)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_inputs(cfg, seed=1):
+    from paper_1909_01149_gb300 import synth
+    if cfg["kind"] == "mouse":
+        X, _ = synth.mouse_like(cfg["dims"], cfg["R"], data_seed=seed, dtype=np.float32)
+    else:
+        X, _ = synth.planted(cfg["dims"], cfg["R"], seed, noise=cfg["noise"],
+                             dtype=np.float64 if cfg["dtype"] == "f64" else np.float32)
+    H0 = synth.init_factors(cfg["dims"], cfg["R"], seed + 1,
+                            dtype=np.float64 if cfg["dtype"] == "f64" else np.float32)
+    return X, H0
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def pm_source_sha(use_tc):
+    f = "kern_pm_tc.cu" if use_tc else "kern_pm_simt.cu"
+    data = open(os.path.join(ROOT, "paper_1909_01149_gb300", "csrc", f), "rb").read()
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def profiled_traffic(workload, sha):
+    """DRAM bytes per partial-MTTKRP launch from the committed ncu summary,
+    or None when the kernel source changed since it was taken."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for name in sorted(os.listdir(d)):
+        if not name.endswith(".txt"):
+            continue
+        kv = {}
+        for line in open(os.path.join(d, name)):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("workload") == workload and kv.get("kernel_source_sha") == sha:
+            try:
+                return float(kv["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- arms
+def run_planc(args, cfg):
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+
+    ws, rank, local = dist_setup()
+    t0 = time.time()
+    X, H0 = make_inputs(cfg)
+    log(f"[rank {rank}] inputs ready in {time.time() - t0:.1f}s")
+    dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cfg["dtype"]]
+    fdt = torch.float64 if cfg["dtype"] == "f64" else torch.float32
+    X_host = torch.from_numpy(synth.flat(X)).to(dt).pin_memory()
+    Xd = X_host.cuda()
+    H0d = [torch.from_numpy(h).to(fdt).cuda() for h in H0]
+    H = [h.clone() for h in H0d]
+    stream = torch.cuda.current_stream()
+    ctx = planc.Context(Xd, cfg["dims"], cfg["R"], stream=stream)
+    iters = cfg["iters"]
+    alg = args.alg or cfg["alg"]
+
+    def step(profile=False):
+        for h, h0 in zip(H, H0d):
+            h.copy_(h0)
+        return ctx.solve(H, alg=alg, iters=iters, use_graph=not profile, profile=profile)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+
+    # --- timed region: K steps, device-timed with events on the launch stream
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        res = step()
+        launches += res["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = allreduce_max(e0.elapsed_time(e1), ws)
+    value = ws * args.steps * iters / (ms / 1e3)
+    rel_err = res["rel_err"][-1]
+
+    # --- partial-MTTKRP launch durations (events around each launch, same stream)
+    pm_ms, pm_n = 0.0, 0
+    for _ in range(max(1, args.steps // 2)):
+        r = step(profile=True)
+        pm_ms += r["pm_ms"]
+        pm_n += r["pm_launches"]
+    torch.cuda.synchronize()
+    S = ctx.split
+    L = int(np.prod(cfg["dims"][:S]))
+    Cc = int(np.prod(cfg["dims"][S:]))
+    xb = {"f32": 4, "f64": 8, "bf16": 2}[cfg["dtype"]]
+    fb = 8 if cfg["dtype"] == "f64" else 4
+    I = L * Cc
+    R = cfg["R"]
+    # algorithmic bytes: X once, the partial result once, the factor rows of the KRP
+    left_b = I * xb + L * R * fb + sum(cfg["dims"][S:]) * R * fb
+    right_b = I * xb + Cc * R * fb + sum(cfg["dims"][:S]) * R * fb
+    alg_bytes = (left_b + right_b) / 2.0
+    avg_ms = pm_ms / max(pm_n, 1)
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    use_tc = bool(res.get("use_tc", False))
+    traffic = profiled_traffic(cfg["workload"], pm_source_sha(use_tc))
+
+    # --- end to end through the public API with host buffers
+    Hh = [torch.from_numpy(h).to(fdt).pin_memory() for h in H0]
+    Hout = [torch.empty_like(h).pin_memory() for h in Hh]
+    h2d = X_host.numel() * X_host.element_size() + sum(h.numel() * h.element_size() for h in Hh)
+    d2h = sum(h.numel() * h.element_size() for h in Hout) + 8 * R + 8
+    barrier(ws)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        Xd.copy_(X_host, non_blocking=True)
+        for h, hh in zip(H, Hh):
+            h.copy_(hh, non_blocking=True)
+        r = ctx.solve(H, alg=alg, iters=iters)  # returns lambda and the fit on the host
+        for ho, h in zip(Hout, H):
+            ho.copy_(h, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e2e_ms = allreduce_max(f0.elapsed_time(f1), ws)
+    e2e = ws * args.steps * iters / (e2e_ms / 1e3)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "iter/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if cfg["dtype"] == "f64" else "f32" if cfg["dtype"] == "f32" else "bf16-storage/f32-accumulate",
+        "data": "synthetic (seeded planted CP tensor; no dataset)",
+        "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "R": R,
+                   "alg": alg, "outer_iters_per_step": iters, "split": S,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (X = %.0f MB > 129 MB)" % (I * xb / 1e6)},
+        "final_rel_err": rel_err,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "partial MTTKRP (both root branches)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                     "launches_timed": pm_n},
+        "e2e": {"value": round(e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    ctx.close()
+    del Xd
+    torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not args.no_mixed and args.config == "c2":
+        out["mixed"] = run_mixed(args)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, X, H0, alg)
+    return out, rank
+
+
+def run_mixed(args):
+    """BF16-storage vs FP32 on the 4-way mouse-like workload (BPP), equal
+    iterations: iter/s and final relative error of each."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    cfg = CONFIGS["c3"]
+    X, H0 = make_inputs(cfg)
+    out = {"workload": cfg["workload"], "alg": cfg["alg"], "iters": cfg["iters"]}
+    for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
+        Xd = torch.from_numpy(synth.flat(X)).to(dt).cuda()
+        H0d = [torch.from_numpy(h).cuda() for h in H0]
+        H = [h.clone() for h in H0d]
+        with planc.Context(Xd, cfg["dims"], cfg["R"]) as ctx:
+            def step():
+                for h, h0 in zip(H, H0d):
+                    h.copy_(h0)
+                return ctx.solve(H, alg=cfg["alg"], iters=cfg["iters"])
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            n = max(2, args.steps // 2)
+            for _ in range(n):
+                r = step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        out[name] = {"iter_s": round(n * cfg["iters"] / (ms / 1e3), 2),
+                     "rel_err": r["rel_err"][-1]}
+        del Xd
+        torch.cuda.empty_cache()
+    out["rel_err_diff"] = abs(out["bf16"]["rel_err"] - out["fp32"]["rel_err"])
+    out["speedup_bf16_over_fp32"] = round(out["bf16"]["iter_s"] / out["fp32"]["iter_s"], 3)
+    return out
+
+
+def cpu_baseline(cfg, X, H0, alg):
+    """The FP64 oracle, as it stands, on a bounded sample: one outer iteration
+    of the full workload (every mode's MTTKRP, NNLS, normalisation, error)."""
+    import oracle as o
+    Xs = np.asarray(X, dtype=np.float64)
+    Hs = [np.asarray(h, dtype=np.float64) for h in H0]
+    t = time.time()
+    o.nncp(Xs, Hs, alg, iters=1)
+    dt = time.time() - t
+    return {"value": round(1.0 / dt, 5), "unit": "iter/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"1 outer iteration (alpha, {len(cfg['dims'])} mode updates, error) "
+                      f"of the full {cfg['workload']} workload, NumPy FP64, default BLAS threads"}
+
+
+def run_reference(args, cfg):
+    """The oracle arm: each step is one outer iteration of the FP64 oracle on
+    the full workload, timed on the host cores."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None, rank
+    import oracle as o
+    X, H0 = make_inputs(cfg)
+    Xs = np.asarray(X, dtype=np.float64)
+    Hs = [np.asarray(h, dtype=np.float64) for h in H0]
+    alg = args.alg or cfg["alg"]
+    for _ in range(args.warmup):
+        o.nncp(Xs, Hs, alg, iters=1)
+    t = time.time()
+    for _ in range(args.steps):
+        o.nncp(Xs, Hs, alg, iters=1)
+    dt = time.time() - t
+    v = args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "iter/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded planted CP tensor; no dataset)",
+           "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "R": cfg["R"],
+                      "alg": alg, "outer_iters_per_step": 1},
+           "cpu_baseline": {"value": round(v, 5), "unit": "iter/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": "1 outer iteration of the full workload per step"},
+           "e2e": {"value": round(v, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    return out, rank
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="planc", choices=["planc", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--alg", default=None)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warmup raised to 3 (timing rule)")
+        args.warmup = 3
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        out, rank = run_reference(args, cfg)
+    else:
+        out, rank = run_planc(args, cfg)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "planc":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * planc.h -- C ABI of libplanc.so, a GB300 (sm_103a) implementation of the
+ * hot path of alternating-update non-negative CP decomposition (NNCP) as
+ * described in "PLANC: Parallel Low-rank Approximation with Non-negativity
+ * Constraints" (arXiv 1909.01149).
+ *
+ * The problem (Eq. nncp):  min_{H^(n) >= 0} || X - sum_r H^(1)(:,r) o ... o
+ * H^(N)(:,r) ||^2, solved by the alternating updates of Alg. 1 with the
+ * normalisation and error computation of Alg. 4.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns a planc_status_t; nothing throws or aborts across the
+ *    ABI.  On failure planc_last_error(ctx) holds a one-line message.
+ *  - X is an I_1 x ... x I_N dense tensor stored linearly with mode 1
+ *    fastest (the paper's "natural mode-descending" order, Sec. 4.1.2).
+ *    It lives in device memory, is BORROWED by planc_init and must stay
+ *    alive and unchanged until planc_destroy.
+ *  - A factor matrix H^(n) is I_n x R, ROW-MAJOR (the R entries of a row are
+ *    contiguous), in device memory, of the context's factor dtype (F64 when X
+ *    is F64, else F32).  "void* const* H" is a HOST array of N device
+ *    pointers, one per mode.
+ *  - MTTKRP results M^(n) have the same layout as H^(n).
+ *  - Gram matrices G^(n) = H^(n)^T H^(n) and S^(n) are R x R row-major
+ *    double (FP64) in device memory; "G" arrays hold N of them back to back.
+ *  - lambda is a length-R double vector.
+ *  - All device buffers passed in are caller-owned; the library owns only
+ *    its workspace (partial-MTTKRP temporaries, split-K partials, reduction
+ *    scratch), allocated in planc_init and freed in planc_destroy.
+ *  - Calls are asynchronous on the context's CUDA stream, except those that
+ *    return host scalars (planc_fit, planc_nncp_solve, planc_cp_grad), which
+ *    synchronise that stream before returning.
+ *  - Modes are 0-based at the ABI (mode n = paper's mode n+1).
+ */
+#ifndef PLANC_H
+#define PLANC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PLANC_OK = 0,
+  PLANC_E_INVALID = 1,        /* bad argument (NULL pointer, out-of-range n) */
+  PLANC_E_SHAPE = 2,          /* N < 2, R < 1, a dimension < 1, size overflow */
+  PLANC_E_DTYPE = 3,          /* unsupported dtype combination */
+  PLANC_E_NOMEM = 4,          /* workspace allocation failed */
+  PLANC_E_CUDA = 5,           /* a CUDA runtime/driver call failed */
+  PLANC_E_NUMERIC = 6,        /* non-finite value or failed Cholesky */
+  PLANC_E_NOT_CONVERGED = 7,  /* reserved: NNLS caps are reported, not errors */
+  PLANC_E_TIMEOUT = 8,        /* a bounded device-side wait gave up */
+  PLANC_E_UNSUPPORTED = 9     /* valid request this build does not implement */
+} planc_status_t;
+
+typedef enum { PLANC_F64 = 0, PLANC_F32 = 1, PLANC_BF16 = 2, PLANC_F16 = 3 } planc_dtype_t;
+
+/* NNLS-Update choices of Sec. 4.3 (MU, HALS, BPP, ADMM) plus projected
+ * gradient (PGD), the project's gradient-driven option. */
+typedef enum {
+  PLANC_MU = 0, PLANC_HALS = 1, PLANC_BPP = 2, PLANC_ADMM = 3, PLANC_PGD = 4
+} planc_nls_t;
+
+/* Tuning of the NNLS updates; planc_nls_opts_default() fills the values the
+ * library's readings of Sec. 4.3 use. */
+typedef struct {
+  double mu_eps;        /* MU denominator guard (Eq. muupd): 1e-16 */
+  int admm_max_inner;   /* ADMM inner steps cap (Sec. 4.3.4): 5 */
+  double admm_tol;      /* ADMM primal/dual stopping ratio: 1e-2 */
+  int bpp_max_iter;     /* BPP exchange cap; <= 0 means 10 * R */
+  int pgd_steps;        /* projected-gradient steps per update: 1 */
+} planc_nls_opts;
+
+/* Options of planc_nncp_solve. */
+typedef struct {
+  planc_nls_t alg;      /* NNLS-Update of Alg. 1 */
+  int iters;            /* outer iterations to run (Sec. 6.1.2: fixed count) */
+  double tol;           /* stop when rel. error <= tol; <= 0 runs all iters */
+  planc_nls_opts nls;
+  int use_graph;        /* 1: replay each outer iteration as a CUDA graph */
+  int profile;          /* 1: time the partial-MTTKRP launches with events */
+} planc_solve_opts;
+
+/* Result record of planc_nncp_solve (host memory). */
+typedef struct {
+  int iters_done;
+  double rel_err;       /* eps of the last outer iteration (Alg. 4) */
+  double fit;           /* 1 - eps */
+  double* rel_err_hist; /* optional host array, length >= opts.iters */
+  int32_t* inner_hist;  /* optional host array, length >= opts.iters * N:
+                           inner steps per NNLS call (ADMM steps, max BPP
+                           exchanges over rows, 1 for MU/HALS/PGD) */
+  int bpp_unconverged;  /* rows whose BPP hit the exchange cap (summed) */
+  float pm_ms;          /* profile: summed time of the partial MTTKRPs */
+  int pm_launches;      /* profile: number of partial-MTTKRP launches timed */
+  long long launches;   /* kernels this call launched (graph replays included) */
+  int pm_tensor_cores;  /* bit 0 / bit 1: left / right partial MTTKRP ran on
+                           the tcgen05 tensor-core path */
+} planc_report;
+
+typedef struct planc_ctx* planc_t;
+
+/* ---- status and defaults ------------------------------------------------ */
+
+/* Static string naming a status code. */
+const char* planc_status_str(planc_status_t s);
+
+/* Last error message of ctx (empty string if none); valid until the next
+ * call on ctx.  planc_last_error(NULL) returns the last error of a failed
+ * planc_init on the calling thread. */
+const char* planc_last_error(planc_t ctx);
+
+/* Default NNLS options (see planc_nls_opts). Never fails. */
+planc_nls_opts planc_nls_opts_default(void);
+
+/* Root split S of the dimension tree (Sec. 4.2.2) for dims[0..N-1], returned
+ * 1-based in *split (1 <= S < N): the contiguous split whose two mode
+ * products are nearest (minimal |log(prod_{k<S} I_k / prod_{k>=S} I_k)|),
+ * ties to the larger S.  Host-only.  PLANC_E_SHAPE on N < 2 or dims < 1. */
+planc_status_t planc_plan_split(int N, const int64_t* dims, int* split);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context for the tensor X (Alg. 1 "Require").
+ *   N, dims      order and mode sizes (N >= 2, dims[n] >= 1, prod < 2^40)
+ *   R            CP rank (1 <= R <= 256)
+ *   x_dtype, X   storage type and device pointer of X (borrowed, see above);
+ *                F32/BF16/F16 data are accumulated in FP32, F64 in FP64
+ *   f_dtype      factor dtype: F64 iff x_dtype is F64, else F32
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ *   split        root split S, 1-based; -1 chooses planc_plan_split's S
+ * Allocates the workspace (dimension-tree temporaries, split-K partials,
+ * reduction scratch).  Errors: PLANC_E_SHAPE, PLANC_E_DTYPE, PLANC_E_INVALID,
+ * PLANC_E_NOMEM, PLANC_E_CUDA (no device / not sm_103). */
+planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R,
+                          planc_dtype_t x_dtype, const void* X,
+                          planc_dtype_t f_dtype, void* cuda_stream, int split);
+
+/* Free the workspace and the context (NULL is a no-op). */
+planc_status_t planc_destroy(planc_t ctx);
+
+/* The split S (1-based) the context uses. */
+int planc_get_split(planc_t ctx);
+
+/* Text of the dimension tree used for dims[0..N-1] with root split `split`
+ * (1-based; -1 = planc_plan_split's choice): the root line, then one line per
+ * edge, "PM {1,...,N} -> {a,...,b}" for the two partial MTTKRPs and
+ * "mTTV {c,...,b} -> {...}" for the multi-TTVs of Alg. 3 (below the root the
+ * first mode of a node is split off, Fig. ourDT).  Host-only; writes at most
+ * len bytes including the terminating NUL.  PLANC_E_INVALID if it does not
+ * fit, PLANC_E_SHAPE on a bad N or split. */
+planc_status_t planc_describe(int N, const int64_t* dims, int split, char* buf, size_t len);
+
+/* ---- the steps of Alg. 1 ------------------------------------------------ */
+
+/* alpha = ||X||^2 (Alg. 4, Norm-Squared), FP64 result written to the device
+ * double *alpha.  Asynchronous. */
+planc_status_t planc_sqnorm(planc_t ctx, double* alpha);
+
+/* M^(n) = X_(n) (H^N kr ... kr H^(n+1) kr H^(n-1) kr ... kr H^1)
+ * (Alg. 1 MTTKRP), computed through the dimension tree of Alg. 3: the
+ * partial MTTKRP of the root branch that holds mode n followed by the
+ * multi-TTV chain down to leaf n.  H[k] for k != n are read; H[n] is not.
+ * M is a device I_n x R row-major buffer (caller-owned).  Asynchronous.
+ * Errors: PLANC_E_INVALID (n out of range, NULL pointers). */
+planc_status_t planc_mttkrp(planc_t ctx, void* const* H, int n, void* M);
+
+/* Partial MTTKRP (Sec. 4.2.2) of one root branch:
+ *   side 0: T^{1:S} = X_(1:S) K^{S+1:N}  ((prod_{k<S} I_k) x R)
+ *   side 1: T^{S+1:N} = X_(1:S)^T K^{1:S}  ((prod_{k>=S} I_k) x R)
+ * written column-major (R slowest) to the device buffer T.  The benchmark
+ * and the tests use this to time and check the HBM-bound kernel alone. */
+planc_status_t planc_partial_mttkrp(planc_t ctx, void* const* H, int side,
+                                    void* T);
+
+/* S^(n) = G^(1) * ... * G^(n-1) * G^(n+1) * ... * G^(N) (Alg. 1 line "S").
+ * G: device N*R*R doubles; S: device R*R doubles.  Asynchronous. */
+planc_status_t planc_gram_hadamard(planc_t ctx, const double* G, int n,
+                                   double* S);
+
+/* G = H^T H (Alg. 1, local SYRK) for a rows x R row-major factor H (ctx
+ * factor dtype), accumulated with FP64 across row blocks; G device R*R
+ * doubles.  Asynchronous. */
+planc_status_t planc_gram(planc_t ctx, int64_t rows, const void* H, double* G);
+
+/* NNLS-Update (Alg. 1; Sec. 4.3): updates the rows x R row-major Hhat in
+ * place, given S (device R*R doubles, symmetric positive semidefinite) and
+ * M (device rows x R, ctx factor dtype).  On entry H is the warm start; on
+ * exit the updated (unnormalised) factor.
+ *   alg  MU (Eq. muupd, one step), HALS (Eq. halsupd, one sweep in column
+ *        order), BPP (Eq. snls, exact NNLS per row, FP64 passive-set
+ *        Cholesky), ADMM (Eq. admmupd, FP64 Cholesky of S + rho I, U reset
+ *        to zero), PGD (projected gradient).
+ *   opts may be NULL (defaults).
+ *   aux  ADMM dual U (device rows x R) to use and return, or NULL for the
+ *        library's zero-initialised scratch; ignored by other algorithms.
+ *   inner_iters  device int32 or NULL: ADMM steps taken / max BPP exchanges
+ *        over rows (1 for MU, HALS; pgd_steps for PGD).
+ * Asynchronous.  A BPP row that hits the exchange cap returns its current
+ * clipped iterate (no error).  Errors: PLANC_E_INVALID, PLANC_E_SHAPE
+ * (rows > the largest mode of the context). */
+planc_status_t planc_nls_update(planc_t ctx, planc_nls_t alg,
+                                const planc_nls_opts* opts, int64_t rows,
+                                const double* S, const void* M, void* H,
+                                void* aux, int32_t* inner_iters);
+
+/* Column normalisation of Alg. 4: lambda_r = ||Hhat(:, r)||_2 (FP64
+ * accumulation), H = Hhat diag(lambda)^{-1} in place (a zero column keeps
+ * lambda_r = 0 and stays zero), and, if G is not NULL, G = H^T H of the
+ * normalised H.  lambda: device R doubles.  Asynchronous. */
+planc_status_t planc_normalize(planc_t ctx, int64_t rows, void* H,
+                               double* lambda, double* G);
+
+/* Relative error of the model [[lambda; H^(1..N)]] by the identity of
+ * Sec. A.2 / Alg. 4: eps = sqrt(max(0, alpha - 2 beta + gamma) / alpha) with
+ * alpha = ||X||^2, beta = <M^(N), H^(N) diag(lambda)>, gamma = lambda^T
+ * (G^(1) * ... * G^(N)) lambda.  Runs an MTTKRP for the last mode.
+ * lambda is a DEVICE double[R]; rel_err and fit are HOST doubles (fit =
+ * 1 - eps; either may be NULL).  Synchronises the stream. */
+planc_status_t planc_fit(planc_t ctx, void* const* H, const double* lambda,
+                         double* rel_err, double* fit);
+
+/* The whole of Alg. 1 + Alg. 4: alpha = ||X||^2, lambda = 1, G^(n) of the
+ * initial factors, then opts->iters outer iterations of (dimension-tree
+ * MTTKRP, S^(n), NNLS-Update with warm start H^(n) diag(lambda),
+ * normalisation, G^(n)) for n = 1..N and the error identity after mode N.
+ * H: host array of N device pointers, initial factors in, normalised
+ * factors out.  lambda: HOST double[R] out.  report: optional host record.
+ * Synchronises the stream. */
+planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts,
+                                void* const* H, double* lambda,
+                                planc_report* report);
+
+/* Default solve options: HALS, 10 iterations, tol 0, default NNLS options,
+ * graph replay on, profiling off. */
+planc_solve_opts planc_solve_opts_default(void);
+
+/* CP reconstruction loss f = ||X - [[H^(1..N)]]||^2 (Eq. nncp objective,
+ * lambda = 1) and its gradient df/dH^(n) = 2 (H^(n) S^(n) - M^(n)) for every
+ * mode (the MTTKRP and Hadamard-of-Grams matrices of Alg. 1).  H and dH:
+ * host arrays of N device pointers (dH row-major I_n x R, caller-owned).
+ * loss: HOST double (may be NULL).  The two root partial MTTKRPs are each
+ * computed once from the given factors (2 passes over X for any N) and the
+ * multi-TTV chains are recomputed per mode, nothing else is stored.
+ * Synchronises the stream. */
+planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,
+                             double* loss);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLANC_H */

@@ -36,6 +36,7 @@ from .nncp import (  # noqa: F401
     khatri_rao,
     krp_except,
     mttkrp,
+    mttkrp_rows,
     mttkrp_bruteforce,
     gram,
     gram_hadamard,

@@ -71,6 +71,16 @@ def mttkrp(X: np.ndarray, H, n: int) -> np.ndarray:
     return unfold(X, n) @ krp_except(H, n)
 
 
+def mttkrp_rows(X: np.ndarray, H, n: int, rows) -> np.ndarray:
+    """Selected rows of M^(n): the definition applied to the sub-tensor
+    X[..., rows, ...] (mode n restricted to `rows`).  Lets a full-size result
+    be sampled without forming the whole matricization."""
+    idx = [slice(None)] * X.ndim
+    idx[n] = np.asarray(rows)
+    Xs = np.asarray(X[tuple(idx)], dtype=np.float64)
+    return mttkrp(Xs, [h if k != n else h[np.asarray(rows)] for k, h in enumerate(H)], n)
+
+
 def mttkrp_bruteforce(X: np.ndarray, H, n: int) -> np.ndarray:
     """Element-wise MTTKRP sum with Python loops; for tiny tensors only.
 
@@ -212,7 +222,8 @@ def nls_admm(S, M, H, U=None, max_inner: int = ADMM_MAX_INNER,
     hold (tol = 1e-2); the paper defers the exact rule to its reference.
     """
     R = S.shape[0]
-    rho = float(np.trace(S)) / R
+    tr = float(np.trace(S))
+    rho = tr / R if tr > 0 else 1.0  # reading: an all-zero S uses rho = 1
     L = np.linalg.cholesky(S + rho * np.eye(R))
     H = np.array(H, dtype=np.float64, copy=True)
     U = np.zeros_like(H) if U is None else np.array(U, dtype=np.float64)
@@ -351,7 +362,8 @@ def fit_identity(alpha, M_N, Hhat_N, S_N, G_N, lam):
     Returns (eps, fit)."""
     beta = float(np.sum(M_N * Hhat_N))
     gamma = float(lam @ (S_N * G_N) @ lam)
-    eps = math.sqrt(max(0.0, alpha - 2.0 * beta + gamma) / alpha)
+    # reading: an all-zero tensor (alpha = 0) reports eps = 0
+    eps = math.sqrt(max(0.0, alpha - 2.0 * beta + gamma) / alpha) if alpha > 0 else 0.0
     return eps, 1.0 - eps
 
 

@@ -6,11 +6,12 @@ binding is imported lazily so that ``synth`` (seeded inputs) can be used on a
 machine without the built library.
 """
 
+import importlib
+
 __all__ = ["planc", "synth"]
 
 
 def __getattr__(name):
-    if name == "planc":
-        from . import planc
-        return planc
+    if name in ("planc", "synth"):
+        return importlib.import_module("." + name, __name__)
     raise AttributeError(name)

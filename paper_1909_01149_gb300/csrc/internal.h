@@ -1,0 +1,170 @@
+// Internal declarations of libplanc: the context, and the host launchers of
+// every kernel (each launcher lives beside its kernels in a .cu file).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/planc.h"
+#include "common.cuh"
+
+namespace planc {
+
+// Type-erased description of a partial Khatri-Rao product (see Krp<TF>).
+struct KrpHost {
+  int nm = 0;
+  int64_t dim[PLANC_MAX_N] = {};
+  const void* H[PLANC_MAX_N] = {};
+};
+
+// Count of kernels this library has launched (all contexts); the solve
+// reports how many of its kernels ran.
+void note_launches(int n);
+long long launch_count();
+
+inline size_t dtype_size(planc_dtype_t d) {
+  return d == PLANC_F64 ? 8 : d == PLANC_F32 ? 4 : 2;
+}
+
+// ---- partial MTTKRP (root branches of the dimension tree, Sec. 4.2.2) -----
+// SIMT path, any dtype/shape/rank.  Computes, for side "left",
+//   out[m, r] = sum_{c<C} X[m + L c] * K[c, r]           (m < L)
+// and for side "right"
+//   out[m, r] = sum_{l<L} X[l + L m] * K[l, r]           (m < C)
+// with K the partial Khatri-Rao product `krp`.  Output is R-slowest
+// (out[m + Mdim r]) or row-major (out[m R + r]).  With nsplit > 1 the
+// reduction dimension is split over CTAs into `part` (nsplit x Mdim x R)
+// and summed in a fixed order by a second kernel.
+int pm_simt_nsplit(bool left, int64_t L, int64_t C, int R, int sm_count);
+cudaError_t launch_pm_simt(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
+                           bool left, const KrpHost& krp, int R, void* out,
+                           bool out_rowmajor, void* part, int nsplit, cudaStream_t st);
+
+// tcgen05 path (FP32 X as 3xTF32, BF16/F16 X as kind::f16 with a two-term
+// BF16 split of the Khatri-Rao operand).  Returns cudaErrorNotSupported when
+// the shape/rank/dtype is not eligible; the caller then uses the SIMT path.
+bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R);
+size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
+                             int sm_count);
+cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
+                         bool left, const KrpHost& krp, int R, void* out,
+                         bool out_rowmajor, void* work, size_t work_bytes,
+                         int* err_flag, int sm_count, cudaStream_t st);
+
+// ---- multi-TTV (Sec. 4.2.2) --------------------------------------------------
+// T is the node tensor T^{a:b} viewed as T[p + P1 q + P1 Q r].
+// contract_first: out[q, r] = sum_p T[p, q, r] h[p, r]  (h row-major P1 x R)
+// contract_rest : out[p, r] = sum_q T[p, q, r] K[q, r]  (K partial KRP)
+cudaError_t launch_contract_first(bool f64, const void* T, int64_t P1, int64_t Q, int R,
+                                  const void* h, void* out, bool out_rowmajor,
+                                  cudaStream_t st);
+int contract_rest_qsplit(int64_t P1, int64_t Q, int R, int sm_count);
+cudaError_t launch_contract_rest(bool f64, const void* T, int64_t P1, int64_t Q, int R,
+                                 const KrpHost& krp, void* out, void* part, int qsplit,
+                                 cudaStream_t st);
+
+// ---- reductions, Grams, normalisation, error ---------------------------------
+int sqnorm_blocks(int64_t n, int sm_count);
+cudaError_t launch_sqnorm(planc_dtype_t xdt, const void* X, int64_t n, double* part,
+                          int nblk, double* alpha, cudaStream_t st);
+cudaError_t launch_gram_hadamard(const double* G, int N, int n, int R, double* S,
+                                 cudaStream_t st);
+int rowblocks(int64_t rows);
+// Column sums of squares of Hhat per row block (FP64 partials) and, if M is
+// given, per-block partials of <M, Hhat>.
+cudaError_t launch_colsq(bool f64, int64_t rows, int R, const void* Hhat, const void* M,
+                         double* colsq_part, double* dot_part, int nblk, cudaStream_t st);
+// lambda from the partials, H = Hhat / lambda in place, FP64 Gram partials.
+cudaError_t launch_scale_gram(bool f64, int64_t rows, int R, void* H, const double* colsq_part,
+                              int nblk, double* lambda, double* gram_part, bool scale,
+                              cudaStream_t st);
+// G = sum of the Gram partials (fixed order).
+cudaError_t launch_gram_reduce(int R, const double* gram_part, int nblk, double* G,
+                               cudaStream_t st);
+// The error identity of Alg. 4: eps = sqrt(max(0, alpha - 2 beta + gamma) /
+// alpha) with beta = sum of the dot partials and gamma = lambda^T (G^(1) *
+// ... * G^(N)) lambda.  fit_out receives {eps, beta, gamma}.
+cudaError_t launch_fit(int R, const double* Gall, int N, const double* lambda,
+                       const double* dot_part, int dot_nblk, const double* alpha,
+                       double* fit_out, cudaStream_t st);
+// <M, H diag(lambda)> partials for planc_fit.
+cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, const void* H,
+                              const double* lambda, double* dot_part, int nblk,
+                              cudaStream_t st);
+cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st);
+
+// ---- NNLS updates (Sec. 4.3) ---------------------------------------------------
+struct NlsArgs {
+  planc_nls_t alg;
+  planc_nls_opts opts;
+  int64_t rows;
+  int R;
+  const double* S;        // R x R FP64
+  const void* M;          // rows x R
+  void* H;                // rows x R, in/out
+  const double* lambda;   // warm-start column scale (NULL = none)
+  void* U;                // ADMM dual (rows x R)
+  bool U_zero;            // ADMM: start from U = 0 (else read U)
+  int32_t* inner;         // device int or NULL
+  double* scratch;        // FP64 scratch (>= nls_scratch_doubles)
+  int* flags;             // int scratch (>= 8 ints)
+  bool f64;
+};
+size_t nls_scratch_doubles(int64_t rows, int R);
+cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st);
+
+// ---- PM-right / mTTV split reductions -------------------------------------------
+cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,
+                                void* out, bool out_rowmajor, cudaStream_t st);
+
+}  // namespace planc
+
+// ---- the context ------------------------------------------------------------------
+struct planc_ctx {
+  int N = 0, R = 0, S = 0;          // S: number of modes in the left branch
+  int64_t dims[PLANC_MAX_N] = {};
+  int64_t L = 1, C = 1, I = 1, max_dim = 1;
+  planc_dtype_t xd = PLANC_F32, fd = PLANC_F32;
+  const void* X = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 148;
+  std::string err;
+
+  // workspace (one allocation, carved)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* T_side[2] = {nullptr, nullptr};  // root partials T^{1:S}, T^{S+1:N}
+  void* node[2] = {nullptr, nullptr};    // internal-node ping-pong
+  void* part = nullptr;                  // split-K / q-split partials
+  size_t part_bytes = 0;
+  void* tc_work = nullptr;               // tcgen05 path scratch
+  size_t tc_bytes = 0;
+  int* tc_err = nullptr;                 // tcgen05 bounded-wait error flag
+  void* Mbuf = nullptr;                  // max_dim x R
+  void* Ubuf = nullptr;                  // ADMM dual, max_dim x R
+  double* G = nullptr;                   // N x R x R
+  double* Sm = nullptr;                  // R x R
+  double* lam = nullptr;                 // R
+  double* scal = nullptr;                // [0] alpha, [1..] scratch
+  double* hist = nullptr;                // per-iteration rel. error (device)
+  int hist_cap = 0;
+  double* red = nullptr;                 // reduction partials
+  size_t red_doubles = 0;
+  double* nls_scr = nullptr;             // NNLS scratch
+  size_t nls_scr_doubles = 0;
+  int32_t* inner = nullptr;              // per-call inner counts (device)
+  int inner_cap = 0;
+  int* flags = nullptr;
+
+  // dimension-tree state during a solve
+  int nsplit[2] = {1, 1};
+  bool use_tc[2] = {false, false};
+  size_t node_elems = 0;
+
+  // profiling (partial-MTTKRP launches)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+};

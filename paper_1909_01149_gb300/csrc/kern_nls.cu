@@ -1,0 +1,532 @@
+// NNLS-Update kernels (Sec. 4.3): MU, HALS, ADMM, BPP and projected
+// gradient, all in the row form of Eq. nls (rows of Hhat are independent,
+// given S = K^T K and M = X_(n) K).
+//
+// MU, HALS, ADMM steps and PGD keep one row per thread with the row in
+// registers (R padded to RP in {16, 32, 64}) and S (or the ADMM inverse) in
+// shared memory, read as warp-wide broadcasts.  BPP gives each row a warp
+// and does its passive-set Cholesky solves in FP64.  ADMM factors S + rho I
+// once per call in FP64 and keeps the explicit inverse for the row solves.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace planc {
+
+namespace {
+
+constexpr int ROWS_PER_CTA = 32;  // one warp per CTA: rows spread over many SMs
+
+// Stage S (FP64, R x R) into shared memory as TA, zero-padded to RP x RP.
+template <typename TA, int RP>
+__device__ __forceinline__ void stage_S(TA* Ss, const double* __restrict__ S, int R) {
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+    int i = e / RP, j = e - i * RP;
+    Ss[e] = (i < R && j < R) ? (TA)S[i * R + j] : TA(0);
+  }
+}
+
+template <typename TA, int RP>
+__device__ __forceinline__ void load_row(TA* v, const TA* __restrict__ src, int64_t row, int R,
+                                         const double* __restrict__ lam) {
+#pragma unroll
+  for (int k = 0; k < RP; ++k) {
+    TA x = TA(0);
+    if (k < R) {
+      x = src[row * R + k];
+      if (lam) x = (TA)((double)x * lam[k]);
+    }
+    v[k] = x;
+  }
+}
+
+// d = sum_k v[k] * Srow[k], four independent chains
+template <typename TA, int RP>
+__device__ __forceinline__ TA dot_row(const TA* v, const TA* Srow) {
+  TA a0 = TA(0), a1 = TA(0), a2 = TA(0), a3 = TA(0);
+#pragma unroll
+  for (int k = 0; k < RP; k += 4) {
+    a0 = fma(v[k + 0], Srow[k + 0], a0);
+    a1 = fma(v[k + 1], Srow[k + 1], a1);
+    a2 = fma(v[k + 2], Srow[k + 2], a2);
+    a3 = fma(v[k + 3], Srow[k + 3], a3);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Per-thread row storage in shared memory: element k of the calling thread's
+// row lives at v[k * ROWS_PER_CTA + lane] (each lane its own bank).
+template <typename TA>
+__device__ __forceinline__ TA& rowv(TA* v, int k) { return v[k * ROWS_PER_CTA + threadIdx.x]; }
+
+// ---- MU (Eq. muupd): H <- H * M / (H S + eps) ---------------------------------------
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+nls_mu_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
+              TA* __restrict__ H, const double* __restrict__ lam, double eps) {
+  __shared__ __align__(16) TA Ss[RP * RP];
+  stage_S<TA, RP>(Ss, S, R);
+  __syncthreads();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  TA h[RP];
+  load_row<TA, RP>(h, H, i, R, lam);
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    TA d = dot_row<TA, RP>(h, Ss + r * RP);
+    TA hr = H[i * R + r];
+    if (lam) hr = (TA)((double)hr * lam[r]);
+    H[i * R + r] = hr * M[i * R + r] / (d + (TA)eps);
+  }
+}
+
+// ---- HALS (Eq. halsupd): one Gauss-Seidel sweep over the columns ----------------------
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+nls_hals_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
+                TA* __restrict__ H, const double* __restrict__ lam, double tiny) {
+  __shared__ __align__(16) TA Ss[RP * RP];
+  __shared__ TA hv[RP * ROWS_PER_CTA];
+  stage_S<TA, RP>(Ss, S, R);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < rows;
+  for (int k = 0; k < RP; ++k) {
+    TA x = TA(0);
+    if (live && k < R) {
+      x = H[i * R + k];
+      if (lam) x = (TA)((double)x * lam[k]);
+    }
+    rowv(hv, k) = x;
+  }
+  __syncthreads();
+  if (!live) return;
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    TA srr = Ss[r * RP + r];
+    if (srr > (TA)tiny) {
+      const TA* Sr = Ss + r * RP;
+      TA a0 = TA(0), a1 = TA(0), a2 = TA(0), a3 = TA(0);
+#pragma unroll
+      for (int k = 0; k < RP; k += 4) {
+        a0 = fma(rowv(hv, k + 0), Sr[k + 0], a0);
+        a1 = fma(rowv(hv, k + 1), Sr[k + 1], a1);
+        a2 = fma(rowv(hv, k + 2), Sr[k + 2], a2);
+        a3 = fma(rowv(hv, k + 3), Sr[k + 3], a3);
+      }
+      TA d = (a0 + a1) + (a2 + a3);
+      TA v = rowv(hv, r) + (M[i * R + r] - d) / srr;
+      rowv(hv, r) = v > TA(0) ? v : TA(0);
+    }
+  }
+  for (int r = 0; r < R; ++r) H[i * R + r] = rowv(hv, r);
+}
+
+// ---- projected gradient: H <- [H - eta (H S - M)]_+, eta = 1 / ||S||_F --------------
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+nls_pgd_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
+               TA* __restrict__ H, const double* __restrict__ lam, int steps) {
+  __shared__ __align__(16) TA Ss[RP * RP];
+  __shared__ TA hv[RP * ROWS_PER_CTA];
+  stage_S<TA, RP>(Ss, S, R);
+  // eta = 1 / ||S||_F; every lane holds the warp-wide sum (one warp per CTA)
+  double f = 0.0;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) f += S[e] * S[e];
+  f = warp_sum(f);
+  __syncthreads();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const TA eta = (TA)(1.0 / fmax(sqrt(f), 1e-300));
+  TA h[RP];
+  load_row<TA, RP>(h, H, i, R, lam);
+#pragma unroll
+  for (int k = 0; k < RP; ++k) rowv(hv, k) = h[k];
+  for (int st = 0; st < steps; ++st) {
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      TA g = dot_row<TA, RP>(h, Ss + r * RP) - M[i * R + r];
+      TA x = rowv(hv, r) - eta * g;
+      rowv(hv, r) = x > TA(0) ? x : TA(0);
+    }
+#pragma unroll
+    for (int k = 0; k < RP; ++k) h[k] = rowv(hv, k);
+  }
+  for (int r = 0; r < R; ++r) H[i * R + r] = rowv(hv, r);
+}
+
+// ---- ADMM (Eq. admmupd) --------------------------------------------------------------
+// Scratch layout (doubles): [0] rho, [1] Cholesky status, [8 ..) W = (S + rho I)^{-1}
+// (R x R, FP64), then W as TA, then per-step per-block norm partials.
+constexpr int ADMM_W = 8;
+
+__global__ void __launch_bounds__(256)
+admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64) {
+  extern __shared__ double sm[];
+  double* A = sm;             // R x R: S + rho I, then its Cholesky factor (lower)
+  double* Li = sm + R * R;    // R x R: L^{-1} (lower)
+  __shared__ double s_rho;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int r = 0; r < R; ++r) tr += S[r * R + r];
+    // reading: rho = trace(S) / R; an all-zero S (no information) uses rho = 1
+    s_rho = tr > 0.0 ? tr / R : 1.0;
+    s_bad = 0;
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += nt) {
+    int i = e / R, j = e - i * R;
+    A[e] = S[e] + (i == j ? s_rho : 0.0);
+    Li[e] = 0.0;
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle
+  for (int c = 0; c < R; ++c) {
+    if (tid == 0) {
+      double d = A[c * R + c];
+      if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
+      A[c * R + c] = sqrt(d);
+    }
+    __syncthreads();
+    double dc = A[c * R + c];
+    for (int i = c + 1 + tid; i < R; i += nt) A[i * R + c] /= dc;
+    __syncthreads();
+    int m = R - c - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      int i = c + 1 + e / m, j = c + 1 + e % m;
+      if (j <= i) A[i * R + j] -= A[i * R + c] * A[j * R + c];
+    }
+    __syncthreads();
+  }
+  // L^{-1}: column j by forward substitution (one thread per column)
+  for (int j = tid; j < R; j += nt) {
+    for (int i = j; i < R; ++i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) s -= A[i * R + k] * Li[k * R + j];
+      Li[i * R + j] = s / A[i * R + i];
+    }
+  }
+  __syncthreads();
+  // W = L^{-T} L^{-1}
+  double* W = scr + ADMM_W;
+  for (int e = tid; e < R * R; e += nt) {
+    int i = e / R, j = e - i * R;
+    int k0 = i > j ? i : j;
+    double s = 0.0;
+    for (int k = k0; k < R; ++k) s += Li[k * R + i] * Li[k * R + j];
+    W[e] = s;
+    if (wtf_f64) ((double*)(W + R * R))[e] = s;
+    else ((float*)(W + R * R))[e] = (float)s;
+  }
+  if (tid == 0) { scr[0] = s_rho; scr[1] = s_bad; }
+}
+
+// step k of at most kmax; part holds 4 norms per block per step
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+admm_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ H,
+                 TA* __restrict__ U, const double* __restrict__ lam, const double* __restrict__ scr,
+                 double* __restrict__ part, int nblk, int k, double tol, int u_zero,
+                 int32_t* __restrict__ inner) {
+  extern __shared__ __align__(16) unsigned char admm_smem[];
+  TA* Ws = reinterpret_cast<TA*>(admm_smem);   // RP x RP
+  TA* hv = Ws + RP * RP;                          // RP x ROWS_PER_CTA
+  TA* uv = hv + RP * ROWS_PER_CTA;                // RP x ROWS_PER_CTA
+  __shared__ int s_stop;
+  __shared__ double s_red[4][ROWS_PER_CTA];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int stop = 0;
+    for (int j = 0; j < k && !stop; ++j) {
+      double a = 0, b = 0, c = 0, d = 0;
+      const double* pj = part + (int64_t)j * nblk * 4;
+      for (int bl = 0; bl < nblk; ++bl) {
+        a += pj[bl * 4 + 0]; b += pj[bl * 4 + 1]; c += pj[bl * 4 + 2]; d += pj[bl * 4 + 3];
+      }
+      if (a < tol * b && c < tol * d) stop = 1;
+    }
+    s_stop = stop;
+  }
+  const TA* Wt = (const TA*)(scr + ADMM_W + R * R);
+  for (int e = tid; e < RP * RP; e += blockDim.x) {
+    int i = e / RP, j = e - i * RP;
+    Ws[e] = (i < R && j < R) ? Wt[i * R + j] : TA(0);
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const TA rho = (TA)scr[0];
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+  TA n_pr = TA(0), n_h = TA(0), n_du = TA(0), n_u = TA(0);
+  if (i < rows) {
+    TA rhs[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      TA h = TA(0), u = TA(0), m = TA(0);
+      if (r < R) {
+        h = H[i * R + r];
+        if (k == 0 && lam) h = (TA)((double)h * lam[r]);
+        if (!(u_zero && k == 0)) u = U[i * R + r];
+        m = M[i * R + r];
+      }
+      rowv(hv, r) = h;
+      rowv(uv, r) = u;
+      rhs[r] = m + rho * (h + u);
+    }
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      TA ht = dot_row<TA, RP>(rhs, Ws + r * RP);  // W symmetric
+      TA ur = rowv(uv, r), hr = rowv(hv, r);
+      TA hn = ht - ur;
+      hn = hn > TA(0) ? hn : TA(0);
+      TA un = ur + hn - ht;
+      H[i * R + r] = hn;
+      U[i * R + r] = un;
+      n_pr = fma(hn - ht, hn - ht, n_pr);
+      n_h = fma(hn, hn, n_h);
+      n_du = fma(hn - hr, hn - hr, n_du);
+      n_u = fma(un, un, n_u);
+    }
+  }
+  s_red[0][tid] = (double)n_pr;
+  s_red[1][tid] = (double)n_h;
+  s_red[2][tid] = (double)n_du;
+  s_red[3][tid] = (double)n_u;
+  __syncthreads();
+  if (tid < 4) {
+    double s = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += s_red[tid][t];
+    part[((int64_t)k * nblk + blockIdx.x) * 4 + tid] = s;
+  }
+  if (tid == 0 && blockIdx.x == 0 && inner) *inner = k + 1;
+}
+
+// ---- BPP (Eq. snls; Kim-Park block principal pivoting) ---------------------------------
+// One warp per row, R <= 64 (lane j holds indices j and j + 32), FP64.
+constexpr int BPP_WARPS = 4;
+
+__device__ __forceinline__ uint64_t ballot64(bool lo, bool hi) {
+  uint64_t a = __ballot_sync(0xffffffffu, lo);
+  uint64_t b = __ballot_sync(0xffffffffu, hi);
+  return a | (b << 32);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(32 * BPP_WARPS)
+nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
+               TA* __restrict__ H, const double* __restrict__ lam, int max_iter,
+               int32_t* __restrict__ inner, int* __restrict__ flags) {
+  extern __shared__ double bsm[];
+  double* Ss = bsm;                                   // R x R
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* A = bsm + R * R + (size_t)warp * (R * R + 2 * 64);  // f x f (stride R)
+  double* xs = A + R * R;                              // 64: passive solution / rhs
+  double* zs = xs + 64;                                // 64: full x
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ss[e] = S[e];
+  __syncthreads();
+  const int64_t row = (int64_t)blockIdx.x * BPP_WARPS + warp;
+  if (row >= rows) return;
+
+  const int j0 = lane, j1 = lane + 32;
+  const bool v0 = j0 < R, v1 = j1 < R;
+  double m0 = v0 ? (double)M[row * R + j0] : 0.0;
+  double m1 = v1 ? (double)M[row * R + j1] : 0.0;
+  double w0 = v0 ? (double)H[row * R + j0] * (lam ? lam[j0] : 1.0) : 0.0;
+  double w1 = v1 ? (double)H[row * R + j1] * (lam ? lam[j1] : 1.0) : 0.0;
+  uint64_t F = ballot64(v0 && w0 > 0.0, v1 && w1 > 0.0);  // passive set from the warm start
+  double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
+  int bad = 0;
+
+  // x_F = S_FF^{-1} m_F, x_G = 0; y = S x - m on G, 0 on F
+  auto solve = [&]() {
+    int f = __popcll(F);
+    // index list of F in xs-order: position of j in F = popc(F & ((1<<j)-1))
+    uint64_t below0 = (j0 == 0) ? 0ull : (F & ((1ull << j0) - 1ull));
+    uint64_t below1 = F & ((1ull << j1) - 1ull);
+    int p0 = __popcll(below0), p1 = __popcll(below1);
+    bool in0 = v0 && ((F >> j0) & 1ull), in1 = v1 && ((F >> j1) & 1ull);
+    // build A = S_FF (row-major, stride R) and rhs = m_F
+    // each lane owns the rows/cols of its indices: A[p_a][p_b] = S[a][b]
+    for (int a = 0; a < R; ++a) {
+      if (!((F >> a) & 1ull)) continue;
+      int pa = __popcll(a == 0 ? 0ull : (F & ((1ull << a) - 1ull)));
+      if (in0) A[pa * R + p0] = Ss[a * R + j0];
+      if (in1) A[pa * R + p1] = Ss[a * R + j1];
+    }
+    if (in0) xs[p0] = m0;
+    if (in1) xs[p1] = m1;
+    __syncwarp();
+    // Cholesky (lower) of A, f x f
+    for (int c = 0; c < f; ++c) {
+      if (lane == 0) {
+        double d = A[c * R + c];
+        if (!(d > 0.0)) { bad = 1; d = 1e-300; }
+        A[c * R + c] = sqrt(d);
+      }
+      __syncwarp();
+      double dc = A[c * R + c];
+      for (int i = c + 1 + lane; i < f; i += 32) A[i * R + c] /= dc;
+      __syncwarp();
+      int mm = f - c - 1;
+      for (int e = lane; e < mm * mm; e += 32) {
+        int i = c + 1 + e / mm, j = c + 1 + e % mm;
+        if (j <= i) A[i * R + j] -= A[i * R + c] * A[j * R + c];
+      }
+      __syncwarp();
+    }
+    // forward: L z = m_F (column-oriented)
+    for (int c = 0; c < f; ++c) {
+      double zc = xs[c] / A[c * R + c];
+      __syncwarp();
+      for (int i = c + 1 + lane; i < f; i += 32) xs[i] -= A[i * R + c] * zc;
+      if (lane == 0) xs[c] = zc;
+      __syncwarp();
+    }
+    // backward: L^T x = z
+    for (int c = f - 1; c >= 0; --c) {
+      double xc = xs[c] / A[c * R + c];
+      __syncwarp();
+      for (int i = lane; i < c; i += 32) xs[i] -= A[c * R + i] * xc;
+      if (lane == 0) xs[c] = xc;
+      __syncwarp();
+    }
+    x0 = in0 ? xs[p0] : 0.0;
+    x1 = in1 ? xs[p1] : 0.0;
+    if (v0) zs[j0] = x0;
+    if (v1) zs[j1] = x1;
+    __syncwarp();
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < R; ++k) {
+      double xk = zs[k];
+      if (v0) s0 += Ss[j0 * R + k] * xk;
+      if (v1) s1 += Ss[j1 * R + k] * xk;
+    }
+    y0 = (v0 && !in0) ? s0 - m0 : 0.0;
+    y1 = (v1 && !in1) ? s1 - m1 : 0.0;
+    __syncwarp();
+  };
+
+  solve();
+  int p = 3, ninf = R + 1, it = 0;
+  bool converged = false;
+  while (true) {
+    bool f0 = v0 && ((F >> j0) & 1ull), f1 = v1 && ((F >> j1) & 1ull);
+    bool i0 = v0 && (f0 ? x0 < 0.0 : y0 < 0.0);
+    bool i1 = v1 && (f1 ? x1 < 0.0 : y1 < 0.0);
+    uint64_t V = ballot64(i0, i1);
+    int nv = __popcll(V);
+    if (nv == 0) { converged = true; break; }
+    if (it >= max_iter) break;
+    uint64_t Vh;
+    if (nv < ninf) { ninf = nv; p = 3; Vh = V; }
+    else if (p >= 1) { --p; Vh = V; }
+    else { Vh = 1ull << (63 - __clzll(V)); }
+    F ^= Vh;
+    solve();
+    ++it;
+  }
+  if (v0) H[row * R + j0] = (TA)(x0 > 0.0 ? x0 : 0.0);
+  if (v1) H[row * R + j1] = (TA)(x1 > 0.0 ? x1 : 0.0);
+  if (lane == 0) {
+    if (inner) atomicMax(inner, it);
+    if (!converged) atomicAdd(flags + 0, 1);
+    if (bad) atomicAdd(flags + 1, 1);
+  }
+}
+
+__global__ void set_int_kernel(int32_t* p, int v, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+template <typename TA, int RP>
+cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
+  const int blocks = (int)((a.rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+  const TA* M = (const TA*)a.M;
+  TA* H = (TA*)a.H;
+  switch (a.alg) {
+    case PLANC_MU:
+      nls_mu_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(a.rows, a.R, a.S, M, H, a.lambda,
+                                                            a.opts.mu_eps);
+      note_launches(1);
+      break;
+    case PLANC_HALS:
+      nls_hals_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(
+          a.rows, a.R, a.S, M, H, a.lambda, sizeof(TA) == 8 ? 1e-300 : 1e-30);
+      note_launches(1);
+      break;
+    case PLANC_PGD:
+      nls_pgd_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(a.rows, a.R, a.S, M, H, a.lambda,
+                                                             std::max(1, a.opts.pgd_steps));
+      note_launches(1);
+      break;
+    case PLANC_ADMM: {
+      size_t smem = 2 * (size_t)a.R * a.R * sizeof(double);
+      cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8);
+      note_launches(1);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      double* part = a.scratch + ADMM_W + 2 * (size_t)a.R * a.R;
+      const int kmax = std::min(PLANC_MAX_ADMM_STEPS, std::max(1, a.opts.admm_max_inner));
+      const size_t ssm = (size_t)(RP * RP + 2 * RP * ROWS_PER_CTA) * sizeof(TA);
+      cudaFuncSetAttribute(admm_step_kernel<TA, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ssm);
+      for (int k = 0; k < kmax; ++k) {
+        admm_step_kernel<TA, RP><<<blocks, ROWS_PER_CTA, ssm, st>>>(
+            a.rows, a.R, M, H, (TA*)a.U, a.lambda, a.scratch, part, blocks, k, a.opts.admm_tol,
+            a.U_zero ? 1 : 0, a.inner);
+        note_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename TA>
+cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
+  if (a.alg == PLANC_BPP) {
+    const int blocks = (int)((a.rows + BPP_WARPS - 1) / BPP_WARPS);
+    size_t smem = ((size_t)a.R * a.R + BPP_WARPS * ((size_t)a.R * a.R + 128)) * sizeof(double);
+    cudaFuncSetAttribute(nls_bpp_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    if (a.inner) {
+      set_int_kernel<<<1, 32, 0, st>>>(a.inner, 0, 1);
+      note_launches(1);
+    }
+    int max_iter = a.opts.bpp_max_iter > 0 ? a.opts.bpp_max_iter : 10 * a.R;
+    nls_bpp_kernel<TA><<<blocks, 32 * BPP_WARPS, smem, st>>>(
+        a.rows, a.R, a.S, (const TA*)a.M, (TA*)a.H, a.lambda, max_iter, a.inner, a.flags);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  if (a.inner && a.alg != PLANC_ADMM) {
+    int v = a.alg == PLANC_PGD ? std::max(1, a.opts.pgd_steps) : 1;
+    set_int_kernel<<<1, 32, 0, st>>>(a.inner, v, 1);
+    note_launches(1);
+  }
+  if (a.R <= 16) return run_rowwise<TA, 16>(a, st);
+  if (a.R <= 32) return run_rowwise<TA, 32>(a, st);
+  return run_rowwise<TA, 64>(a, st);
+}
+
+}  // namespace
+
+size_t nls_scratch_doubles(int64_t rows, int R) {
+  int64_t blocks = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+  return ADMM_W + 2 * (size_t)R * R + (size_t)PLANC_MAX_ADMM_STEPS * blocks * 4 + 64;
+}
+
+cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st) {
+  if (a.R > PLANC_MAX_NLS_R) return cudaErrorNotSupported;
+  if (a.f64) return run_nls_t<double>(a, st);
+  return run_nls_t<float>(a, st);
+}
+
+}  // namespace planc

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of libplanc.so (include/planc.h).
+
+Argument marshalling only: every step of the NNCP hot path runs in the CUDA
+library.  PyTorch supplies device memory and the CUDA stream.  If the
+library has not been built, importing this module raises ImportError; there
+is no CPU fallback.
+
+Layouts (see include/planc.h): X is a contiguous 1-D device tensor holding
+the I_1 x ... x I_N tensor with mode 1 fastest; factors and MTTKRP results
+are contiguous I_n x R row-major device tensors; Grams are R x R float64.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libplanc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "planc.h")
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+ALGS = {"mu": 0, "hals": 1, "bpp": 2, "admm": 3, "pgd": 4}
+_DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+
+
+class PlancError(RuntimeError):
+    """A libplanc call returned a non-OK status."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libplanc status {status}: {msg}")
+        self.status = status
+
+
+class NlsOpts(C.Structure):
+    _fields_ = [("mu_eps", C.c_double), ("admm_max_inner", C.c_int),
+                ("admm_tol", C.c_double), ("bpp_max_iter", C.c_int),
+                ("pgd_steps", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("alg", C.c_int), ("iters", C.c_int), ("tol", C.c_double),
+                ("nls", NlsOpts), ("use_graph", C.c_int), ("profile", C.c_int)]
+
+
+class Report(C.Structure):
+    _fields_ = [("iters_done", C.c_int), ("rel_err", C.c_double), ("fit", C.c_double),
+                ("rel_err_hist", C.POINTER(C.c_double)),
+                ("inner_hist", C.POINTER(C.c_int32)),
+                ("bpp_unconverged", C.c_int), ("pm_ms", C.c_float),
+                ("pm_launches", C.c_int), ("launches", C.c_longlong),
+                ("pm_tensor_cores", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libplanc.so is not built ({LIB_PATH}); run "
+            "`python -m paper_1909_01149_gb300.build` (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    PP = C.POINTER(C.c_void_p)
+    sig = {
+        "planc_status_str": (C.c_char_p, [I]),
+        "planc_last_error": (C.c_char_p, [P]),
+        "planc_nls_opts_default": (NlsOpts, []),
+        "planc_solve_opts_default": (SolveOpts, []),
+        "planc_plan_split": (I, [I, C.POINTER(I64), C.POINTER(I)]),
+        "planc_init": (I, [C.POINTER(P), I, C.POINTER(I64), I, I, P, I, P, I]),
+        "planc_destroy": (I, [P]),
+        "planc_get_split": (I, [P]),
+        "planc_describe": (I, [I, C.POINTER(I64), I, C.c_char_p, C.c_size_t]),
+        "planc_sqnorm": (I, [P, P]),
+        "planc_mttkrp": (I, [P, PP, I, P]),
+        "planc_partial_mttkrp": (I, [P, PP, I, P]),
+        "planc_gram_hadamard": (I, [P, P, I, P]),
+        "planc_gram": (I, [P, I64, P, P]),
+        "planc_nls_update": (I, [P, I, C.POINTER(NlsOpts), I64, P, P, P, P, P]),
+        "planc_normalize": (I, [P, I64, P, P, P]),
+        "planc_fit": (I, [P, PP, P, C.POINTER(D), C.POINTER(D)]),
+        "planc_nncp_solve": (I, [P, C.POINTER(SolveOpts), PP, C.POINTER(D), C.POINTER(Report)]),
+        "planc_cp_grad": (I, [P, PP, PP, C.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def header_functions():
+    """Names of the functions include/planc.h declares."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*[\w\s\*]+?\b(planc_\w+)\s*\(", txt, re.M)))
+
+
+def plan_split(dims) -> int:
+    arr = (C.c_int64 * len(dims))(*dims)
+    out = C.c_int()
+    st = lib.planc_plan_split(len(dims), arr, C.byref(out))
+    if st != 0:
+        raise PlancError(st, lib.planc_last_error(None).decode())
+    return out.value
+
+
+def describe(dims, split: int = -1) -> str:
+    """The dimension-tree schedule (host-only, no GPU needed)."""
+    arr = (C.c_int64 * len(dims))(*dims)
+    buf = C.create_string_buffer(16384)
+    st = lib.planc_describe(len(dims), arr, int(split), buf, 16384)
+    if st != 0:
+        raise PlancError(st, lib.planc_last_error(None).decode())
+    return buf.value.decode()
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _ptrs(ts):
+    return (C.c_void_p * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def _check_mat(t, rows, cols, dtype, what):
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype and tuple(t.shape) == (rows, cols)):
+        raise ValueError(f"{what} must be a contiguous CUDA {dtype} tensor of shape "
+                         f"({rows}, {cols}), got {tuple(t.shape)} {t.dtype}")
+
+
+class Context:
+    """One planc_t: the tensor X (borrowed), its rank, split and workspace."""
+
+    def __init__(self, X: torch.Tensor, dims, R: int, split: int = -1, stream=None):
+        if not X.is_cuda or not X.is_contiguous():
+            raise ValueError("X must be a contiguous CUDA tensor (mode-1-fastest flat buffer)")
+        if X.dtype not in _DT:
+            raise ValueError(f"unsupported X dtype {X.dtype}")
+        n = 1
+        for d in dims:
+            n *= int(d)
+        if n != X.numel():
+            raise ValueError(f"X has {X.numel()} entries, dims {tuple(dims)} need {n}")
+        self.X = X  # keep the borrowed buffer alive
+        self.dims = tuple(int(d) for d in dims)
+        self.N = len(self.dims)
+        self.R = int(R)
+        self.fdtype = torch.float64 if X.dtype == torch.float64 else torch.float32
+        self.device = X.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+        arr = (C.c_int64 * self.N)(*self.dims)
+        h = C.c_void_p()
+        st = lib.planc_init(C.byref(h), self.N, arr, self.R, _DT[X.dtype], _ptr(X),
+                            _DT[self.fdtype], self.stream.cuda_stream, int(split))
+        if st != 0:
+            raise PlancError(st, lib.planc_last_error(None).decode())
+        self.h = h
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise PlancError(st, lib.planc_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.planc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def split(self) -> int:
+        return lib.planc_get_split(self.h)
+
+    def describe(self) -> str:
+        return describe(self.dims, self.split)
+
+    def _empty(self, rows, cols=None):
+        cols = self.R if cols is None else cols
+        return torch.empty((rows, cols), dtype=self.fdtype, device=self.device)
+
+    # -- steps of Alg. 1
+    def sqnorm(self) -> torch.Tensor:
+        out = torch.empty(1, dtype=torch.float64, device=self.device)
+        self._check(lib.planc_sqnorm(self.h, _ptr(out)))
+        return out
+
+    def _check_H(self, H, skip=None):
+        if len(H) != self.N:
+            raise ValueError(f"need {self.N} factors")
+        for k, h in enumerate(H):
+            if k != skip:
+                _check_mat(h, self.dims[k], self.R, self.fdtype, f"H[{k}]")
+
+    def mttkrp(self, H, n: int, M: torch.Tensor | None = None) -> torch.Tensor:
+        if 0 <= n < self.N:
+            self._check_H(H, skip=n)
+        M = self._empty(self.dims[n] if 0 <= n < self.N else 1) if M is None else M
+        self._check(lib.planc_mttkrp(self.h, _ptrs(H), int(n), _ptr(M)))
+        return M
+
+    def partial_mttkrp(self, H, side: int, T: torch.Tensor | None = None) -> torch.Tensor:
+        S = self.split
+        rows = 1
+        for d in (self.dims[:S] if side == 0 else self.dims[S:]):
+            rows *= d
+        self._check_H(H)
+        if T is None:
+            T = torch.empty(self.R * rows, dtype=self.fdtype, device=self.device)
+        self._check(lib.planc_partial_mttkrp(self.h, _ptrs(H), int(side), _ptr(T)))
+        return T
+
+    def gram_hadamard(self, G: torch.Tensor, n: int, S: torch.Tensor | None = None):
+        S = torch.empty((self.R, self.R), dtype=torch.float64, device=self.device) if S is None else S
+        self._check(lib.planc_gram_hadamard(self.h, _ptr(G), int(n), _ptr(S)))
+        return S
+
+    def gram(self, H: torch.Tensor, G: torch.Tensor | None = None) -> torch.Tensor:
+        G = torch.empty((self.R, self.R), dtype=torch.float64, device=self.device) if G is None else G
+        self._check(lib.planc_gram(self.h, H.shape[0], _ptr(H), _ptr(G)))
+        return G
+
+    def nls_update(self, alg: str, S, M, H, aux=None, opts: NlsOpts | None = None,
+                   inner: torch.Tensor | None = None):
+        o = lib.planc_nls_opts_default() if opts is None else opts
+        self._check(lib.planc_nls_update(
+            self.h, ALGS[alg], C.byref(o), H.shape[0], _ptr(S), _ptr(M), _ptr(H),
+            None if aux is None else _ptr(aux), None if inner is None else _ptr(inner)))
+        return H
+
+    def normalize(self, H, lam: torch.Tensor | None = None, G: torch.Tensor | None = None):
+        lam = torch.empty(self.R, dtype=torch.float64, device=self.device) if lam is None else lam
+        self._check(lib.planc_normalize(self.h, H.shape[0], _ptr(H), _ptr(lam),
+                                        None if G is None else _ptr(G)))
+        return H, lam
+
+    def fit(self, H, lam: torch.Tensor):
+        e = C.c_double()
+        f = C.c_double()
+        self._check(lib.planc_fit(self.h, _ptrs(H), _ptr(lam), C.byref(e), C.byref(f)))
+        return e.value, f.value
+
+    def solve(self, H, alg: str = "hals", iters: int = 10, tol: float = 0.0,
+              use_graph: bool = True, profile: bool = False, nls: NlsOpts | None = None):
+        o = lib.planc_solve_opts_default()
+        o.alg = ALGS[alg]
+        o.iters = int(iters)
+        o.tol = float(tol)
+        if nls is not None:
+            o.nls = nls
+        o.use_graph = 1 if use_graph else 0
+        o.profile = 1 if profile else 0
+        self._check_H(H)
+        lam = (C.c_double * self.R)()
+        hist = (C.c_double * max(1, iters))()
+        inner = (C.c_int32 * max(1, iters * self.N))()
+        rep = Report()
+        rep.rel_err_hist = C.cast(hist, C.POINTER(C.c_double))
+        rep.inner_hist = C.cast(inner, C.POINTER(C.c_int32))
+        self._check(lib.planc_nncp_solve(self.h, C.byref(o), _ptrs(H), lam, C.byref(rep)))
+        n = rep.iters_done
+        return dict(lam=list(lam), rel_err=list(hist[:n]), inner=list(inner[:n * self.N]),
+                    iters=n, fit=rep.fit, bpp_unconverged=rep.bpp_unconverged,
+                    pm_ms=rep.pm_ms, pm_launches=rep.pm_launches, launches=rep.launches,
+                    use_tc=rep.pm_tensor_cores != 0, tc_mask=rep.pm_tensor_cores)
+
+    def cp_grad(self, H, dH=None):
+        dH = [torch.empty_like(h) for h in H] if dH is None else dH
+        loss = C.c_double()
+        self._check(lib.planc_cp_grad(self.h, _ptrs(H), _ptrs(dH), C.byref(loss)))
+        return loss.value, dH

@@ -1,0 +1,90 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+function include/planc.h declares, and its host-only planning calls agree
+with the paper (Fig. DT) and with the oracle's statement of the split rule.
+"""
+
+import os
+import re
+
+import pytest
+
+import oracle as o
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+def _planc():
+    lib = os.path.join(ROOT, "paper_1909_01149_gb300", "lib", "libplanc.so")
+    if not os.path.exists(lib):
+        from paper_1909_01149_gb300 import build
+        build.build()
+    from paper_1909_01149_gb300 import planc
+    return planc
+
+
+def test_library_exports_every_declared_function():
+    planc = _planc()
+    names = planc.header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(planc.lib, name), f"libplanc.so does not export {name}"
+
+
+def test_header_declarations_are_extern_c_plain_types():
+    txt = open(os.path.join(ROOT, "include", "planc.h")).read()
+    assert 'extern "C"' in txt
+    for banned in ("torch", "at::Tensor", "std::"):
+        assert banned not in txt
+
+
+@pytest.mark.parametrize("dims", [(512, 512, 512), (64, 64, 64), (128, 128, 200, 100),
+                                  (96, 96, 96, 96), (10, 1000), (1000, 10), (2, 3, 4, 5, 6),
+                                  (1, 1, 7), (7, 1, 1), (384, 384, 384, 384), (3, 1000, 2, 2)])
+def test_plan_split_matches_oracle_rule(dims):
+    planc = _planc()
+    assert planc.plan_split(dims) == o.choose_split(dims)
+
+
+def test_plan_split_rejects_bad_shapes():
+    planc = _planc()
+    with pytest.raises(planc.PlancError):
+        planc.plan_split((5,))
+    with pytest.raises(planc.PlancError):
+        planc.plan_split((5, 0, 3))
+
+
+def _edges(text):
+    return sorted(l.strip() for l in text.splitlines()
+                  if l.startswith("PM") or l.startswith("mTTV"))
+
+
+def test_dimension_tree_matches_fig_dt():
+    planc = _planc()
+    gold = open(os.path.join(HERE, "golden", "fig_dt_n5.txt")).read()
+    N = int(re.search(r"^N (\d+)", gold, re.M).group(1))
+    S = int(re.search(r"^S (\d+)", gold, re.M).group(1))
+    got = planc.describe(tuple([8] * N), S)
+    assert _edges(got) == _edges(gold)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6])
+def test_dimension_tree_has_two_pms_and_every_leaf(N):
+    """Two partial MTTKRPs per outer iteration for any N (Sec. 6.2) and one
+    leaf per mode."""
+    planc = _planc()
+    for S in range(1, N):
+        text = planc.describe(tuple([4] * N), S)
+        e = _edges(text)
+        assert sum(1 for l in e if l.startswith("PM")) == 2
+        leaves = set()
+        for line in e:
+            dst = line.split("->")[1].strip()
+            if "," not in dst:
+                leaves.add(int(dst.strip("{}")))
+        # a branch with one mode is its own leaf (the PM output itself)
+        if S == 1:
+            leaves.add(1)
+        if N - S == 1:
+            leaves.add(N)
+        assert leaves == set(range(1, N + 1))
