@@ -318,16 +318,60 @@ def run_planc(args, cfg):
     return out, rank
 
 
+def run_pm_only(args, cfg):
+    """Time the two partial MTTKRPs alone (no solve): a profiling aid."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    torch.cuda.set_device(0)
+    X, H0 = make_inputs(cfg)
+    dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cfg["dtype"]]
+    fdt = torch.float64 if cfg["dtype"] == "f64" else torch.float32
+    Xd = torch.from_numpy(synth.flat(X)).to(dt).cuda()
+    H = [torch.from_numpy(h).to(fdt).cuda() for h in H0]
+    ctx = planc.Context(Xd, cfg["dims"], cfg["R"])
+    T = [ctx.partial_mttkrp(H, s) for s in (0, 1)]
+    for _ in range(args.warmup):
+        for s in (0, 1):
+            ctx.partial_mttkrp(H, s, T[s])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        for s in (0, 1):
+            ctx.partial_mttkrp(H, s, T[s])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (2 * args.steps)
+    xb = {"f32": 4, "f64": 8, "bf16": 2}[cfg["dtype"]]
+    nbytes = int(np.prod(cfg["dims"])) * xb
+    peak, kind = measured_peak()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    out = {"mode": "pm", "workload": cfg["workload"], "avg_launch_ms": ms,
+           "x_bytes_per_launch": nbytes, "GBps_x_only": round(gbs, 1),
+           "frac_of_" + kind: round(gbs / peak, 4), "tc_mask": ctx.tc_mask}
+    ctx.close()
+    return out, 0
+
+
 def run_mixed(args):
-    """BF16-storage vs FP32 on the 4-way mouse-like workload (BPP), equal
-    iterations: iter/s and final relative error of each."""
+    """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP), equal
+    iterations from the same initial factors.  'fp32_same_values' stores the
+    BF16-rounded tensor in FP32, so it solves the identical problem with FP32
+    streaming: the comparison at equal fit.  'fp32' solves the unrounded
+    tensor; 'bf16_err_vs_unrounded' is the BF16 solution's relative error
+    measured against the unrounded tensor."""
     import torch
     from paper_1909_01149_gb300 import planc, synth
     cfg = CONFIGS["c3"]
     X, H0 = make_inputs(cfg)
+    flat = synth.flat(X)
+    Xb = torch.from_numpy(flat).to(torch.bfloat16).cuda()
+    arms = (("bf16", Xb), ("fp32_same_values", Xb.float()),
+            ("fp32", torch.from_numpy(flat).cuda()))
     out = {"workload": cfg["workload"], "alg": cfg["alg"], "iters": cfg["iters"]}
-    for name, dt in (("bf16", torch.bfloat16), ("fp32", torch.float32)):
-        Xd = torch.from_numpy(synth.flat(X)).to(dt).cuda()
+    Hbf = None
+    for name, Xd in arms:
         H0d = [torch.from_numpy(h).cuda() for h in H0]
         H = [h.clone() for h in H0d]
         with planc.Context(Xd, cfg["dims"], cfg["R"]) as ctx:
@@ -347,12 +391,19 @@ def run_mixed(args):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-        out[name] = {"iter_s": round(n * cfg["iters"] / (ms / 1e3), 2),
-                     "rel_err": r["rel_err"][-1]}
-        del Xd
-        torch.cuda.empty_cache()
-    out["rel_err_diff"] = abs(out["bf16"]["rel_err"] - out["fp32"]["rel_err"])
-    out["speedup_bf16_over_fp32"] = round(out["bf16"]["iter_s"] / out["fp32"]["iter_s"], 3)
+            out[name] = {"iter_s": round(n * cfg["iters"] / (ms / 1e3), 2),
+                         "rel_err": r["rel_err"][-1], "tc_mask": ctx.tc_mask}
+            if name == "bf16":
+                Hbf = ([h.clone() for h in H], torch.tensor(r["lam"], dtype=torch.float64,
+                                                              device="cuda"))
+            if name == "fp32" and Hbf is not None:
+                out["bf16_err_vs_unrounded"] = ctx.fit(Hbf[0], Hbf[1])[0]
+    out["rel_err_diff_same_values"] = abs(out["bf16"]["rel_err"] -
+                                          out["fp32_same_values"]["rel_err"])
+    out["speedup_bf16_over_fp32"] = round(out["bf16"]["iter_s"] /
+                                          out["fp32_same_values"]["iter_s"], 3)
+    del Xb, arms
+    torch.cuda.empty_cache()
     return out
 
 
@@ -415,12 +466,30 @@ def main():
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "pm"],
+                    help="pm: time only the two partial MTTKRPs (profiling aid)")
+    ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
+    ap.add_argument("--rank", type=int, default=None, help="override R")
+    ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3
-    cfg = CONFIGS[args.config]
-    if args.impl == "reference":
+    cfg = dict(CONFIGS[args.config])
+    if args.dims or args.rank or args.dtype:
+        if args.dims:
+            cfg["dims"] = tuple(int(v) for v in args.dims.split(","))
+        if args.rank:
+            cfg["R"] = args.rank
+        if args.dtype:
+            cfg["dtype"] = args.dtype
+        cfg["kind"] = "planted"
+        cfg["noise"] = cfg.get("noise") or 0.05
+        cfg["workload"] = "nncp-dense-%s-%s-R%d" % ("x".join(map(str, cfg["dims"])),
+                                                     cfg["dtype"], cfg["R"])
+    if args.mode == "pm":
+        out, rank = run_pm_only(args, cfg)
+    elif args.impl == "reference":
         out, rank = run_reference(args, cfg)
     else:
         out, rank = run_planc(args, cfg)

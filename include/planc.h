@@ -131,6 +131,10 @@ planc_status_t planc_plan_split(int N, const int64_t* dims, int* split);
  *   f_dtype      factor dtype: F64 iff x_dtype is F64, else F32
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  *   split        root split S, 1-based; -1 chooses planc_plan_split's S
+ * The partial MTTKRPs run on the tcgen05 tensor cores when the shape allows
+ * (BF16 X, R <= 64, prod_{k<S} I_k a multiple of 8, X 16-byte aligned) and
+ * on the CUDA-core kernels otherwise; the environment variable
+ * PLANC_PM_PATH=simt, read here, forces the CUDA-core kernels.
  * Allocates the workspace (dimension-tree temporaries, split-K partials,
  * reduction scratch).  Errors: PLANC_E_SHAPE, PLANC_E_DTYPE, PLANC_E_INVALID,
  * PLANC_E_NOMEM, PLANC_E_CUDA (no device / not sm_103). */
@@ -143,6 +147,10 @@ planc_status_t planc_destroy(planc_t ctx);
 
 /* The split S (1-based) the context uses. */
 int planc_get_split(planc_t ctx);
+
+/* Which partial MTTKRPs run on the tcgen05 tensor cores: bit 0 the left
+ * branch T^{1:S}, bit 1 the right branch T^{S+1:N} (0 = CUDA cores). */
+int planc_pm_tensor_cores(planc_t ctx);
 
 /* Text of the dimension tree used for dims[0..N-1] with root split `split`
  * (1-based; -1 = planc_plan_split's choice): the root line, then one line per

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -273,9 +274,14 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   // ---- workspace sizes
   const size_t fs = fsize(ctx);
   size_t part_elems = 0;
+  // PLANC_PM_PATH=simt keeps the partial MTTKRPs on the CUDA-core kernels
+  // (for A/B comparisons); by default eligible shapes use the tensor cores.
+  const char* path = getenv("PLANC_PM_PATH");
+  const bool allow_tc = !(path && strcmp(path, "simt") == 0);
   for (int s = 0; s < 2; ++s) {
     const bool left = s == 0;
-    ctx->use_tc[s] = pm_tc_eligible(x_dtype, left, ctx->L, ctx->C, R);
+    ctx->use_tc[s] = allow_tc && ((uintptr_t)X & 15) == 0 &&
+                     pm_tc_eligible(x_dtype, left, ctx->L, ctx->C, R);
     if (!ctx->use_tc[s]) {
       ctx->nsplit[s] = pm_simt_nsplit(left, ctx->L, ctx->C, R, ctx->sm_count);
       if (ctx->nsplit[s] > 1)
@@ -369,6 +375,10 @@ planc_status_t planc_destroy(planc_t ctx) {
 }
 
 int planc_get_split(planc_t ctx) { return ctx ? ctx->S : -1; }
+
+int planc_pm_tensor_cores(planc_t ctx) {
+  return ctx ? (ctx->use_tc[0] ? 1 : 0) | (ctx->use_tc[1] ? 2 : 0) : 0;
+}
 
 planc_status_t planc_describe(int N, const int64_t* dims, int split, char* buf, size_t len) {
   if (!buf || len == 0) return fail(nullptr, PLANC_E_INVALID, "buf is NULL");
@@ -687,7 +697,10 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
     CK(cudaMemcpyAsync(inner.data(), ctx->inner, (size_t)N * done * 4, cudaMemcpyDeviceToHost,
                        ctx->stream), "D2H");
   }
+  int tc_err = 0;
   CK(cudaMemcpyAsync(flags, ctx->flags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  CK(cudaMemcpyAsync(&tc_err, ctx->tc_err, sizeof tc_err, cudaMemcpyDeviceToHost, ctx->stream),
+     "D2H");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   if (report) {
     report->iters_done = done;
@@ -710,6 +723,8 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
       }
     }
   }
+  if (tc_err != 0)
+    return fail(ctx, PLANC_E_TIMEOUT, "a tensor-core pipeline wait gave up (code %d)", tc_err);
   if (flags[1] != 0) return fail(ctx, PLANC_E_NUMERIC, "BPP met a non-positive pivot in %d rows", flags[1]);
   return PLANC_OK;
 }

@@ -71,6 +71,7 @@ def _load():
         "planc_init": (I, [C.POINTER(P), I, C.POINTER(I64), I, I, P, I, P, I]),
         "planc_destroy": (I, [P]),
         "planc_get_split": (I, [P]),
+        "planc_pm_tensor_cores": (I, [P]),
         "planc_describe": (I, [I, C.POINTER(I64), I, C.c_char_p, C.c_size_t]),
         "planc_sqnorm": (I, [P, P]),
         "planc_mttkrp": (I, [P, PP, I, P]),
@@ -189,6 +190,11 @@ class Context:
 
     def describe(self) -> str:
         return describe(self.dims, self.split)
+
+    @property
+    def tc_mask(self) -> int:
+        """bit 0 / bit 1: left / right partial MTTKRP on the tensor cores."""
+        return lib.planc_pm_tensor_cores(self.h)
 
     def _empty(self, rows, cols=None):
         cols = self.R if cols is None else cols
