@@ -45,9 +45,10 @@ cudaError_t launch_pm_simt(planc_dtype_t xdt, const void* X, int64_t L, int64_t 
 // tcgen05 path (FP32 X as 3xTF32, BF16/F16 X as kind::f16 with a two-term
 // BF16 split of the Khatri-Rao operand).  Returns cudaErrorNotSupported when
 // the shape/rank/dtype is not eligible; the caller then uses the SIMT path.
-bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R);
+bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
+                    const KrpHost& krp_dims);
 size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
-                             int sm_count);
+                             const KrpHost& krp_dims, int sm_count);
 cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
                          bool left, const KrpHost& krp, int R, void* out,
                          bool out_rowmajor, void* work, size_t work_bytes,

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.h"
@@ -42,7 +43,6 @@ constexpr int NTHREADS = 320;
 constexpr int W_TMA = 0, W_MMA = 1, W_B0 = 2, W_EPI0 = 6;
 constexpr int A_STAGE_BYTES = BM * BK * 2;   // 16 KB
 constexpr uint32_t TMEM_COLS = 512;          // two accumulators at columns 0 and 256
-constexpr int MAX_K_STAGES_PER_ITEM = 64;    // right side: bound the accumulation chain
 
 struct TcParams {
   int64_t L, C;        // X_(1:S) is L x C, column-major
@@ -55,6 +55,7 @@ struct TcParams {
   int out_mode;        // 0: out[m + Mdim r]; 1: out[m R + r]; 2: out[z Mdim R + m + Mdim r]
   float* out;
   int* err;
+  int h0_smem;         // 1: the first Khatri-Rao factor is staged in shared memory
   Krp<float> K;
 };
 
@@ -72,6 +73,95 @@ __device__ __forceinline__ Item decode_item(const TcParams& p, int64_t it) {
   r.k0 = r.z * p.kspan;
   r.k1 = min(p.Kdim, r.k0 + p.kspan);
   return r;
+}
+
+
+// Modes a tensor-core Khatri-Rao operand may combine (loops over modes are
+// unrolled to this bound so the per-mode indices stay in registers).
+constexpr int TC_MAXM = 6;
+// Stages accumulated into one TMEM accumulator before the epilogue drains it
+// into FP32 registers: the tensor core's FP32 accumulation is not
+// round-to-nearest, and long chains of accumulations drift low (about 2^-25
+// relative per accumulation); draining every 8 stages bounds the drift.
+constexpr int SEG_STAGES = 8;
+
+// Row k of the Khatri-Rao operand as per-mode row indices (mode 0 fastest).
+__device__ __forceinline__ void kw_set(const TcParams& p, int64_t k64, int* idx) {
+  uint32_t k = (uint32_t)k64;
+#pragma unroll
+  for (int m = 0; m < TC_MAXM; ++m) {
+    if (m < p.K.nm) {
+      const uint32_t d = (uint32_t)p.K.dim[m];
+      const uint32_t q = k / d;
+      idx[m] = (int)(k - q * d);
+      k = q;
+    } else {
+      idx[m] = 0;
+    }
+  }
+}
+
+// Product of the factor rows of modes 1.. (all but the fastest mode) for
+// columns r = lane and lane + 32: it changes only when the fastest index wraps.
+__device__ __forceinline__ void kw_tail(const TcParams& p, const int* idx, int lane, float* P) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = lane + 32 * h;
+    float v = 1.f;
+    if (r < p.R) {
+#pragma unroll
+      for (int m = 1; m < TC_MAXM; ++m)
+        if (m < p.K.nm) v *= __ldg(p.K.H[m] + (int64_t)idx[m] * p.K.R + r);
+    }
+    P[h] = v;
+  }
+}
+// next row: step the fastest index; on a wrap carry into the higher modes
+// and recompute the tail product
+__device__ __forceinline__ void kw_next(const TcParams& p, int* idx, int lane, float* P) {
+  if (++idx[0] < (int)p.K.dim[0]) return;
+  idx[0] = 0;
+  bool carry = true;
+#pragma unroll
+  for (int m = 1; m < TC_MAXM; ++m) {
+    if (carry && m < p.K.nm) {
+      if (++idx[m] < (int)p.K.dim[m]) carry = false;
+      else idx[m] = 0;
+    }
+  }
+  kw_tail(p, idx, lane, P);
+}
+
+
+
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Values of Khatri-Rao rows kk and kk + 1 (the cursor idx/P points at kk and
+// is advanced past kk + 1) for columns r = lane and lane + 32.  SH: the first
+// factor is read from its shared-memory copy at h0_s, else from global h0_g.
+template <bool SH>
+__device__ __forceinline__ void kw_pair(const TcParams& p, uint32_t h0_s, const float* h0_g,
+                                        int* idx, float* P, int lane, int kk, int64_t nvalid,
+                                        float v[2][2]) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const bool kv = kk + t < nvalid;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      float x = 0.f;
+      if (kv && r < p.R) {
+        const int e = idx[0] * p.R + r;
+        x = (SH ? lds_f32(h0_s + 4u * (uint32_t)e) : __ldg(h0_g + e)) * P[h];
+      }
+      v[t][h] = x;
+    }
+    kw_next(p, idx, lane, P);
+  }
 }
 
 // byte offset of element (row n, k) in a K-major 128-byte-swizzled operand
@@ -100,6 +190,7 @@ pm_tc_bf16_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sH0 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(drain) + 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -167,38 +258,41 @@ pm_tc_bf16_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       const uint32_t idesc = instr_desc(1u, LEFT, false, BM, p.N);
       int s = 0;
       uint32_t ph = 0;
-      uint32_t eph[2] = {0, 0};
+      uint32_t eph = 0;  // bit b: phase of acc_empty[b]
       int buf = 0;
       bool ok = true;
       bool issued = false;
       for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
         const Item w = decode_item<LEFT>(p, it);
-        if (!mbar_wait(&acc_empty[buf], eph[buf] ^ 1, abort, p.err, 2)) { ok = false; break; }
-        eph[buf] ^= 1;
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)buf * 256u;
-        uint32_t acc = 0;
-        for (int64_t k = w.k0; k < w.k1; k += BK) {
-          if (!mbar_wait(&full_a[s], ph, abort, p.err, 3)) { ok = false; break; }
-          if (!mbar_wait(&full_b[s], ph, abort, p.err, 4)) { ok = false; break; }
+        for (int64_t k = w.k0; k < w.k1 && ok; ) {
+          // one accumulation segment of at most SEG_STAGES stages
+          if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 2)) { ok = false; break; }
+          eph ^= 1u << buf;
           tc_fence_after();
-          const uint32_t a0 = smem_u32(A + (size_t)s * A_STAGE_BYTES);
-          const uint32_t b0 = smem_u32(B + (size_t)s * b_stage_bytes);
+          const uint32_t d = tmem + (uint32_t)buf * 256u;
+          uint32_t acc = 0;
+          for (int st = 0; st < SEG_STAGES && k < w.k1; ++st, k += BK) {
+            if (!mbar_wait(&full_a[s], ph, abort, p.err, 3)) { ok = false; break; }
+            if (!mbar_wait(&full_b[s], ph, abort, p.err, 4)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(A + (size_t)s * A_STAGE_BYTES);
+            const uint32_t b0 = smem_u32(B + (size_t)s * b_stage_bytes);
 #pragma unroll
-          for (int kk = 0; kk < BK / UK; ++kk) {
-            const uint64_t ad = LEFT ? smem_desc(a0 + kk * 2048, A_STAGE_BYTES / 2, 1024, kLayoutSW128)
-                                     : smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
-            const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
-            mma_f16_ss(d, ad, bd, idesc, acc);
-            acc = 1;
+            for (int kk = 0; kk < BK / UK; ++kk) {
+              const uint64_t ad = LEFT ? smem_desc(a0 + kk * 2048, A_STAGE_BYTES / 2, 1024, kLayoutSW128)
+                                       : smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
+              const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+              mma_f16_ss(d, ad, bd, idesc, acc);
+              acc = 1;
+            }
+            issued = true;
+            mma_commit(&empty[s]);
+            if (++s == stages) { s = 0; ph ^= 1; }
           }
-          issued = true;
-          mma_commit(&empty[s]);
-          if (++s == stages) { s = 0; ph ^= 1; }
+          if (!ok) break;
+          mma_commit(&acc_full[buf]);
+          buf ^= 1;
         }
-        if (!ok) break;
-        mma_commit(&acc_full[buf]);
-        buf ^= 1;
       }
       if (issued) {
         // every MMA of this thread has finished once this arrives
@@ -210,11 +304,20 @@ pm_tc_bf16_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
     }
   } else if (warp < W_EPI0) {
     // ---------------------------------------------------------------- KRP producers
-    const int t = threadIdx.x - W_B0 * 32;  // 0..127
-    const int kk = t & 63;
-    const int half = t >> 6;
+    // The first Khatri-Rao factor is staged in shared memory once; warp wi
+    // then builds rows [16 wi, 16 wi + 16) of every stage, two rows at a
+    // time (lane = column r), so each of the three terms of a row pair is one
+    // 32-bit store into the swizzled tile.
+    const int wi = warp - W_B0;
     const int RB = p.RB;
-    const int r_lo = half * (RB / 2), r_hi = r_lo + RB / 2;
+    const bool h0_shared = p.h0_smem != 0;
+    const uint32_t h0_s = smem_u32(sH0);
+    if (h0_shared) {
+      const int64_t n0 = p.K.dim[0] * (int64_t)p.R;
+      for (int64_t e = threadIdx.x - W_B0 * 32; e < n0; e += 128) sH0[e] = __ldg(p.K.H[0] + e);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    constexpr int ROWS = BK / 4;
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
@@ -223,20 +326,37 @@ pm_tc_bf16_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       for (int64_t k = w.k0; k < w.k1; k += BK) {
         if (!mbar_wait(&empty[s], ph ^ 1, abort, p.err, 5)) { ok = false; break; }
         uint8_t* b = B + (size_t)s * b_stage_bytes;
-        const int64_t kg = k + kk;
-        const bool valid = kg < w.k1;
-        int64_t off[PLANC_MAX_N];
-        if (valid) krp_decode(p.K, kg, off);
-        for (int r = r_lo; r < r_hi; ++r) {
-          float v = (valid && r < p.R) ? krp_value(p.K, off, r) : 0.f;
-          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-          const float r1 = v - __bfloat162float(hi);
-          const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-          const float r2 = r1 - __bfloat162float(mid);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
-          *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(r, kk)) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(RB + r, kk)) = mid;
-          *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(2 * RB + r, kk)) = lo;
+        const int kb = wi * ROWS;
+        int idx[TC_MAXM];
+        float P[2];
+        kw_set(p, k + kb, idx);
+        kw_tail(p, idx, lane, P);
+        const int64_t nvalid = w.k1 - k;
+#pragma unroll 4
+        for (int kk = kb; kk < kb + ROWS; kk += 2) {
+          float v[2][2];
+          if (h0_shared) kw_pair<true>(p, h0_s, p.K.H[0], idx, P, lane, kk, nvalid, v);
+          else kw_pair<false>(p, h0_s, p.K.H[0], idx, P, lane, kk, nvalid, v);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            if (r < RB) {
+              const __nv_bfloat162 hi = __floats2bfloat162_rn(v[0][h], v[1][h]);
+              const float2 h2 = __bfloat1622float2(hi);
+              const float a0 = v[0][h] - h2.x, a1 = v[1][h] - h2.y;
+              const __nv_bfloat162 mid = __floats2bfloat162_rn(a0, a1);
+              const float2 m2 = __bfloat1622float2(mid);
+              const __nv_bfloat162 lo = __floats2bfloat162_rn(a0 - m2.x, a1 - m2.y);
+              // rows r, RB + r, 2 RB + r share (row & 7) since RB % 8 == 0
+              const uint32_t in_row = ((((uint32_t)kk >> 3) ^ ((uint32_t)r & 7u)) << 4) +
+                                      (((uint32_t)kk & 7u) << 1);
+              const uint32_t r0 = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
+              const uint32_t rstride = (uint32_t)RB * 128u;  // RB rows further down
+              *reinterpret_cast<__nv_bfloat162*>(b + r0 + in_row) = hi;
+              *reinterpret_cast<__nv_bfloat162*>(b + r0 + rstride + in_row) = mid;
+              *reinterpret_cast<__nv_bfloat162*>(b + r0 + 2 * rstride + in_row) = lo;
+            }
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -248,39 +368,48 @@ pm_tc_bf16_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
-    uint32_t fph[2] = {0, 0};
+    uint32_t fph = 0;  // bit b: phase of acc_full[b]
     int buf = 0;
-    for (int64_t it = blockIdx.x; it < p.items; it += gridDim.x) {
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
       const Item w = decode_item<LEFT>(p, it);
-      if (!mbar_wait(&acc_full[buf], fph[buf], abort, p.err, 6)) break;
-      fph[buf] ^= 1;
-      tc_fence_after();
-      const uint32_t taddr = tmem + (uint32_t)buf * 256u + ((uint32_t)(q * 32) << 16);
-      const int64_t m = w.m0 + row;
-      const bool live = m < p.Mdim;
-      for (int r0 = 0; r0 < p.RB; r0 += 16) {
-        float h[16], md[16], lo[16];
-        tmem_ld16(taddr + r0, h);
-        tmem_ld16(taddr + p.RB + r0, md);
-        tmem_ld16(taddr + 2 * p.RB + r0, lo);
-        tmem_ld_wait();
-        if (live) {
+      float sum[64];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int r = r0 + j;
-            if (r < p.R) {
-              const float v = h[j] + (md[j] + lo[j]);
-              if (p.out_mode == 0) p.out[m + p.Mdim * r] = v;
-              else if (p.out_mode == 1) p.out[m * p.R + r] = v;
-              else p.out[w.z * p.Mdim * p.R + m + p.Mdim * r] = v;
-            }
+      for (int j = 0; j < 64; ++j) sum[j] = 0.f;
+      for (int64_t k = w.k0; k < w.k1; k += (int64_t)SEG_STAGES * BK) {
+        if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 6)) { ok = false; break; }
+        fph ^= 1u << buf;
+        tc_fence_after();
+        const uint32_t taddr = tmem + (uint32_t)buf * 256u + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c * 16 < p.RB) {
+            float h[16], md[16], lo[16];
+            tmem_ld16(taddr + c * 16, h);
+            tmem_ld16(taddr + p.RB + c * 16, md);
+            tmem_ld16(taddr + 2 * p.RB + c * 16, lo);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum[c * 16 + j] += h[j] + (md[j] + lo[j]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        buf ^= 1;
+      }
+      if (!ok) break;
+      const int64_t m = w.m0 + row;
+      if (m < p.Mdim) {
+#pragma unroll
+        for (int r = 0; r < 64; ++r) {
+          if (r < p.R) {
+            if (p.out_mode == 0) p.out[m + p.Mdim * r] = sum[r];
+            else if (p.out_mode == 1) p.out[m * p.R + r] = sum[r];
+            else p.out[w.z * p.Mdim * p.R + m + p.Mdim * r] = sum[r];
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
-      buf ^= 1;
     }
   }
 
@@ -346,6 +475,7 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sH0 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(drain) + 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -413,38 +543,40 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       const uint32_t id_half = instr_desc(2u, false, false, BM, RB);
       int s = 0, as = 0;
       uint32_t ph = 0, aph = 0;
-      uint32_t eph[2] = {0, 0};
+      uint32_t eph = 0;  // bit b: phase of acc_empty[b]
       int buf = 0;
       bool ok = true, issued = false;
       for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
         const Item w = decode_item<LEFT>(p, it);
-        if (!mbar_wait(&acc_empty[buf], eph[buf] ^ 1, abort, p.err, 12)) { ok = false; break; }
-        eph[buf] ^= 1;
-        tc_fence_after();
-        const uint32_t d = tmem + d_col0 + (uint32_t)buf * (uint32_t)(2 * RB);
-        uint32_t acc = 0;
-        for (int64_t k = w.k0; k < w.k1; k += F_BK) {
-          if (!mbar_wait(&full_b[s], ph, abort, p.err, 13)) { ok = false; break; }
-          if (!mbar_wait(&a_full[as], aph, abort, p.err, 14)) { ok = false; break; }
+        for (int64_t k = w.k0; k < w.k1 && ok; ) {
+          if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 12)) { ok = false; break; }
+          eph ^= 1u << buf;
           tc_fence_after();
-          const uint32_t b0 = smem_u32(B + (size_t)s * b_stage_bytes);
-          const uint32_t a_hi = tmem + (uint32_t)as * 64u;
+          const uint32_t d = tmem + d_col0 + (uint32_t)buf * (uint32_t)(2 * RB);
+          uint32_t acc = 0;
+          for (int st = 0; st < SEG_STAGES && k < w.k1; ++st, k += F_BK) {
+            if (!mbar_wait(&full_b[s], ph, abort, p.err, 13)) { ok = false; break; }
+            if (!mbar_wait(&a_full[as], aph, abort, p.err, 14)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t b0 = smem_u32(B + (size_t)s * b_stage_bytes);
+            const uint32_t a_hi = tmem + (uint32_t)as * 64u;
 #pragma unroll
-          for (int kk = 0; kk < F_BK / F_UK; ++kk) {
-            const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
-            mma_tf32_ts(d, a_hi + kk * F_UK, bd, id_full, acc);
-            mma_tf32_ts(d + RB, a_hi + 32 + kk * F_UK, bd, id_half, 1u);
-            acc = 1;
+            for (int kk = 0; kk < F_BK / F_UK; ++kk) {
+              const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+              mma_tf32_ts(d, a_hi + kk * F_UK, bd, id_full, acc);
+              mma_tf32_ts(d + RB, a_hi + 32 + kk * F_UK, bd, id_half, 1u);
+              acc = 1;
+            }
+            issued = true;
+            mma_commit(&b_empty[s]);
+            mma_commit(&a_empty[as]);
+            if (++s == stages) { s = 0; ph ^= 1; }
+            if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
           }
-          issued = true;
-          mma_commit(&b_empty[s]);
-          mma_commit(&a_empty[as]);
-          if (++s == stages) { s = 0; ph ^= 1; }
-          if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
+          if (!ok) break;
+          mma_commit(&acc_full[buf]);
+          buf ^= 1;
         }
-        if (!ok) break;
-        mma_commit(&acc_full[buf]);
-        buf ^= 1;
       }
       if (issued) {
         mma_commit(drain);
@@ -454,11 +586,18 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       }
     }
   } else if (warp < F_W_CONV0) {
-    // Khatri-Rao producers: B = [k_hi | k_lo], 2 R' rows x 32 k, tf32
-    const int t = threadIdx.x - W_B0 * 32;  // 0..127
-    const int kk = t & 31;
-    const int quarter = t >> 5;             // 4 groups of R'/4 columns
-    const int r_lo = quarter * (RB / 4), r_hi = r_lo + RB / 4;
+    // Khatri-Rao producers: B = [k_hi | k_lo], 2 R' rows x 32 k, tf32.  The
+    // first factor is staged in shared memory; warp wi builds rows
+    // [8 wi, 8 wi + 8) of each stage in pairs (lane = column r).
+    const int wi = warp - W_B0;
+    const bool h0_shared = p.h0_smem != 0;
+    const uint32_t h0_s = smem_u32(sH0);
+    if (h0_shared) {
+      const int64_t n0 = p.K.dim[0] * (int64_t)p.R;
+      for (int64_t e = threadIdx.x - W_B0 * 32; e < n0; e += 128) sH0[e] = __ldg(p.K.H[0] + e);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    constexpr int ROWS = F_BK / 4;
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
@@ -467,16 +606,30 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       for (int64_t k = w.k0; k < w.k1; k += F_BK) {
         if (!mbar_wait(&b_empty[s], ph ^ 1, abort, p.err, 15)) { ok = false; break; }
         uint8_t* b = B + (size_t)s * b_stage_bytes;
-        const int64_t kg = k + kk;
-        const bool valid = kg < w.k1;
-        int64_t off[PLANC_MAX_N];
-        if (valid) krp_decode(p.K, kg, off);
-        for (int r = r_lo; r < r_hi; ++r) {
-          const float v = (valid && r < p.R) ? krp_value(p.K, off, r) : 0.f;
-          const float hi = tf32_rn(v);
-          const float lo = tf32_rn(v - hi);
-          *reinterpret_cast<float*>(b + sw128_off32(r, kk)) = hi;
-          *reinterpret_cast<float*>(b + sw128_off32(RB + r, kk)) = lo;
+        const int kb = wi * ROWS;
+        int idx[TC_MAXM];
+        float P[2];
+        kw_set(p, k + kb, idx);
+        kw_tail(p, idx, lane, P);
+        const int64_t nvalid = w.k1 - k;
+#pragma unroll
+        for (int kk = kb; kk < kb + ROWS; kk += 2) {
+          float v[2][2];
+          if (h0_shared) kw_pair<true>(p, h0_s, p.K.H[0], idx, P, lane, kk, nvalid, v);
+          else kw_pair<false>(p, h0_s, p.K.H[0], idx, P, lane, kk, nvalid, v);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            if (r < RB) {
+              const float h0v = tf32_rn(v[0][h]), h1v = tf32_rn(v[1][h]);
+              const uint32_t in_row = ((((uint32_t)kk >> 2) ^ ((uint32_t)r & 7u)) << 4) +
+                                      (((uint32_t)kk & 3u) << 2);
+              const uint32_t r0 = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
+              *reinterpret_cast<float2*>(b + r0 + in_row) = make_float2(h0v, h1v);
+              *reinterpret_cast<float2*>(b + r0 + (uint32_t)RB * 128u + in_row) =
+                  make_float2(tf32_rn(v[0][h] - h0v), tf32_rn(v[1][h] - h1v));
+            }
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -497,20 +650,22 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       for (int64_t k = w.k0; k < w.k1; k += F_BK) {
         if (!mbar_wait(&full_x[s], ph, abort, p.err, 16)) { ok = false; break; }
         if (!mbar_wait(&a_empty[as], aph ^ 1, abort, p.err, 17)) { ok = false; break; }
-        const uint8_t* x = Xs + (size_t)s * F_X_STAGE_BYTES;
+        const uint32_t x = smem_u32(Xs + (size_t)s * F_X_STAGE_BYTES);
         float v[F_BK];
         if (LEFT) {
           // tile stored [k][128 rows], 512 B per k (no swizzle)
 #pragma unroll
-          for (int c = 0; c < F_BK; ++c)
-            v[c] = *reinterpret_cast<const float*>(x + c * 512 + row * 4);
+          for (int c = 0; c < F_BK; ++c) v[c] = lds_f32(x + c * 512 + row * 4);
         } else {
           // tile stored [128 rows][32 k], 128-byte swizzled
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const float4 f = *reinterpret_cast<const float4*>(
-                x + row * 128 + (((j ^ (row & 7)) & 7) << 4));
-            v[4 * j + 0] = f.x; v[4 * j + 1] = f.y; v[4 * j + 2] = f.z; v[4 * j + 3] = f.w;
+            const uint32_t a = x + row * 128 + (((j ^ (row & 7)) & 7) << 4);
+            asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                         : "=f"(v[4 * j + 0]), "=f"(v[4 * j + 1]), "=f"(v[4 * j + 2]),
+                           "=f"(v[4 * j + 3])
+                         : "r"(a)
+                         : "memory");
           }
         }
         __syncwarp();
@@ -537,42 +692,507 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
       }
     }
   } else {
-    // epilogue
+    // epilogue: drain each accumulation segment into FP32 registers
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    uint32_t fph[2] = {0, 0};
+    uint32_t fph = 0;  // bit b: phase of acc_full[b]
     int buf = 0;
-    for (int64_t it = blockIdx.x; it < p.items; it += gridDim.x) {
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
       const Item w = decode_item<LEFT>(p, it);
-      if (!mbar_wait(&acc_full[buf], fph[buf], abort, p.err, 18)) break;
-      fph[buf] ^= 1;
-      tc_fence_after();
-      const uint32_t taddr =
-          tmem + d_col0 + (uint32_t)buf * (uint32_t)(2 * RB) + ((uint32_t)(q * 32) << 16);
-      const int64_t m = w.m0 + row;
-      const bool live = m < p.Mdim;
-      for (int r0 = 0; r0 < RB; r0 += 16) {
-        float h[16], c[16];
-        tmem_ld16(taddr + r0, h);
-        tmem_ld16(taddr + RB + r0, c);
-        tmem_ld_wait();
-        if (live) {
+      float sum[64];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int r = r0 + j;
-            if (r < p.R) {
-              const float v = h[j] + c[j];
-              if (p.out_mode == 0) p.out[m + p.Mdim * r] = v;
-              else if (p.out_mode == 1) p.out[m * p.R + r] = v;
-              else p.out[w.z * p.Mdim * p.R + m + p.Mdim * r] = v;
+      for (int j = 0; j < 64; ++j) sum[j] = 0.f;
+      for (int64_t k = w.k0; k < w.k1; k += (int64_t)SEG_STAGES * F_BK) {
+        if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 18)) { ok = false; break; }
+        fph ^= 1u << buf;
+        tc_fence_after();
+        const uint32_t taddr =
+            tmem + d_col0 + (uint32_t)buf * (uint32_t)(2 * RB) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c * 16 < RB) {
+            float h[16], cr[16];
+            tmem_ld16(taddr + c * 16, h);
+            tmem_ld16(taddr + RB + c * 16, cr);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum[c * 16 + j] += h[j] + cr[j];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        buf ^= 1;
+      }
+      if (!ok) break;
+      const int64_t m = w.m0 + row;
+      if (m < p.Mdim) {
+#pragma unroll
+        for (int r = 0; r < 64; ++r) {
+          if (r < p.R) {
+            if (p.out_mode == 0) p.out[m + p.Mdim * r] = sum[r];
+            else if (p.out_mode == 1) p.out[m * p.R + r] = sum[r];
+            else p.out[w.z * p.Mdim * p.R + m + p.Mdim * r] = sum[r];
+          }
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == W_MMA) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ---- resident Khatri-Rao operand ------------------------------------------------------
+//
+// The Khatri-Rao operand factors row-wise as K[k, r] = H_in[k_in, r] * W[k_out, r]:
+// one factor ("inner", the fastest mode of the operand) times the product of
+// the others.  Here the split and swizzled H_in is built once per CTA and
+// stays resident in shared memory as the MMA's B operand, so the pipeline
+// carries only X; the outer weights W are applied when the epilogue drains
+// the TMEM accumulators:
+//
+//   left : T(l, r)    = sum_{o} W[o, r] * sum_{c} X[l, c, o] H_in[c, r]
+//          (X_(1:S) seen as L x d_in x n_out; one drain per outer index o)
+//   right: T(c, r)    = sum_{j} W[j, r] * sum_{l} X[l, j, c] H_in[l, r]
+//          (rows (j, c) of X seen as d_in x (L/d_in * C); the epilogue
+//          weights every row by W[j] and sums the 128 rows of a tile, which
+//          all belong to one c because L/d_in is a multiple of 128)
+//
+// FP32 X keeps the TMEM-resident 3xTF32 split of the converters; BF16 X is
+// read by the MMA straight from the TMA tile.
+struct TcrParams {
+  int64_t L, C;
+  int64_t rows;         // A rows: left L, right (L / d_in) * C
+  int R, RB, N;         // rank, rank rounded to 16, MMA N of the widest block
+  int d_in;             // rows of the resident factor
+  int nst;              // stages per inner pass: ceil(d_in / bk)
+  int stages;           // X pipeline depth
+  int64_t n_out;        // left: outer indices C / d_in
+  int64_t o_span;       // left: outer indices per work item
+  int64_t m_tiles;      // left: 128-row tiles of A
+  int64_t items;
+  int tpc;              // right: 128-row tiles per output row c (= jdim / 128)
+  int tpi;              // right: tiles per work item (divides tpc)
+  int nsplit;           // right: work items per output row c (= tpc / tpi)
+  int64_t jdim;         // right: L / d_in
+  int out_mode;         // 0: out[m + Mdim r]; 1: out[m R + r]; 2: partial slice z
+  int64_t Mdim;         // rows of the final output (left L, right C)
+  float* out;
+  int* err;
+  const float* Hin;     // resident factor, d_in x R row-major
+  Krp<float> W;         // the other factors (outer weights)
+};
+
+// weights W[o, r] = prod_m Hw_m[o_m, r] for r < R (o enumerates the weight
+// modes, fastest first)
+__device__ __forceinline__ void tcr_weights(const TcrParams& p, int64_t o, float* w) {
+  int idx[TC_MAXM];
+  uint32_t k = (uint32_t)o;
+#pragma unroll
+  for (int m = 0; m < TC_MAXM; ++m) {
+    if (m < p.W.nm) {
+      const uint32_t d = (uint32_t)p.W.dim[m];
+      const uint32_t q = k / d;
+      idx[m] = (int)(k - q * d);
+      k = q;
+    } else {
+      idx[m] = 0;
+    }
+  }
+#pragma unroll
+  for (int r4 = 0; r4 < 16; ++r4) {
+    float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (4 * r4 < p.R) {
+#pragma unroll
+      for (int m = 0; m < TC_MAXM; ++m) {
+        if (m < p.W.nm) {
+          const float* row = p.W.H[m] + (int64_t)idx[m] * p.R + 4 * r4;
+          if ((p.R & 3) == 0) {
+            const float4 h = __ldg(reinterpret_cast<const float4*>(row));
+            v.x *= h.x; v.y *= h.y; v.z *= h.z; v.w *= h.w;
+          } else {
+            v.x *= __ldg(row);
+            if (4 * r4 + 1 < p.R) v.y *= __ldg(row + 1);
+            if (4 * r4 + 2 < p.R) v.z *= __ldg(row + 2);
+            if (4 * r4 + 3 < p.R) v.w *= __ldg(row + 3);
+          }
+        }
+      }
+    }
+    w[4 * r4 + 0] = v.x; w[4 * r4 + 1] = v.y; w[4 * r4 + 2] = v.z; w[4 * r4 + 3] = v.w;
+  }
+}
+
+// Sum of v[r] over the 32 lanes of the warp for r < 32: a recursive-halving
+// reduce-scatter; lane r returns the warp-wide sum of v[r].
+__device__ __forceinline__ float warp_reduce_scatter32(float* v, int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+template <bool LEFT, bool F32>
+__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
+pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcrParams p) {
+  constexpr int BKX = F32 ? F_BK : BK;             // reduction elements per stage
+  constexpr int UKX = F32 ? F_UK : UK;
+  constexpr int XST = BM * BKX * (F32 ? 4 : 2);    // X stage bytes (16 KB)
+  constexpr int W_EPI = F32 ? 6 : 2;               // epilogue warps (F32: converters 2..5)
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const int stages = p.stages;
+  const int RB = p.RB;
+  const int bstage = (F32 ? 2 : 3) * RB * 128;     // bytes of one B stage image
+  uint8_t* Xs = smem;
+  uint8_t* Bimg = Xs + (size_t)stages * XST;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bimg + (size_t)p.nst * bstage);
+  uint64_t* full_x = bars;                    // TMA -> consumer (MMA or converters)
+  uint64_t* x_empty = full_x + stages;        // consumer -> TMA
+  uint64_t* a_full = x_empty + stages;        // F32: converters -> MMA
+  uint64_t* a_empty = a_full + F_A_SLOTS;     // F32: MMA -> converters
+  uint64_t* acc_full = a_empty + F_A_SLOTS;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* red = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(drain) + 16);  // 4 x 64
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full_x[s], 1);
+      mbar_init(&x_empty[s], F32 ? 4 : 1);
+    }
+    for (int a = 0; a < F_A_SLOTS; ++a) {
+      mbar_init(&a_full[a], 4);
+      mbar_init(&a_empty[a], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == W_MMA) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  // the resident B image: stage j holds rows j*BKX .. j*BKX+BKX-1 of H_in
+  // as split terms, K-major, 128-byte swizzled
+  {
+    const int64_t total = (int64_t)p.nst * BKX * RB;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+      const int r = (int)(e % RB);
+      const int k = (int)(e / RB);
+      const int j = k / BKX, kk = k - j * BKX;
+      const float v = (k < p.d_in && r < p.R) ? __ldg(p.Hin + (int64_t)k * p.R + r) : 0.f;
+      uint8_t* b = Bimg + (size_t)j * bstage;
+      if (F32) {
+        const float hi = tf32_rn(v);
+        *reinterpret_cast<float*>(b + sw128_off32(r, kk)) = hi;
+        *reinterpret_cast<float*>(b + sw128_off32(RB + r, kk)) = tf32_rn(v - hi);
+      } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(r, kk)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(RB + r, kk)) = mid;
+        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(2 * RB + r, kk)) =
+            __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      }
+    }
+    fence_proxy_async_smem();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t d_col0 = F32 ? F_A_SLOTS * 64 : 0;
+  const uint32_t d_stride = F32 ? (uint32_t)(2 * RB) : 256u;
+
+  // Work item layout.  Left: item = (128-row tile of L, range of outer
+  // indices).  Right: item = (output row c, slice of its tpc row tiles).
+  const int nsub = LEFT ? 1 : p.tpi;
+  auto tile_m0 = [&](int64_t it, int u) -> int64_t {
+    if (LEFT) return (it % p.m_tiles) * BM;
+    const int64_t c = it / p.nsplit, z = it % p.nsplit;
+    return ((c * p.tpc) + z * p.tpi + u) * BM;
+  };
+  auto item_o0 = [&](int64_t it) { return LEFT ? (it / p.m_tiles) * p.o_span : (int64_t)0; };
+  auto item_o1 = [&](int64_t it) {
+    return LEFT ? min(p.n_out, (it / p.m_tiles) * p.o_span + p.o_span) : (int64_t)1;
+  };
+
+  if (warp == W_TMA) {
+    if (lane == 0) {
+      prefetch_tmap(&tmap);
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_ph = 0;
+      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+        for (int u = 0; u < nsub && ok; ++u) {
+          const int64_t m0 = tile_m0(it, u);
+          for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
+            for (int j = 0; j < p.nst; ++j) {
+              if (!mbar_wait(&x_empty[s], ph ^ 1, abort, p.err, 21)) { ok = false; break; }
+              armed |= 1u << s;
+              armed_ph = (armed_ph & ~(1u << s)) | (ph << s);
+              mbar_arrive_expect_tx(&full_x[s], XST);
+              uint8_t* x = Xs + (size_t)s * XST;
+              if (LEFT) {
+                tma_load_3d(x, &tmap, &full_x[s], (int)m0, j * BKX, (int)o);
+                if (!F32) tma_load_3d(x + XST / 2, &tmap, &full_x[s], (int)m0 + 64, j * BKX, (int)o);
+              } else {
+                tma_load_2d(x, &tmap, &full_x[s], j * BKX, (int)m0);
+              }
+              if (++s == stages) { s = 0; ph ^= 1; }
             }
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
-      buf ^= 1;
+      if (!ok) {
+        for (int t = 0; t < stages; ++t) {
+          if (!((armed >> t) & 1u)) continue;
+          const uint32_t par = (armed_ph >> t) & 1u;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full_x[t], par) && clock64() - t0 < kWaitCycles / 16) {
+          }
+        }
+      }
+    }
+  } else if (warp == W_MMA) {
+    if (lane == 0) {
+      const uint32_t id_a = F32 ? instr_desc(2u, false, false, BM, 2 * RB)
+                                : instr_desc(1u, LEFT, false, BM, 3 * RB);
+      const uint32_t id_b = instr_desc(2u, false, false, BM, RB);
+      int s = 0, as = 0;
+      uint32_t ph = 0, aph = 0, eph = 0;
+      int buf = 0;
+      bool ok = true, issued = false;
+      const uint32_t b_base = smem_u32(Bimg);
+      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+        for (int u = 0; u < nsub && ok; ++u) {
+          for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
+            for (int g0 = 0; g0 < p.nst && ok; g0 += SEG_STAGES) {
+              if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 22)) {
+                ok = false;
+                break;
+              }
+              eph ^= 1u << buf;
+              tc_fence_after();
+              const uint32_t d = tmem + d_col0 + (uint32_t)buf * d_stride;
+              uint32_t acc = 0;
+              const int g1 = min(p.nst, g0 + SEG_STAGES);
+              for (int j = g0; j < g1; ++j) {
+                // FP32: the converters consume X and hand over TMEM slots;
+                // BF16: the MMA reads the X tile itself
+                if (F32) {
+                  if (!mbar_wait(&a_full[as], aph, abort, p.err, 24)) { ok = false; break; }
+                } else {
+                  if (!mbar_wait(&full_x[s], ph, abort, p.err, 23)) { ok = false; break; }
+                }
+                tc_fence_after();
+                const uint32_t b0 = b_base + (uint32_t)(j * bstage);
+                if (F32) {
+                  const uint32_t a_hi = tmem + (uint32_t)as * 64u;
+#pragma unroll
+                  for (int kk = 0; kk < BKX / UKX; ++kk) {
+                    const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+                    mma_tf32_ts(d, a_hi + kk * UKX, bd, id_a, acc);
+                    mma_tf32_ts(d + RB, a_hi + 32 + kk * UKX, bd, id_b, 1u);
+                    acc = 1;
+                  }
+                  mma_commit(&a_empty[as]);
+                  if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
+                } else {
+                  const uint32_t a0 = smem_u32(Xs + (size_t)s * XST);
+#pragma unroll
+                  for (int kk = 0; kk < BKX / UKX; ++kk) {
+                    const uint64_t ad = LEFT ? smem_desc(a0 + kk * 2048, XST / 2, 1024, kLayoutSW128)
+                                             : smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
+                    const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+                    mma_f16_ss(d, ad, bd, id_a, acc);
+                    acc = 1;
+                  }
+                  mma_commit(&x_empty[s]);
+                  if (++s == stages) { s = 0; ph ^= 1; }
+                }
+                issued = true;
+              }
+              if (!ok) break;
+              mma_commit(&acc_full[buf]);
+              buf ^= 1;
+            }
+          }
+        }
+      }
+      if (issued) {
+        mma_commit(drain);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (F32 && warp < W_EPI) {
+    // X converters: row m of the tile (TMEM lane m) -> tf32 hi | lo in TMEM
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int s = 0, as = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+      for (int u = 0; u < nsub && ok; ++u) {
+        for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
+          for (int j = 0; j < p.nst; ++j) {
+            if (!mbar_wait(&full_x[s], ph, abort, p.err, 25)) { ok = false; break; }
+            if (!mbar_wait(&a_empty[as], aph ^ 1, abort, p.err, 26)) { ok = false; break; }
+            const uint32_t x = smem_u32(Xs + (size_t)s * XST);
+            float v[F_BK];
+            if (LEFT) {
+#pragma unroll
+              for (int c = 0; c < F_BK; ++c) v[c] = lds_f32(x + c * 512 + row * 4);
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const uint32_t a = x + row * 128 + (((jj ^ (row & 7)) & 7) << 4);
+                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                             : "=f"(v[4 * jj + 0]), "=f"(v[4 * jj + 1]), "=f"(v[4 * jj + 2]),
+                               "=f"(v[4 * jj + 3])
+                             : "r"(a)
+                             : "memory");
+              }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&x_empty[s]);
+            tc_fence_after();
+            uint32_t hi[F_BK], lo[F_BK];
+#pragma unroll
+            for (int c = 0; c < F_BK; ++c) {
+              const float h = tf32_rn(v[c]);
+              hi[c] = __float_as_uint(h);
+              lo[c] = __float_as_uint(tf32_rn(v[c] - h));
+            }
+            const uint32_t a = tmem + lane_base + (uint32_t)as * 64u;
+            tmem_st16(a, hi);
+            tmem_st16(a + 16, hi + 16);
+            tmem_st16(a + 32, lo);
+            tmem_st16(a + 48, lo + 16);
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[as]);
+            if (++s == stages) { s = 0; ph ^= 1; }
+            if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
+          }
+        }
+      }
+    }
+  } else if (warp >= W_EPI) {
+    // epilogue: drain each group into registers and apply the outer weights
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    uint32_t fph = 0;
+    int buf = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+      float sum[64];
+#pragma unroll
+      for (int r = 0; r < 64; ++r) sum[r] = 0.f;
+      for (int u = 0; u < nsub && ok; ++u) {
+        float w[64];
+        if (!LEFT) {
+          // row (j, c) of this tile carries the weight W[j]
+          const int64_t jrow = (tile_m0(it, u) + row) % p.jdim;
+          if (p.W.nm > 0) tcr_weights(p, jrow, w);
+        }
+        for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
+          if (LEFT && p.W.nm > 0) tcr_weights(p, o, w);
+          const bool weighted = p.W.nm > 0;
+          for (int g0 = 0; g0 < p.nst; g0 += SEG_STAGES) {
+            if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 27)) { ok = false; break; }
+            fph ^= 1u << buf;
+            tc_fence_after();
+            const uint32_t taddr =
+                tmem + d_col0 + (uint32_t)buf * d_stride + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if (c * 16 < RB) {
+                float h[16], t1[16], t2[16];
+                tmem_ld16(taddr + c * 16, h);
+                tmem_ld16(taddr + RB + c * 16, t1);
+                if (!F32) tmem_ld16(taddr + 2 * RB + c * 16, t2);
+                tmem_ld_wait();
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                  const float v = F32 ? h[jj] + t1[jj] : h[jj] + (t1[jj] + t2[jj]);
+                  sum[c * 16 + jj] = weighted ? fmaf(v, w[c * 16 + jj], sum[c * 16 + jj])
+                                              : sum[c * 16 + jj] + v;
+                }
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            buf ^= 1;
+          }
+        }
+      }
+      if (!ok) break;
+      if (LEFT) {
+        const int64_t m = tile_m0(it, 0) + row;
+        if (m < p.rows) {
+          float* base;
+          int64_t stride;
+          if (p.out_mode == 1) {
+            base = p.out + m * p.R;
+            stride = 1;
+          } else {
+            base = p.out + (p.out_mode == 2 ? (it / p.m_tiles) * p.Mdim * p.R : 0) + m;
+            stride = p.Mdim;
+          }
+#pragma unroll
+          for (int r = 0; r < 64; ++r)
+            if (r < p.R) base[r * stride] = sum[r];
+        }
+      } else {
+        // sum the item's rows (one output row c): reduce-scatter within the
+        // warp (lane r ends with column r), then across the four warps
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (32 * h < p.R) {
+            const float v = warp_reduce_scatter32(sum + 32 * h, lane);
+            red[q * 64 + 32 * h + lane] = v;
+          }
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        const int tid = threadIdx.x - W_EPI * 32;
+        if (tid < p.R) {
+          const float v = (red[tid] + red[64 + tid]) + (red[128 + tid] + red[192 + tid]);
+          const int64_t c = it / p.nsplit, z = it % p.nsplit;
+          if (p.out_mode == 0) p.out[c + p.Mdim * tid] = v;
+          else if (p.out_mode == 1) p.out[c * p.R + tid] = v;
+          else p.out[z * p.Mdim * p.R + c + p.Mdim * tid] = v;
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+      }
     }
   }
 
@@ -601,26 +1221,40 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-int stages_for(int N) {
-  const int budget = 200 * 1024;
-  int per = A_STAGE_BYTES + N * 128;
-  int s = budget / per;
-  return std::max(2, std::min(6, s));
-}
+// Shared-memory plan: pipeline depth and whether the first Khatri-Rao
+// factor (h0_bytes) is staged in shared memory (kept only if at least four
+// stages still fit).
+struct SmemPlan {
+  int stages;
+  int h0_smem;
+  size_t bytes;
+};
 
-int stages_for_f32(int RB) {
-  const int budget = 200 * 1024;
-  int per = F_X_STAGE_BYTES + 2 * RB * 128;
-  return std::max(2, std::min(6, budget / per));
-}
-
-size_t smem_bytes_f32(int RB, int stages) {
-  return 1024 + (size_t)stages * (F_X_STAGE_BYTES + 2 * RB * 128) +
-         (4 * stages + 2 * F_A_SLOTS + 5) * 8 + 16;
-}
-
-size_t smem_bytes(int N, int stages) {
-  return 1024 + (size_t)stages * (A_STAGE_BYTES + N * 128) + (3 * stages + 5) * 8 + 16;
+SmemPlan plan_smem(bool f32, int RB, int N, int64_t h0_bytes) {
+  const size_t budget = 227 * 1024 - 256;
+  const size_t per = f32 ? (size_t)F_X_STAGE_BYTES + 2 * RB * 128 : (size_t)A_STAGE_BYTES + N * 128;
+  auto bars = [&](int st) -> size_t {
+    return (f32 ? (4 * st + 2 * F_A_SLOTS + 5) : (3 * st + 5)) * 8 + 16;
+  };
+  auto total = [&](int st, size_t h0) { return 1024 + st * per + bars(st) + h0; };
+  SmemPlan pl{2, 0, 0};
+  for (int st = 6; st >= 4; --st) {
+    if (h0_bytes <= 64 * 1024 && total(st, (size_t)h0_bytes) <= budget) {
+      pl.stages = st;
+      pl.h0_smem = 1;
+      pl.bytes = total(st, (size_t)h0_bytes);
+      return pl;
+    }
+  }
+  for (int st = 6; st >= 2; --st) {
+    if (total(st, 0) <= budget) {
+      pl.stages = st;
+      pl.bytes = total(st, 0);
+      return pl;
+    }
+  }
+  pl.bytes = total(2, 0);
+  return pl;
 }
 
 // Reduction elements per work item (a multiple of the stage depth bk):
@@ -638,34 +1272,199 @@ int64_t item_kspan(int64_t Mdim, int64_t Kdim, int sm_count, int bk, int64_t max
 }
 
 int stage_bk(planc_dtype_t xdt) { return xdt == PLANC_F32 ? F_BK : BK; }
-int64_t stage_max_k(planc_dtype_t xdt) { return xdt == PLANC_F32 ? 2048 : 4096; }
+int64_t stage_max_k(planc_dtype_t) { return 1LL << 30; }
+
+
+// ---- resident-operand plan ----------------------------------------------------------
+struct TcrPlan {
+  bool ok = false;
+  int RB = 16, nst = 1, stages = 2;
+  int64_t d_in = 0, n_out = 1, jdim = 1, rows = 0, m_tiles = 0, o_span = 1, items = 0;
+  int tpc = 1, nsplit = 1;
+  int64_t splits = 1;   // partial slices summed afterwards (left: outer splits, right: nsplit)
+  size_t smem = 0;
+};
+
+TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, const KrpHost& kh,
+                 int sm_count) {
+  TcrPlan pl;
+  if (xdt != PLANC_BF16 && xdt != PLANC_F32) return pl;
+  if (R < 1 || R > 64 || kh.nm < 1 || kh.nm - 1 > TC_MAXM) return pl;
+  const bool f32 = xdt == PLANC_F32;
+  const int64_t e = f32 ? 4 : 2;
+  const int bk = f32 ? F_BK : BK;
+  pl.RB = round_up(R, 16);
+  pl.d_in = kh.dim[0];
+  pl.nst = (int)((pl.d_in + bk - 1) / bk);
+  const size_t bstage = (size_t)(f32 ? 2 : 3) * pl.RB * 128;
+  const size_t bimg = (size_t)pl.nst * bstage;
+  if (bimg > 136 * 1024) return pl;
+  if (L >= (1LL << 31) || C >= (1LL << 31)) return pl;
+  if (left) {
+    if ((L * e) % 16 != 0) return pl;
+    pl.n_out = C / pl.d_in;
+    pl.rows = L;
+    pl.m_tiles = (L + BM - 1) / BM;
+    int64_t osplit = 1;
+    if (pl.m_tiles < 2 * sm_count)
+      osplit = std::min<int64_t>(pl.n_out, (2 * sm_count + pl.m_tiles - 1) / pl.m_tiles);
+    pl.o_span = (pl.n_out + osplit - 1) / osplit;
+    pl.splits = (pl.n_out + pl.o_span - 1) / pl.o_span;
+    pl.items = pl.m_tiles * pl.splits;
+  } else {
+    if ((pl.d_in * e) % 16 != 0) return pl;
+    pl.jdim = L / pl.d_in;
+    if (pl.jdim % BM != 0) return pl;
+    pl.rows = pl.jdim * C;
+    if (pl.rows >= (1LL << 31)) return pl;
+    pl.m_tiles = pl.rows / BM;
+    pl.tpc = (int)(pl.jdim / BM);
+    // items per output row c: enough items for ~4 per SM, dividing tpc
+    int ns = 1;
+    while (ns < pl.tpc && C * ns < 4LL * sm_count) ns *= 2;
+    while (pl.tpc % ns != 0) --ns;
+    pl.nsplit = ns;
+    pl.splits = ns;
+    pl.items = C * ns;
+  }
+  const size_t xst = (size_t)BM * bk * e;
+  const size_t budget = 227 * 1024 - 256;
+  for (int st = 6; st >= 3; --st) {
+    const size_t total = 1024 + st * xst + bimg + (2 * st + 2 * F_A_SLOTS + 5) * 8 + 16 + 1024;
+    if (total <= budget) {
+      pl.stages = st;
+      pl.smem = total;
+      pl.ok = true;
+      return pl;
+    }
+  }
+  return pl;
+}
+
+KrpHost dims_only(const KrpHost& kh) { return kh; }
 
 }  // namespace
 
-bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R) {
-  (void)left;
+bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
+                    const KrpHost& kh) {
   if (xdt != PLANC_BF16 && xdt != PLANC_F32) return false;
   if (R < 1 || R > 64) return false;
+  if (kh.nm < 1 || kh.nm > TC_MAXM) return false;
   // TMA: the row stride of X_(1:S) (L elements) must be a multiple of 16 bytes
-  if ((L * (int64_t)dtype_size(xdt)) % 16 != 0) return false;
+  if ((L * (int64_t)dtype_size(xdt)) % 16 != 0 &&
+      !tcr_plan(xdt, left, L, C, R, kh, 148).ok)
+    return false;
   if (L >= (1LL << 31) || C >= (1LL << 31)) return false;
   if (encode_fn() == nullptr) return false;
   return true;
 }
 
 size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
-                             int sm_count) {
-  if (!pm_tc_eligible(xdt, left, L, C, R)) return 0;
+                             const KrpHost& kh, int sm_count) {
+  if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return 0;
+  const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
+  if (pl.ok) return pl.splits > 1 ? (size_t)pl.splits * (left ? L : C) * R * sizeof(float) : 0;
   const int64_t Mdim = left ? L : C, Kdim = left ? C : L;
   const int64_t span = item_kspan(Mdim, Kdim, sm_count, stage_bk(xdt), stage_max_k(xdt));
   const int64_t splits = (Kdim + span - 1) / span;
   return splits > 1 ? (size_t)splits * Mdim * R * sizeof(float) : 0;
 }
 
+namespace {
+
+cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
+                       const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
+                       size_t work_bytes, int* err_flag, const TcrPlan& pl, cudaStream_t st) {
+  const bool f32 = xdt == PLANC_F32;
+  TcrParams p{};
+  p.L = L;
+  p.C = C;
+  p.rows = pl.rows;
+  p.R = R;
+  p.RB = pl.RB;
+  p.N = (f32 ? 2 : 3) * pl.RB;
+  p.d_in = (int)pl.d_in;
+  p.nst = pl.nst;
+  p.stages = pl.stages;
+  p.n_out = pl.n_out;
+  p.o_span = pl.o_span;
+  p.m_tiles = pl.m_tiles;
+  p.items = pl.items;
+  p.tpc = pl.tpc;
+  p.nsplit = pl.nsplit;
+  p.tpi = pl.tpc / pl.nsplit;
+  p.jdim = pl.jdim;
+  p.Mdim = left ? L : C;
+  p.err = err_flag;
+  p.Hin = (const float*)kh.H[0];
+  p.W.nm = kh.nm - 1;
+  p.W.R = R;
+  for (int m = 1; m < kh.nm; ++m) {
+    p.W.dim[m - 1] = kh.dim[m];
+    p.W.H[m - 1] = (const float*)kh.H[m];
+  }
+  if (pl.splits > 1) {
+    if (work_bytes < (size_t)pl.splits * p.Mdim * R * sizeof(float)) return cudaErrorInvalidValue;
+    p.out_mode = 2;
+    p.out = (float*)work;
+  } else {
+    p.out_mode = out_rowmajor ? 1 : 0;
+    p.out = (float*)out;
+  }
+  const cuuint64_t e = f32 ? 4 : 2;
+  CUtensorMap tmap;
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult cr;
+  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (left) {
+    // X as L x d_in x n_out
+    cuuint64_t gdim[3] = {(cuuint64_t)L, (cuuint64_t)pl.d_in, (cuuint64_t)pl.n_out};
+    cuuint64_t gstride[2] = {(cuuint64_t)L * e, (cuuint64_t)L * pl.d_in * e};
+    cuuint32_t box[3] = {f32 ? 128u : 64u, (cuuint32_t)(f32 ? F_BK : BK), 1u};
+    cr = encode_fn()(&tmap, dt, 3, const_cast<void*>(X), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     f32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    // X as d_in x rows (rows = (L / d_in) * C)
+    cuuint64_t gdim[2] = {(cuuint64_t)pl.d_in, (cuuint64_t)pl.rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)pl.d_in * e};
+    cuuint32_t box[2] = {(cuuint32_t)(f32 ? F_BK : BK), 128u};
+    cr = encode_fn()(&tmap, dt, 2, const_cast<void*>(X), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int threads = f32 ? 320 : 192;
+  cudaError_t err;
+  auto k = left ? (f32 ? pm_tcr_kernel<true, true> : pm_tcr_kernel<true, false>)
+                : (f32 ? pm_tcr_kernel<false, true> : pm_tcr_kernel<false, false>);
+  err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(pl.items, sms);
+  k<<<grid, threads, pl.smem, st>>>(tmap, p);
+  note_launches(1);
+  err = cudaGetLastError();
+  if (err != cudaSuccess || pl.splits == 1) return err;
+  return launch_split_reduce(false, work, (int)pl.splits, p.Mdim, R, out, out_rowmajor, st);
+}
+
+}  // namespace
+
 cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
                          const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
                          size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st) {
-  if (!pm_tc_eligible(xdt, left, L, C, R)) return cudaErrorNotSupported;
+  if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return cudaErrorNotSupported;
+  {
+    const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
+    if (pl.ok && getenv("PLANC_TC_STREAMED_KRP") == nullptr)
+      return launch_tcr(xdt, X, L, C, left, kh, R, out, out_rowmajor, work, work_bytes, err_flag,
+                        pl, st);
+  }
+  if ((L * (int64_t)dtype_size(xdt)) % 16 != 0) return cudaErrorNotSupported;
   if (((uintptr_t)X & 15) != 0) return cudaErrorNotSupported;
   TcParams p{};
   p.L = L;
@@ -674,7 +1473,9 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
   const bool f32 = xdt == PLANC_F32;
   p.RB = round_up(R, 16);
   p.N = f32 ? 2 * p.RB : 3 * p.RB;
-  p.stages = f32 ? stages_for_f32(p.RB) : stages_for(p.N);
+  const SmemPlan sp = plan_smem(f32, p.RB, p.N, kh.dim[0] * (int64_t)R * 4);
+  p.stages = sp.stages;
+  p.h0_smem = sp.h0_smem;
   p.err = err_flag;
   p.K.nm = kh.nm;
   p.K.R = R;
@@ -717,7 +1518,7 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
   }
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
-  const size_t smem = f32 ? smem_bytes_f32(p.RB, p.stages) : smem_bytes(p.N, p.stages);
+  const size_t smem = sp.bytes;
   const int grid = (int)std::min<int64_t>(p.items, sm_count);
   cudaError_t e;
   if (f32) {

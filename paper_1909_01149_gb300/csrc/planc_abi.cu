@@ -280,15 +280,17 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   const bool allow_tc = !(path && strcmp(path, "simt") == 0);
   for (int s = 0; s < 2; ++s) {
     const bool left = s == 0;
+    KrpHost kd;  // dims of the branch's Khatri-Rao operand (pointers unused)
+    for (int m = left ? S : 0; m < (left ? N : S); ++m) kd.dim[kd.nm++] = dims[m];
     ctx->use_tc[s] = allow_tc && ((uintptr_t)X & 15) == 0 &&
-                     pm_tc_eligible(x_dtype, left, ctx->L, ctx->C, R);
+                     pm_tc_eligible(x_dtype, left, ctx->L, ctx->C, R, kd);
     if (!ctx->use_tc[s]) {
       ctx->nsplit[s] = pm_simt_nsplit(left, ctx->L, ctx->C, R, ctx->sm_count);
       if (ctx->nsplit[s] > 1)
         part_elems = std::max(part_elems, (size_t)ctx->nsplit[s] * (left ? ctx->L : ctx->C) * R);
     } else {
       ctx->tc_bytes = std::max(ctx->tc_bytes, pm_tc_workspace_bytes(x_dtype, left, ctx->L, ctx->C,
-                                                                     R, ctx->sm_count));
+                                                                     R, kd, ctx->sm_count));
     }
   }
   // multi-TTV leaf partials, every (node, mode) pair the walks can meet
