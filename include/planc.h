@@ -256,6 +256,34 @@ planc_solve_opts planc_solve_opts_default(void);
 planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,
                              double* loss);
 
+/* ---- allocation-free variant --------------------------------------------- */
+
+/* alpha = ||X||^2 for a flat device buffer X of n elements of x_dtype, written
+ * to the device double *alpha, on cuda_stream (NULL = legacy stream), without
+ * a context and without allocating any device memory.  (The paper has no
+ * counterpart; this is a library convenience.)
+ *
+ * For callers that cannot allocate device memory when they need the
+ * reduction: work enqueued while a stream is being captured into a CUDA graph
+ * (allocation is not allowed during capture), runtimes that own all device
+ * memory through their own fixed pool, and latency-critical loops that must
+ * stay out of the allocator.  The per-block partial sums live in a
+ * statically sized device array inside the library (1024 doubles, 8 KiB per
+ * device that loads the library, held until the process exits); the result
+ * equals planc_sqnorm's.
+ *
+ * The first call on each device looks up that array's device address with
+ * cudaGetSymbolAddress while the device is current; make that first call
+ * outside any stream capture.  All calls share the one array, so calls whose
+ * work overlaps on the GPU (different streams, no ordering between them) race
+ * on it; calls ordered on one stream are safe.  Every call overwrites the
+ * partials it reads, so nothing needs clearing between calls.
+ * Errors: PLANC_E_INVALID (NULL pointer), PLANC_E_DTYPE, PLANC_E_SHAPE (n < 1,
+ * n > 2^40, or a GPU whose reduction grid would need more than 1024
+ * partials), PLANC_E_CUDA.  Asynchronous. */
+planc_status_t planc_sqnorm_noalloc(planc_dtype_t x_dtype, const void* X, int64_t n,
+                                    double* alpha, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ def _load():
         "planc_fit": (I, [P, PP, P, C.POINTER(D), C.POINTER(D)]),
         "planc_nncp_solve": (I, [P, C.POINTER(SolveOpts), PP, C.POINTER(D), C.POINTER(Report)]),
         "planc_cp_grad": (I, [P, PP, PP, C.POINTER(D)]),
+        "planc_sqnorm_noalloc": (I, [I, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
