@@ -62,6 +62,7 @@ cudaError_t launch_contract_first(bool f64, const void* T, int64_t P1, int64_t Q
                                   const void* h, void* out, bool out_rowmajor,
                                   cudaStream_t st);
 int contract_rest_qsplit(int64_t P1, int64_t Q, int R, int sm_count);
+bool contract_rest_v4_ok(int64_t P1, const void* T);
 cudaError_t launch_contract_rest(bool f64, const void* T, int64_t P1, int64_t Q, int R,
                                  const KrpHost& krp, void* out, void* part, int qsplit,
                                  cudaStream_t st);
@@ -82,7 +83,7 @@ cudaError_t launch_scale_gram(bool f64, int64_t rows, int R, void* H, const doub
                               int nblk, double* lambda, double* gram_part, bool scale,
                               cudaStream_t st);
 // G = sum of the Gram partials (fixed order).
-cudaError_t launch_gram_reduce(int R, const double* gram_part, int nblk, double* G,
+cudaError_t launch_gram_reduce(int R, const double* gram_part, int nblk, double* G, float* Gf,
                                cudaStream_t st);
 // The error identity of Alg. 4: eps = sqrt(max(0, alpha - 2 beta + gamma) /
 // alpha) with beta = sum of the dot partials and gamma = lambda^T (G^(1) *
@@ -116,6 +117,13 @@ struct NlsArgs {
 size_t nls_scratch_doubles(int64_t rows, int R);
 cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st);
 
+// ---- fused per-mode update (S, NNLS, normalisation, Gram, error) ------------------
+bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R);
+cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
+                              float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
+                              const planc_nls_opts& o, int32_t* inner, const double* alpha,
+                              double* fit_out, cudaStream_t st);
+
 // ---- PM-right / mTTV split reductions -------------------------------------------
 cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,
                                 void* out, bool out_rowmajor, cudaStream_t st);
@@ -146,6 +154,7 @@ struct planc_ctx {
   void* Mbuf = nullptr;                  // max_dim x R
   void* Ubuf = nullptr;                  // ADMM dual, max_dim x R
   double* G = nullptr;                   // N x R x R
+  float* Gf = nullptr;                   // the same Grams rounded to FP32
   double* Sm = nullptr;                  // R x R
   double* lam = nullptr;                 // R
   double* scal = nullptr;                // [0] alpha, [1..] scratch
@@ -162,6 +171,7 @@ struct planc_ctx {
   // dimension-tree state during a solve
   int nsplit[2] = {1, 1};
   bool use_tc[2] = {false, false};
+  bool fused_modes = true;
   size_t node_elems = 0;
 
   // profiling (partial-MTTKRP launches)

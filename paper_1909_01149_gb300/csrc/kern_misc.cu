@@ -184,13 +184,14 @@ scale_gram_kernel(int64_t rows, int R, int64_t rb, TA* __restrict__ H,
 
 // ---- G = sum of Gram partials --------------------------------------------------------
 __global__ void gram_reduce_kernel(int R, const double* __restrict__ gram_part, int nblk,
-                                   double* __restrict__ G) {
+                                   double* __restrict__ G, float* __restrict__ Gf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int RR = R * R;
   if (i >= RR) return;
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += gram_part[(int64_t)b * RR + i];
   G[i] = s;
+  if (Gf) Gf[i] = (float)s;
 }
 
 // ---- error identity (Alg. 4) ---------------------------------------------------------
@@ -330,10 +331,10 @@ cudaError_t launch_scale_gram(bool f64, int64_t rows, int R, void* H, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_reduce(int R, const double* gram_part, int nblk, double* G,
+cudaError_t launch_gram_reduce(int R, const double* gram_part, int nblk, double* G, float* Gf,
                                cudaStream_t st) {
   int RR = R * R;
-  gram_reduce_kernel<<<(RR + 255) / 256, 256, 0, st>>>(R, gram_part, nblk, G);
+  gram_reduce_kernel<<<(RR + 255) / 256, 256, 0, st>>>(R, gram_part, nblk, G, Gf);
   note_launches(1);
   return cudaGetLastError();
 }

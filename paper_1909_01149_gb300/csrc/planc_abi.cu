@@ -278,6 +278,9 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   // (for A/B comparisons); by default eligible shapes use the tensor cores.
   const char* path = getenv("PLANC_PM_PATH");
   const bool allow_tc = !(path && strcmp(path, "simt") == 0);
+  // PLANC_FUSED_MODES=0 keeps every mode update on the multi-kernel path
+  const char* fm = getenv("PLANC_FUSED_MODES");
+  ctx->fused_modes = !(fm && strcmp(fm, "0") == 0);
   for (int s = 0; s < 2; ++s) {
     const bool left = s == 0;
     KrpHost kd;  // dims of the branch's Khatri-Rao operand (pointers unused)
@@ -324,6 +327,7 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   add((size_t)ctx->max_dim * R * fs);       // Mbuf
   add((size_t)ctx->max_dim * R * fs);       // Ubuf
   add((size_t)N * R * R * 8);               // G
+  add((size_t)N * R * R * 4);               // G in FP32
   add((size_t)R * R * 8);                   // S
   add((size_t)R * 8);                       // lambda
   add(64 * 8);                              // scal
@@ -350,6 +354,7 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   ctx->Mbuf = carve(p, (size_t)ctx->max_dim * R * fs);
   ctx->Ubuf = carve(p, (size_t)ctx->max_dim * R * fs);
   ctx->G = (double*)carve(p, (size_t)N * R * R * 8);
+  ctx->Gf = (float*)carve(p, (size_t)N * R * R * 4);
   ctx->Sm = (double*)carve(p, (size_t)R * R * 8);
   ctx->lam = (double*)carve(p, (size_t)R * 8);
   ctx->scal = (double*)carve(p, 64 * 8);
@@ -462,7 +467,12 @@ static planc_status_t gram_impl(planc_t ctx, int64_t rows, void* H, double* G, d
     CK(launch_colsq(is_f64(ctx), rows, R, H, M, colsq, dotp, nb, ctx->stream), "colsq launch");
   CK(launch_scale_gram(is_f64(ctx), rows, R, H, colsq, nb, lambda, gpart, scale, ctx->stream),
      "scale/gram launch");
-  if (G) CK(launch_gram_reduce(R, gpart, nb, G, ctx->stream), "gram reduce launch");
+  if (G) {
+    // the solver's own Grams also keep their FP32 copy (read by the fused mode update)
+    float* Gf = (G >= ctx->G && G < ctx->G + (size_t)ctx->N * R * R) ? ctx->Gf + (G - ctx->G)
+                                                                        : nullptr;
+    CK(launch_gram_reduce(R, gpart, nb, G, Gf, ctx->stream), "gram reduce launch");
+  }
   (void)dot_part_out;
   return PLANC_OK;
 }
@@ -569,6 +579,14 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
     if ((st = dt_mode(ctx, H, n, ctx->Mbuf, &cur[s], &cf[s])) != PLANC_OK) return st;
+    const bool last = n == N - 1;
+    if (ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R)) {
+      // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after mode N)
+      CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n], ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
+                           last ? ctx->scal + 8 : nullptr, ctx->stream),
+         "fused mode update launch");
+      continue;
+    }
     CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->stream), "gram_hadamard launch");
     NlsArgs a;
     a.alg = o.alg;
@@ -592,12 +610,12 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
     double* colsq = ctx->red;
     double* dotp = colsq + (size_t)nb * R;
     double* gpart = dotp + nb;
-    const bool last = n == N - 1;
     CK(launch_colsq(is_f64(ctx), rows, R, H[n], last ? ctx->Mbuf : nullptr, colsq, dotp, nb,
                     ctx->stream), "colsq launch");
     CK(launch_scale_gram(is_f64(ctx), rows, R, H[n], colsq, nb, ctx->lam, gpart, true,
                          ctx->stream), "scale/gram launch");
-    CK(launch_gram_reduce(R, gpart, nb, ctx->G + (size_t)n * R * R, ctx->stream),
+    CK(launch_gram_reduce(R, gpart, nb, ctx->G + (size_t)n * R * R, ctx->Gf + (size_t)n * R * R,
+                          ctx->stream),
        "gram reduce launch");
     if (last)
       CK(launch_fit(R, ctx->G, N, ctx->lam, dotp, nb, ctx->scal, ctx->scal + 8, ctx->stream),
