@@ -122,7 +122,7 @@ bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R);
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, cudaStream_t st);
+                              double* fit_out, int* err, cudaStream_t st);
 
 // ---- PM-right / mTTV split reductions -------------------------------------------
 cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,

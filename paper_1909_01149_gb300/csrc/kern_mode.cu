@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace planc {
 
@@ -81,9 +82,10 @@ __device__ __forceinline__ double srow_dot(const double* h, uint32_t srow) {
 }
 
 // l = sqrt(s) and il = 1 / l in FP64 (0 and 0 for s <= 0): an FP32
-// reciprocal-square-root seed refined by two Newton-Raphson steps
-// y <- y (3 - s y^2) / 2, each of which squares the relative error; FP64
-// sqrt and division are avoided because this GPU's FP64 pipe is narrow.
+// reciprocal-square-root seed (relative error below 2^-21) refined by one
+// Newton-Raphson step y <- y (3 - s y^2) / 2, which squares the relative
+// error (below 1e-12 after it); FP64 sqrt and division are avoided because
+// this GPU's FP64 pipe is narrow.
 __device__ __forceinline__ void sqrt_and_inv(double s, double& l, double& il) {
   if (!(s > 0.0)) {
     l = 0.0;
@@ -97,9 +99,20 @@ __device__ __forceinline__ void sqrt_and_inv(double s, double& l, double& il) {
   }
   double y = (double)rsqrtf((float)s);
   y = y * (1.5 - 0.5 * s * y * y);
-  y = y * (1.5 - 0.5 * s * y * y);
   l = s * y;
   il = y;
+}
+
+// sum over the cluster's CTAs of slot[src * stride], as a fixed pairwise tree
+__device__ __forceinline__ double slot_sum(const double* slot, int stride) {
+  double v[MC_CS];
+#pragma unroll
+  for (int i = 0; i < MC_CS; ++i) v[i] = slot[i * stride];
+#pragma unroll
+  for (int w = 1; w < MC_CS; w *= 2)
+#pragma unroll
+    for (int i = 0; i + w < MC_CS; i += 2 * w) v[i] += v[i + w];
+  return v[0];
 }
 
 // x / y for the MU ratio: the FP32 fast division (within 2 ulp for the
@@ -161,47 +174,51 @@ struct McLayout {
   static constexpr int RCN = MC_NT / NBLK;              // row chunks of the Gram
   static constexpr int NP = RP * (RP + 1) / 2;          // packed pairs r <= s
   static constexpr int NPO = (NP + MC_CS - 1) / MC_CS;  // pairs owned per CTA
-  // scratch `red`: [0, MC_NT) column partials, then 4 beta and 4 gamma warp sums
-  static constexpr int RED = MC_NT + 8;
+  static constexpr int RED = 8;                         // beta / gamma warp sums
   // byte offsets
   static constexpr size_t oSs = 0;
   static constexpr size_t oHs = oSs + sizeof(TA) * RP * RP;
   static constexpr size_t oMs = oHs + sizeof(TA) * MC_RPC * RP;
-  static constexpr size_t oTp = oMs + sizeof(TA) * MC_RPC * RP;
+  static constexpr size_t oLin = oMs + sizeof(TA) * MC_RPC * RP;  // bulk-copy landing area
+  static constexpr size_t oTp = oLin + sizeof(TA) * 2 * MC_RPC * RP;
   static constexpr size_t oCs = oTp + sizeof(TA) * RCN * NBLK * 16;
   static constexpr size_t oGs = oCs + sizeof(double) * MC_CS * RP;
   static constexpr size_t oBeta = oGs + sizeof(double) * MC_CS * NPO;
   static constexpr size_t oGam = oBeta + sizeof(double) * MC_CS;
   static constexpr size_t oRed = oGam + sizeof(double) * MC_CS;
   static constexpr size_t bytes = oRed + sizeof(double) * RED;
-  static_assert(MC_NT % RP == 0 && MC_NT == MC_RPC, "one row per thread");
+  static_assert(MC_NT % RP == 0 && MC_NT == MC_RPC && NPO <= MC_NT, "one row / pair per thread");
 };
 
 // G: the N Grams (FP64, R x R each), Gf: the same in FP32.  Mode n's entries
-// of both are overwritten with G^(n) of the updated factor.
+// of both are overwritten with G^(n) of the updated factor.  err: set to 10
+// if the wait for the bulk copies of M and H gives up.
 template <typename TA, int RP>
 __global__ void __launch_bounds__(MC_NT, 1)
 mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     float* __restrict__ Gf, const TA* __restrict__ M, TA* __restrict__ H,
                     double* __restrict__ lam, int alg, double mu_eps, int pgd_steps, double tiny,
                     int32_t* __restrict__ inner, const double* __restrict__ alpha,
-                    double* __restrict__ fit_out) {
+                    double* __restrict__ fit_out, int* __restrict__ err) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
   extern __shared__ __align__(16) unsigned char mc_smem[];
   TA* Ss = reinterpret_cast<TA*>(mc_smem + L::oSs);                 // S^(n), RP x RP
   TA* Hs = reinterpret_cast<TA*>(mc_smem + L::oHs);                 // this CTA's rows
   TA* Ms = reinterpret_cast<TA*>(mc_smem + L::oMs);                 // its rows of M
+  TA* Lin = reinterpret_cast<TA*>(mc_smem + L::oLin);               // M, H as copied
   TA* tp = reinterpret_cast<TA*>(mc_smem + L::oTp);                 // Gram tile partials
-  double* cs_slot = reinterpret_cast<double*>(mc_smem + L::oCs);    // [src CTA][r]
+  double* cs_slot = reinterpret_cast<double*>(mc_smem + L::oCs);    // [src CTA][r]: Ghat(r, r)
   double* g_slot = reinterpret_cast<double*>(mc_smem + L::oGs);     // [src CTA][owned pair]
   double* beta_slot = reinterpret_cast<double*>(mc_smem + L::oBeta);  // [src CTA] (CTA 0)
   double* gam_slot = reinterpret_cast<double*>(mc_smem + L::oGam);    // [src CTA] (CTA 0)
   double* red = reinterpret_cast<double*>(mc_smem + L::oRed);
-  __shared__ double s_lam[RP];
+  __shared__ double s_lam[RP], s_il[RP];
   __shared__ TA s_lamt[RP], s_inv[RP];
   __shared__ TA s_rinv[RP];  // 1 / S(r, r), or 0 where S(r, r) <= tiny (column kept)
   __shared__ TA s_eta;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_abort;
   const int t = threadIdx.x;
   const int RR = R * R;
   const uint32_t c = cluster_rank();
@@ -213,24 +230,37 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
   // (row a, column k); stepping j advances by (q_step, k_step) with a carry
   const int q_step = MC_NT / R, k_step = MC_NT - (MC_NT / R) * R;
   const int a_0 = t / R, k_0 = t - (t / R) * R;
+  const TA* Mrow = M + (size_t)row0 * R;
+  TA* Hrow = H + (size_t)row0 * R;
+  // this CTA's rows of M and H arrive by two bulk copies when both ranges
+  // start on 16 bytes and span a multiple of 16 bytes
+  const uint32_t cbytes = (uint32_t)(nel * sizeof(TA));
+  const bool bulk = nel > 0 && (cbytes & 15u) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(Mrow) | reinterpret_cast<uintptr_t>(Hrow)) & 15u) == 0;
 
   // every CTA of the cluster must be running before any remote store
   cluster_arrive_relaxed();
-
-  // ---- every global load of the prologue is issued up front: this CTA's
-  // rows of M and H (coalesced), lambda, and the other Grams
-  constexpr int LPT = MC_RPC * RP / MC_NT;  // staged elements per thread
   constexpr int EPT = RP * RP / MC_NT;      // entries of S per thread
-  TA mv[LPT], hv[LPT];
-#pragma unroll
-  for (int j = 0; j < LPT; ++j) {
-    const int e = t + j * MC_NT;
-    mv[j] = e < nel ? M[(size_t)row0 * R + e] : TA(0);
-    hv[j] = e < nel ? H[(size_t)row0 * R + e] : TA(0);
-  }
+
   const double lam_t = t < R ? lam[t] : 0.0;
+  // owned pair of this thread (for G^(n) and gamma): p = t * MC_CS + c
+  const int p_own = t * MC_CS + (int)c;
+  int r_own = 0, s_own = 0;
+  if (t < L::NPO && p_own < L::NP) tri_unpack(p_own, RP, r_own, s_own);
+  const bool owns = t < L::NPO && p_own < L::NP && s_own < R;
+  // FP64 entries of the other Grams at the owned pair, for the entry S(r, s)
+  // of gamma after the last mode (held in registers until then; more than
+  // four other modes are read at that point instead)
+  constexpr int QPRE = 4;
+  double gq[QPRE];
+  const bool pre = fit_out && owns && N - 1 <= QPRE;
+#pragma unroll
+  for (int qi = 0; qi < QPRE; ++qi)
+    gq[qi] = (pre && qi + 1 < N) ? G[(size_t)(qi < n ? qi : qi + 1) * RR + r_own * R + s_own] : 1.0;
   // S^(n) = Hadamard of the other Grams, in TA (from the FP32 copies when TA
-  // is FP32); entry (i, k) of S for e = t + j * MC_NT
+  // is FP32); entry (i, k) of S for e = t + j * MC_NT.  With at most QPRE
+  // other modes all entries are loaded before the row copies are issued and
+  // multiplied after.
   TA v[EPT];
   int off[EPT];
 #pragma unroll
@@ -240,19 +270,55 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
     v[j] = in ? TA(1) : TA(0);
     off[j] = in ? i * R + k : 0;
   }
-#pragma unroll 4
-  for (int qi = 0; qi + 1 < N; ++qi) {
+  constexpr int QS = sizeof(TA) == 4 ? QPRE : 1;  // (FP64: loaded when used)
+  const bool sfast = sizeof(TA) == 4 && N - 1 <= QPRE;
+  TA gl[QS][EPT];
+#pragma unroll
+  for (int qi = 0; qi < QS; ++qi) {
     const size_t q = (size_t)(qi < n ? qi : qi + 1);
-    TA g[EPT];
-    if constexpr (sizeof(TA) == 4) {
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) g[j] = Gf[q * RR + off[j]];
-    } else {
-#pragma unroll
-      for (int j = 0; j < EPT; ++j) g[j] = G[q * RR + off[j]];
+    for (int j = 0; j < EPT; ++j) {
+      TA x = TA(1);
+      if (sfast && qi + 1 < N) {
+        if constexpr (sizeof(TA) == 4) x = Gf[q * RR + off[j]];
+        else x = G[q * RR + off[j]];
+      }
+      gl[qi][j] = x;
     }
+  }
+  constexpr int LPT = MC_RPC * RP / MC_NT;  // staged elements per thread
+  TA mv[LPT], hv[LPT];
+  if (bulk) {
+    if (t == 0) {
+      s_abort = 0;
+      tc::mbar_init(&s_bar, 1);
+      tc::fence_mbar_init();
+      tc::mbar_arrive_expect_tx(&s_bar, 2 * cbytes);
+      tc::bulk_g2s(Lin, Mrow, cbytes, &s_bar);
+      tc::bulk_g2s(Lin + MC_RPC * RP, Hrow, cbytes, &s_bar);
+    }
+  } else {
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) v[j] *= g[j];
+    for (int j = 0; j < LPT; ++j) {
+      const int e = t + j * MC_NT;
+      mv[j] = e < nel ? Mrow[e] : TA(0);
+      hv[j] = e < nel ? Hrow[e] : TA(0);
+    }
+  }
+  if (sfast) {
+#pragma unroll
+    for (int qi = 0; qi < QS; ++qi)
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) v[j] *= gl[qi][j];
+  } else {
+    for (int qi = 0; qi + 1 < N; ++qi) {
+      const size_t q = (size_t)(qi < n ? qi : qi + 1);
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) {
+        if constexpr (sizeof(TA) == 4) v[j] *= Gf[q * RR + off[j]];
+        else v[j] *= G[q * RR + off[j]];
+      }
+    }
   }
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
@@ -264,8 +330,7 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
     s_lam[t] = lam_t;
     s_lamt[t] = (TA)lam_t;
   }
-  // staged rows; padding rows are zero (mv = hv = 0 past nel)
-  {
+  if (!bulk) {  // staged rows; padding rows are zero (mv = hv = 0 past nel)
     int a = a_0, k = k_0;
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
@@ -286,6 +351,27 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
     Hs[S::idx(t, k)] = TA(0);
   }
   __syncthreads();
+  if (bulk) {
+    // every thread waits for the copies (bounded); on a timeout the error
+    // word is set and the kernel runs to the end on whatever arrived
+    tc::mbar_wait(&s_bar, 0, &s_abort, err, 10);
+    const TA* Lm = Lin;
+    const TA* Lh = Lin + MC_RPC * RP;
+    int a = a_0, k = k_0;
+#pragma unroll 4
+    for (int e = t; e < MC_RPC * R; e += MC_NT) {
+      const bool in = e < nel;
+      Ms[S::idx(a, k)] = in ? Lm[e] : TA(0);
+      Hs[S::idx(a, k)] = in ? Lh[e] : TA(0);
+      a += q_step;
+      k += k_step;
+      if (k >= R) {
+        k -= R;
+        ++a;
+      }
+    }
+    __syncthreads();
+  }
   if (alg == PLANC_PGD && t < 32) {
     TA f = TA(0);
     for (int e = t; e < RP * RP; e += 32) f = fma(Ss[e], Ss[e], f);
@@ -359,70 +445,11 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
     }
   }
   const double bw = warp_sum((double)beta_t);
-  if ((t & 31) == 0) red[MC_NT + (t >> 5)] = bw;
+  if ((t & 31) == 0) red[t >> 5] = bw;
   __syncthreads();
 
-  // ---- column sums of squares of this CTA's rows: thread (r, chunk)
-  constexpr int CH = MC_NT / RP;
-  {
-    constexpr int RPCH = MC_RPC / CH;
-    const int r = t % RP, ch = t / RP;
-    TA a = TA(0);
-    for (int i = ch * RPCH; i < (ch + 1) * RPCH; ++i) {
-      const TA x = Hs[S::idx(i, r)];
-      a = fma(x, x, a);
-    }
-    red[ch * RP + r] = (double)a;
-  }
-  __syncthreads();
-  cluster_wait();  // pairs with the arrive at kernel start: every CTA is running
-  if (t < RP) {
-    double s = 0.0;
-    for (int ch = 0; ch < CH; ++ch) s += red[ch * RP + t];
-    for (uint32_t dst = 0; dst < MC_CS; ++dst) st_cluster(cs_slot + c * RP + t, dst, s);
-  }
-  if (t == 0) {
-    double b = 0.0;
-    for (int w = 0; w < MC_NT / 32; ++w) b += red[MC_NT + w];
-    st_cluster(beta_slot + c, 0, b);
-  }
-  cluster_arrive();
-  cluster_wait();
-
-  // ---- lambda (identical in every CTA: same slots, same order)
-  if (t < RP) {
-    double s = 0.0;
-    for (int src = 0; src < MC_CS; ++src) s += cs_slot[src * RP + t];
-    double l = 0.0, il = 0.0;  // a zero column keeps lambda = 0 and stays zero
-    if (t < R) sqrt_and_inv(s, l, il);
-    s_lam[t] = l;
-    s_inv[t] = (TA)il;
-    if (c == 0 && t < R) lam[t] = l;
-  }
-  __syncthreads();
-  // ---- normalise this CTA's rows: H = Hhat diag(lambda)^-1
-#pragma unroll
-  for (int g = 0; g < S::GR; ++g) {
-    TA* p = Hs + S::gidx(t, g);
-#pragma unroll
-    for (int u = 0; u < S::VPG; ++u) p[u] *= s_inv[g * S::VPG + u];
-  }
-  __syncthreads();
-  {
-    int a = a_0, k = k_0;
-#pragma unroll 4
-    for (int e = t; e < nel; e += MC_NT) {  // coalesced write of the R live columns
-      H[(size_t)row0 * R + e] = Hs[S::idx(a, k)];
-      a += q_step;
-      k += k_step;
-      if (k >= R) {
-        k -= R;
-        ++a;
-      }
-    }
-  }
-
-  // ---- Gram partial of this CTA: 4x4 tiles (rb <= sb) x row chunks, in TA
+  // ---- Ghat = Hhat^T Hhat over this CTA's rows: 4x4 tiles (rb <= sb) x row
+  // chunks, in TA.  Its diagonal gives lambda, and G^(n) = Ghat / (lambda lambda^T).
   if (t < L::RCN * L::NBLK) {
     const int blk = t % L::NBLK, ch = t / L::NBLK;
     int rb, sb;
@@ -445,50 +472,88 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
     for (int e = 0; e < 16; ++e) tp[(ch * L::NBLK + blk) * 16 + e] = acc[e];
   }
   __syncthreads();
-  // combine the chunks (in TA) and push each pair to its owner CTA (p % MC_CS)
+  cluster_wait();  // pairs with the arrive at kernel start: every CTA is running
+  // combine the chunks (in TA); the diagonal goes to every CTA (lambda), the
+  // other pairs to their owner (p % MC_CS); beta to CTA 0
   for (int p = t; p < L::NP; p += MC_NT) {
     int r, s;
     tri_unpack(p, RP, r, s);
     const int blk = tri_index(r / 4, s / 4, L::NB), e = (r % 4) * 4 + (s % 4);
     TA ga = TA(0);
     for (int ch = 0; ch < L::RCN; ++ch) ga += tp[(ch * L::NBLK + blk) * 16 + e];
-    st_cluster(g_slot + c * L::NPO + p / MC_CS, (uint32_t)(p % MC_CS), (double)ga);
+    if (r == s) {
+      for (uint32_t dst = 0; dst < MC_CS; ++dst) st_cluster(cs_slot + c * RP + r, dst, (double)ga);
+    } else {
+      st_cluster(g_slot + c * L::NPO + p / MC_CS, (uint32_t)(p % MC_CS), (double)ga);
+    }
+  }
+  if (t == 0) {
+    double b = 0.0;
+    for (int w = 0; w < MC_NT / 32; ++w) b += red[w];
+    st_cluster(beta_slot + c, 0, b);
   }
   cluster_arrive();
   cluster_wait();
 
-  // ---- owned pairs: G^(n) entries (FP64 across the CTAs), and the gamma
-  // partial of the error identity with the FP64 entry of S^(n)
+  // ---- lambda (identical in every CTA: same slots, same order)
+  if (t < RP) {
+    const double s = slot_sum(cs_slot + t, RP);
+    double l = 0.0, il = 0.0;  // a zero column keeps lambda = 0 and stays zero
+    if (t < R) sqrt_and_inv(s, l, il);
+    s_lam[t] = l;
+    s_il[t] = il;
+    s_inv[t] = (TA)il;
+    if (c == 0 && t < R) lam[t] = l;
+  }
+  __syncthreads();
+  // ---- H = Hhat diag(lambda)^-1 for this CTA's rows (coalesced write)
+  {
+    int a = a_0, k = k_0;
+#pragma unroll 4
+    for (int e = t; e < nel; e += MC_NT) {
+      Hrow[e] = Hs[S::idx(a, k)] * s_inv[k];
+      a += q_step;
+      k += k_step;
+      if (k >= R) {
+        k -= R;
+        ++a;
+      }
+    }
+  }
+  // ---- owned pair: G^(n)(r, s) = Ghat(r, s) / (lambda_r lambda_s); gamma
+  // partial lambda^T (S * G^(n)) lambda = sum S(r, s) Ghat(r, s)
   double gam = 0.0;
-  double* Gn = G + (size_t)n * RR;
-  float* Gnf = Gf + (size_t)n * RR;
-  for (int j = t; j < L::NPO; j += MC_NT) {
-    const int p = j * MC_CS + (int)c;
-    if (p >= L::NP) break;
-    int r, s;
-    tri_unpack(p, RP, r, s);
-    if (s >= R) continue;
-    double g = 0.0;
-    for (int src = 0; src < MC_CS; ++src) g += g_slot[src * L::NPO + j];
+  if (owns) {
+    const int r = r_own, s = s_own;
+    double gh = 0.0;
+    gh = r == s ? slot_sum(cs_slot + r, RP) : slot_sum(g_slot + t, L::NPO);
+    const double g = gh * s_il[r] * s_il[s];
+    double* Gn = G + (size_t)n * RR;
+    float* Gnf = Gf + (size_t)n * RR;
     Gn[r * R + s] = g;
     Gn[s * R + r] = g;
     Gnf[r * R + s] = (float)g;
     Gnf[s * R + r] = (float)g;
     if (fit_out) {
       double sv = 1.0;
-      for (int q = 0; q < N; ++q)
-        if (q != n) sv *= G[(size_t)q * RR + r * R + s];
-      gam += (r == s ? 1.0 : 2.0) * s_lam[r] * s_lam[s] * sv * g;
+      if (pre) {
+#pragma unroll
+        for (int qi = 0; qi < QPRE; ++qi) sv *= gq[qi];
+      } else {
+        for (int q = 0; q < N; ++q)
+          if (q != n) sv *= G[(size_t)q * RR + r * R + s];
+      }
+      gam = (r == s ? 1.0 : 2.0) * sv * gh;
     }
   }
   if (c == 0 && t == 0 && inner) *inner = alg == PLANC_PGD ? pgd_steps : 1;
   if (!fit_out) return;  // uniform over the cluster: no remote access follows
   gam = warp_sum(gam);
-  if ((t & 31) == 0) red[MC_NT + 4 + (t >> 5)] = gam;
+  if ((t & 31) == 0) red[4 + (t >> 5)] = gam;
   __syncthreads();
   if (t == 0) {
     double s = 0.0;
-    for (int w = 0; w < MC_NT / 32; ++w) s += red[MC_NT + 4 + w];
+    for (int w = 0; w < MC_NT / 32; ++w) s += red[4 + w];
     st_cluster(gam_slot + c, 0, s);
   }
   cluster_arrive();
@@ -511,7 +576,7 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
 template <typename TA, int RP>
 cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const void* M, void* H,
                    double* lam, planc_nls_t alg, const planc_nls_opts& o, int32_t* inner,
-                   const double* alpha, double* fit_out, cudaStream_t st) {
+                   const double* alpha, double* fit_out, int* err, cudaStream_t st) {
   const size_t smem = McLayout<TA, RP>::bytes;
   auto kern = mode_cluster_kernel<TA, RP>;
   cudaError_t e =
@@ -531,7 +596,7 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, kern, rows, R, N, n, G, Gf, (const TA*)M, (TA*)H, lam, (int)alg,
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
-                         inner, alpha, fit_out);
+                         inner, alpha, fit_out, err);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -546,17 +611,17 @@ bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R) {
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, cudaStream_t st) {
+                              double* fit_out, int* err, cudaStream_t st) {
   const int r = (int)rows;
   double* Gw = const_cast<double*>(G);
   if (f64) {
     if (R <= 16)
-      return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, st);
-    return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, st);
+      return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
+    return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
   }
   if (R <= 16)
-    return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, st);
-  return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, st);
+    return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
+  return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
 }
 
 }  // namespace planc

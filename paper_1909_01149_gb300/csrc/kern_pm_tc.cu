@@ -782,6 +782,7 @@ struct TcrParams {
   int64_t jdim;         // right: L / d_in
   int out_mode;         // 0: out[m + Mdim r]; 1: out[m R + r]; 2: partial slice z
   int64_t Mdim;         // rows of the final output (left L, right C)
+  int aslots;           // FP32: TMEM slots for the converted X tiles (<= F_A_SLOTS)
   float* out;
   int* err;
   const float* Hin;     // resident factor, d_in x R row-major
@@ -790,6 +791,7 @@ struct TcrParams {
 
 // weights W[o, r] = prod_m Hw_m[o_m, r] for r < R (o enumerates the weight
 // modes, fastest first)
+template <int RBX>
 __device__ __forceinline__ void tcr_weights(const TcrParams& p, int64_t o, float* w) {
   int idx[TC_MAXM];
   uint32_t k = (uint32_t)o;
@@ -805,7 +807,7 @@ __device__ __forceinline__ void tcr_weights(const TcrParams& p, int64_t o, float
     }
   }
 #pragma unroll
-  for (int r4 = 0; r4 < 16; ++r4) {
+  for (int r4 = 0; r4 < RBX / 4; ++r4) {
     float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
     if (4 * r4 < p.R) {
 #pragma unroll
@@ -844,7 +846,8 @@ __device__ __forceinline__ float warp_reduce_scatter32(float* v, int lane) {
   return v[0];
 }
 
-template <bool LEFT, bool F32>
+// RBX: 32 or 64, the register arrays of the epilogue hold RBX columns (RB <= RBX)
+template <bool LEFT, bool F32, int RBX>
 __global__ void __launch_bounds__(F32 ? 320 : 192, 1)
 pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcrParams p) {
   constexpr int BKX = F32 ? F_BK : BK;             // reduction elements per stage
@@ -889,6 +892,19 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     *abort = 0;
     fence_mbar_init();
   }
+  // H_in (d_in x R, row-major FP32) arrives by one bulk copy into the X stage
+  // area (idle until the pipeline starts) when aligned and small enough; the
+  // image below is then built from shared memory
+  uint64_t* hbar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(red) + 1024);
+  const uint32_t hbytes = (uint32_t)((int64_t)p.d_in * p.R * 4);
+  const bool hbulk = (hbytes & 15u) == 0 && (reinterpret_cast<uintptr_t>(p.Hin) & 15u) == 0 &&
+                     (size_t)hbytes <= (size_t)stages * XST;
+  if (hbulk && threadIdx.x == 0) {
+    mbar_init(hbar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(hbar, hbytes);
+    bulk_g2s(Xs, p.Hin, hbytes, hbar);
+  }
   if (warp == W_MMA) {
     tmem_alloc(tmem_slot, TMEM_COLS);
     tmem_relinquish();
@@ -896,25 +912,42 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   // the resident B image: stage j holds rows j*BKX .. j*BKX+BKX-1 of H_in
   // as split terms, K-major, 128-byte swizzled
   {
-    const int64_t total = (int64_t)p.nst * BKX * RB;
-    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-      const int r = (int)(e % RB);
-      const int k = (int)(e / RB);
-      const int j = k / BKX, kk = k - j * BKX;
-      const float v = (k < p.d_in && r < p.R) ? __ldg(p.Hin + (int64_t)k * p.R + r) : 0.f;
-      uint8_t* b = Bimg + (size_t)j * bstage;
-      if (F32) {
-        const float hi = tf32_rn(v);
-        *reinterpret_cast<float*>(b + sw128_off32(r, kk)) = hi;
-        *reinterpret_cast<float*>(b + sw128_off32(RB + r, kk)) = tf32_rn(v - hi);
-      } else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const float r1 = v - __bfloat162float(hi);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(r, kk)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(RB + r, kk)) = mid;
-        *reinterpret_cast<__nv_bfloat16*>(b + sw128_off(2 * RB + r, kk)) =
-            __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    const float* hsrc = p.Hin;
+    if (hbulk) {
+      __syncthreads();  // hbar initialised
+      mbar_wait(hbar, 0, abort, p.err, 28);
+      hsrc = reinterpret_cast<const float*>(Xs);
+    }
+    const int total = p.nst * BKX * RB;
+    constexpr int BATCH = 8;  // loads issued together (global fallback)
+    for (int e0 = threadIdx.x; e0 < total; e0 += BATCH * (int)blockDim.x) {
+      float v[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        const int k = e / RB, r = e - (e / RB) * RB;
+        v[u] = (e < total && k < p.d_in && r < p.R) ? hsrc[k * p.R + r] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        if (e >= total) break;
+        const int k = e / RB, r = e - (e / RB) * RB;
+        const int j = k / BKX, kk = k - j * BKX;
+        uint8_t* bb = Bimg + (size_t)j * bstage;
+        if (F32) {
+          const float hi = tf32_rn(v[u]);
+          *reinterpret_cast<float*>(bb + sw128_off32(r, kk)) = hi;
+          *reinterpret_cast<float*>(bb + sw128_off32(RB + r, kk)) = tf32_rn(v[u] - hi);
+        } else {
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v[u]);
+          const float r1 = v[u] - __bfloat162float(hi);
+          const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+          *reinterpret_cast<__nv_bfloat16*>(bb + sw128_off(r, kk)) = hi;
+          *reinterpret_cast<__nv_bfloat16*>(bb + sw128_off(RB + r, kk)) = mid;
+          *reinterpret_cast<__nv_bfloat16*>(bb + sw128_off(2 * RB + r, kk)) =
+              __float2bfloat16_rn(r1 - __bfloat162float(mid));
+        }
       }
     }
     fence_proxy_async_smem();
@@ -923,7 +956,11 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t d_col0 = F32 ? F_A_SLOTS * 64 : 0;
+  // FP32: p.aslots TMEM slots of 64 columns (x hi | x lo), then two
+  // accumulator buffers [hi (RB) | lo (RB)]: x_hi [k_hi | k_lo] lands on both,
+  // x_lo k_hi on the lo half.  BF16: buffers of 256 columns [hi | mid | lo].
+  const int aslots = F32 ? p.aslots : 1;
+  const uint32_t d_col0 = F32 ? (uint32_t)aslots * 64u : 0u;
   const uint32_t d_stride = F32 ? (uint32_t)(2 * RB) : 256u;
 
   // Work item layout.  Left: item = (128-row tile of L, range of outer
@@ -1020,7 +1057,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                     acc = 1;
                   }
                   mma_commit(&a_empty[as]);
-                  if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
+                  if (++as == aslots) { as = 0; aph ^= 1; }
                 } else {
                   const uint32_t a0 = smem_u32(Xs + (size_t)s * XST);
 #pragma unroll
@@ -1100,7 +1137,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_full[as]);
             if (++s == stages) { s = 0; ph ^= 1; }
-            if (++as == F_A_SLOTS) { as = 0; aph ^= 1; }
+            if (++as == aslots) { as = 0; aph ^= 1; }
           }
         }
       }
@@ -1113,18 +1150,18 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     int buf = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
-      float sum[64];
+      float sum[RBX];
 #pragma unroll
-      for (int r = 0; r < 64; ++r) sum[r] = 0.f;
+      for (int r = 0; r < RBX; ++r) sum[r] = 0.f;
       for (int u = 0; u < nsub && ok; ++u) {
-        float w[64];
+        float w[RBX];
         if (!LEFT) {
           // row (j, c) of this tile carries the weight W[j]
           const int64_t jrow = (tile_m0(it, u) + row) % p.jdim;
-          if (p.W.nm > 0) tcr_weights(p, jrow, w);
+          if (p.W.nm > 0) tcr_weights<RBX>(p, jrow, w);
         }
         for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
-          if (LEFT && p.W.nm > 0) tcr_weights(p, o, w);
+          if (LEFT && p.W.nm > 0) tcr_weights<RBX>(p, o, w);
           const bool weighted = p.W.nm > 0;
           for (int g0 = 0; g0 < p.nst; g0 += SEG_STAGES) {
             if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 27)) { ok = false; break; }
@@ -1133,19 +1170,26 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
             const uint32_t taddr =
                 tmem + d_col0 + (uint32_t)buf * d_stride + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < RBX / 16; ++c) {
               if (c * 16 < RB) {
-                float h[16], t1[16], t2[16];
-                tmem_ld16(taddr + c * 16, h);
+                float v[16], t1[16];
+                tmem_ld16(taddr + c * 16, v);
                 tmem_ld16(taddr + RB + c * 16, t1);
-                if (!F32) tmem_ld16(taddr + 2 * RB + c * 16, t2);
-                tmem_ld_wait();
+                if (F32) {
+                  tmem_ld_wait();
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                  const float v = F32 ? h[jj] + t1[jj] : h[jj] + (t1[jj] + t2[jj]);
-                  sum[c * 16 + jj] = weighted ? fmaf(v, w[c * 16 + jj], sum[c * 16 + jj])
-                                              : sum[c * 16 + jj] + v;
+                  for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj];
+                } else {
+                  float t2[16];
+                  tmem_ld16(taddr + 2 * RB + c * 16, t2);
+                  tmem_ld_wait();
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj] + t2[jj];
                 }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                  sum[c * 16 + jj] = weighted ? fmaf(v[jj], w[c * 16 + jj], sum[c * 16 + jj])
+                                              : sum[c * 16 + jj] + v[jj];
               }
             }
             tc_fence_before();
@@ -1169,14 +1213,14 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
             stride = p.Mdim;
           }
 #pragma unroll
-          for (int r = 0; r < 64; ++r)
+          for (int r = 0; r < RBX; ++r)
             if (r < p.R) base[r * stride] = sum[r];
         }
       } else {
         // sum the item's rows (one output row c): reduce-scatter within the
         // warp (lane r ends with column r), then across the four warps
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < RBX / 32; ++h) {
           if (32 * h < p.R) {
             const float v = warp_reduce_scatter32(sum + 32 * h, lane);
             red[q * 64 + 32 * h + lane] = v;
@@ -1330,7 +1374,7 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
   const size_t xst = (size_t)BM * bk * e;
   const size_t budget = 227 * 1024 - 256;
   for (int st = 6; st >= 3; --st) {
-    const size_t total = 1024 + st * xst + bimg + (2 * st + 2 * F_A_SLOTS + 5) * 8 + 16 + 1024;
+    const size_t total = 1024 + st * xst + bimg + (2 * st + 2 * F_A_SLOTS + 5) * 8 + 16 + 1024 + 16;
     if (total <= budget) {
       pl.stages = st;
       pl.smem = total;
@@ -1395,6 +1439,8 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   p.tpi = pl.tpc / pl.nsplit;
   p.jdim = pl.jdim;
   p.Mdim = left ? L : C;
+  // TMEM: aslots x 64 A columns + 2 buffers x 2 RB accumulator columns <= 512
+  p.aslots = 4;
   p.err = err_flag;
   p.Hin = (const float*)kh.H[0];
   p.W.nm = kh.nm - 1;
@@ -1437,8 +1483,11 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int threads = f32 ? 320 : 192;
   cudaError_t err;
-  auto k = left ? (f32 ? pm_tcr_kernel<true, true> : pm_tcr_kernel<true, false>)
-                : (f32 ? pm_tcr_kernel<false, true> : pm_tcr_kernel<false, false>);
+  auto k = pl.RB <= 32
+               ? (left ? (f32 ? pm_tcr_kernel<true, true, 32> : pm_tcr_kernel<true, false, 32>)
+                       : (f32 ? pm_tcr_kernel<false, true, 32> : pm_tcr_kernel<false, false, 32>))
+               : (left ? (f32 ? pm_tcr_kernel<true, true, 64> : pm_tcr_kernel<true, false, 64>)
+                       : (f32 ? pm_tcr_kernel<false, true, 64> : pm_tcr_kernel<false, false, 64>));
   err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 148;

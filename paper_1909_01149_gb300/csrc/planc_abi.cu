@@ -583,7 +583,7 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
     if (ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R)) {
       // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after mode N)
       CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n], ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
-                           last ? ctx->scal + 8 : nullptr, ctx->stream),
+                           last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->stream),
          "fused mode update launch");
       continue;
     }
@@ -744,7 +744,8 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
     }
   }
   if (tc_err != 0)
-    return fail(ctx, PLANC_E_TIMEOUT, "a tensor-core pipeline wait gave up (code %d)", tc_err);
+    return fail(ctx, PLANC_E_TIMEOUT,
+                "a pipeline wait gave up (code %d: 1-3 partial MTTKRP, 10 mode update)", tc_err);
   if (flags[1] != 0) return fail(ctx, PLANC_E_NUMERIC, "BPP met a non-positive pivot in %d rows", flags[1]);
   return PLANC_OK;
 }
