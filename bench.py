@@ -8,7 +8,8 @@ NNLS update, normalisation, Gram) per mode and the error identity (all rows
 of the hot path).  value = outer iterations per second over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl planc|reference]
-                  [--config c2|c3|c1] [--alg hals|mu|admm|bpp|pgd]
+                  [--config c2|c3|c1|c4] [--alg hals|mu|admm|bpp|pgd]
+                  [--mode solve|pm|grad]
                   [--no-mixed] [--no-cpu-baseline]
 
 --impl reference times the FP64 NumPy oracle on the host cores (bounded
@@ -43,6 +44,10 @@ CONFIGS = {
     # 64^3 FP64, R = 8, HALS, 20 iterations
     "c1": dict(workload="nncp-dense-3way-64x64x64-fp64-R8", dims=(64, 64, 64), R=8,
                dtype="f64", alg="hals", iters=20, noise=0.01, kind="planted"),
+    # 96^4 FP32, R = 64: CP-loss gradient (--mode grad) and 100 projected-gradient
+    # outer iterations (the solve with the PGD update)
+    "c4": dict(workload="nncp-dense-4way-96x96x96x96-fp32-R64", dims=(96, 96, 96, 96), R=64,
+               dtype="f32", alg="pgd", iters=100, noise=0.01, kind="planted"),
 }
 METRIC = "NNCP outer iterations/s (+ partial-MTTKRP HBM GB/s)"
 
@@ -354,6 +359,37 @@ def run_pm_only(args, cfg):
     return out, 0
 
 
+def run_grad(args, cfg):
+    """Time planc_cp_grad (loss and all N factor gradients; two passes over X
+    through the root partial MTTKRPs, multi-TTV chains, Grams, H S - M)."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    torch.cuda.set_device(0)
+    X, H0 = make_inputs(cfg)
+    dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cfg["dtype"]]
+    fdt = torch.float64 if cfg["dtype"] == "f64" else torch.float32
+    Xd = torch.from_numpy(synth.flat(X)).to(dt).cuda()
+    H = [torch.from_numpy(h).to(fdt).cuda() for h in H0]
+    ctx = planc.Context(Xd, cfg["dims"], cfg["R"])
+    dH = [torch.empty_like(h) for h in H]
+    for _ in range(args.warmup):
+        loss, _ = ctx.cp_grad(H, dH)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss, _ = ctx.cp_grad(H, dH)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    xb = {"f32": 4, "f64": 8, "bf16": 2}[cfg["dtype"]]
+    nbytes = 2 * int(np.prod(cfg["dims"])) * xb
+    out = {"mode": "grad", "workload": cfg["workload"], "grads_per_s": round(1.0 / sec, 2),
+           "ms_per_grad": round(sec * 1e3, 4), "x_pass_bytes": nbytes,
+           "x_GBps": round(nbytes / sec / 1e9, 1), "loss": loss, "tc_mask": ctx.tc_mask,
+           "note": "host-timed per call (each call synchronises to return the loss)"}
+    ctx.close()
+    return out, 0
+
+
 def run_mixed(args):
     """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP), equal
     iterations from the same initial factors.  'fp32_same_values' stores the
@@ -466,8 +502,9 @@ def main():
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "pm"],
-                    help="pm: time only the two partial MTTKRPs (profiling aid)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad"],
+                    help="pm: time only the two partial MTTKRPs (profiling aid); "
+                         "grad: time the CP-loss gradient (config c4)")
     ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
@@ -489,6 +526,10 @@ def main():
                                                      cfg["dtype"], cfg["R"])
     if args.mode == "pm":
         out, rank = run_pm_only(args, cfg)
+    elif args.mode == "grad":
+        if args.config == "c2" and not (args.dims or args.rank or args.dtype):
+            cfg = dict(CONFIGS["c4"])
+        out, rank = run_grad(args, cfg)
     elif args.impl == "reference":
         out, rank = run_reference(args, cfg)
     else:

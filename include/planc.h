@@ -248,11 +248,15 @@ planc_solve_opts planc_solve_opts_default(void);
 /* CP reconstruction loss f = ||X - [[H^(1..N)]]||^2 (Eq. nncp objective,
  * lambda = 1) and its gradient df/dH^(n) = 2 (H^(n) S^(n) - M^(n)) for every
  * mode (the MTTKRP and Hadamard-of-Grams matrices of Alg. 1).  H and dH:
- * host arrays of N device pointers (dH row-major I_n x R, caller-owned).
- * loss: HOST double (may be NULL).  The two root partial MTTKRPs are each
- * computed once from the given factors (2 passes over X for any N) and the
- * multi-TTV chains are recomputed per mode, nothing else is stored.
- * Synchronises the stream. */
+ * host arrays of N device pointers (dH row-major I_n x R in the factor dtype,
+ * caller-owned, overwritten).  loss: HOST double, or NULL to skip the loss.
+ * The two root partial MTTKRPs are each computed once from the given factors
+ * (2 passes over X for any N) and the multi-TTV chains are recomputed per
+ * mode; nothing else is stored.  The loss uses the identity
+ * f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1, evaluated in
+ * FP64.  Overwrites the context's lambda buffer (the next solve resets it).
+ * Asynchronous when loss is NULL; synchronises the stream otherwise.
+ * Errors: PLANC_E_INVALID (NULL pointers), PLANC_E_UNSUPPORTED (R > 64). */
 planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,
                              double* loss);
 

@@ -95,6 +95,8 @@ cudaError_t launch_fit(int R, const double* Gall, int N, const double* lambda,
 cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, const void* H,
                               const double* lambda, double* dot_part, int nblk,
                               cudaStream_t st);
+cudaError_t launch_cp_grad_rows(bool f64, int64_t rows, int R, const void* H, const double* S,
+                                void* G, cudaStream_t st);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st);
 
 // ---- NNLS updates (Sec. 4.3) ---------------------------------------------------

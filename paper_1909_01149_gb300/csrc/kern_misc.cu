@@ -250,6 +250,30 @@ dot_lambda_kernel(int64_t rows, int R, int64_t rb, const TA* __restrict__ M,
   }
 }
 
+// ---- CP-loss gradient (Eq. nncp objective) -------------------------------------------
+// G[i, r] <- 2 (sum_k H[i, k] S[k, r] - G[i, r]) for an I x R block whose G
+// holds M^(n) on entry: df/dH^(n) = 2 (H^(n) S^(n) - M^(n)).  S (R x R, FP64)
+// is staged in shared memory in the factor precision.
+template <typename TA>
+__global__ void __launch_bounds__(256)
+cp_grad_rows_kernel(int64_t rows, int R, const TA* __restrict__ H, const double* __restrict__ S,
+                    TA* __restrict__ G) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  TA* Ss = reinterpret_cast<TA*>(cg_smem);
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ss[e] = (TA)S[e];
+  __syncthreads();
+  const int64_t total = rows * (int64_t)R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int r = (int)(e - i * R);
+    const TA* h = H + i * R;
+    TA acc = TA(0);
+    for (int k = 0; k < R; ++k) acc = fma(h[k], Ss[k * R + r], acc);
+    G[e] = TA(2) * (acc - G[e]);
+  }
+}
+
 __global__ void fill_kernel(double* p, double v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -358,6 +382,20 @@ cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, cons
     dot_lambda_kernel<float><<<nblk, 256, 0, st>>>(rows, R, rb, (const float*)M,
                                                    (const float*)H, lambda, dot_part);
     note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cp_grad_rows(bool f64, int64_t rows, int R, const void* H, const double* S,
+                                void* G, cudaStream_t st) {
+  const int64_t total = rows * (int64_t)R;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+  if (f64)
+    cp_grad_rows_kernel<double><<<blocks, 256, (size_t)R * R * 8, st>>>(
+        rows, R, (const double*)H, S, (double*)G);
+  else
+    cp_grad_rows_kernel<float><<<blocks, 256, (size_t)R * R * 4, st>>>(
+        rows, R, (const float*)H, S, (float*)G);
+  note_launches(1);
   return cudaGetLastError();
 }
 

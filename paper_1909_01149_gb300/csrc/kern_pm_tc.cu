@@ -783,6 +783,10 @@ struct TcrParams {
   int out_mode;         // 0: out[m + Mdim r]; 1: out[m R + r]; 2: partial slice z
   int64_t Mdim;         // rows of the final output (left L, right C)
   int aslots;           // FP32: TMEM slots for the converted X tiles (<= F_A_SLOTS)
+  int blockmode;        // right branch with L / d_in a multiple of 32 but not of 128:
+                        // items are runs of tpi tiles; each 32-row block (one c)
+                        // writes its weighted row sum to out[block * R + r]
+  int64_t nblocks;      // blockmode: rows / 32
   float* out;
   int* err;
   const float* Hin;     // resident factor, d_in x R row-major
@@ -791,41 +795,52 @@ struct TcrParams {
 
 // weights W[o, r] = prod_m Hw_m[o_m, r] for r < R (o enumerates the weight
 // modes, fastest first)
-template <int RBX>
-__device__ __forceinline__ void tcr_weights(const TcrParams& p, int64_t o, float* w) {
-  int idx[TC_MAXM];
+// Rows of the weight factors for outer index o (o enumerates the weight
+// modes, fastest first): W[o, r] = prod_m row_m[r].
+__device__ __forceinline__ void tcr_rows(const TcrParams& p, int64_t o, const float** row) {
   uint32_t k = (uint32_t)o;
 #pragma unroll
   for (int m = 0; m < TC_MAXM; ++m) {
     if (m < p.W.nm) {
       const uint32_t d = (uint32_t)p.W.dim[m];
       const uint32_t q = k / d;
-      idx[m] = (int)(k - q * d);
+      row[m] = p.W.H[m] + (int64_t)(k - q * d) * p.R;
       k = q;
     } else {
-      idx[m] = 0;
+      row[m] = nullptr;
     }
   }
+}
+
+// weights of columns col .. col + 3 (1 past R)
+__device__ __forceinline__ float4 tcr_w4(const TcrParams& p, const float* const* row, int col) {
+  float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (col < p.R) {
 #pragma unroll
-  for (int r4 = 0; r4 < RBX / 4; ++r4) {
-    float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
-    if (4 * r4 < p.R) {
-#pragma unroll
-      for (int m = 0; m < TC_MAXM; ++m) {
-        if (m < p.W.nm) {
-          const float* row = p.W.H[m] + (int64_t)idx[m] * p.R + 4 * r4;
-          if ((p.R & 3) == 0) {
-            const float4 h = __ldg(reinterpret_cast<const float4*>(row));
-            v.x *= h.x; v.y *= h.y; v.z *= h.z; v.w *= h.w;
-          } else {
-            v.x *= __ldg(row);
-            if (4 * r4 + 1 < p.R) v.y *= __ldg(row + 1);
-            if (4 * r4 + 2 < p.R) v.z *= __ldg(row + 2);
-            if (4 * r4 + 3 < p.R) v.w *= __ldg(row + 3);
-          }
+    for (int m = 0; m < TC_MAXM; ++m) {
+      if (m < p.W.nm) {
+        const float* rr = row[m] + col;
+        if ((p.R & 3) == 0) {
+          const float4 h = __ldg(reinterpret_cast<const float4*>(rr));
+          v.x *= h.x; v.y *= h.y; v.z *= h.z; v.w *= h.w;
+        } else {
+          v.x *= __ldg(rr);
+          if (col + 1 < p.R) v.y *= __ldg(rr + 1);
+          if (col + 2 < p.R) v.z *= __ldg(rr + 2);
+          if (col + 3 < p.R) v.w *= __ldg(rr + 3);
         }
       }
     }
+  }
+  return v;
+}
+
+// weights of columns 16 c .. 16 c + 15
+__device__ __forceinline__ void tcr_w16(const TcrParams& p, const float* const* row, int c,
+                                        float* w) {
+#pragma unroll
+  for (int r4 = 0; r4 < 4; ++r4) {
+    const float4 v = tcr_w4(p, row, 16 * c + 4 * r4);
     w[4 * r4 + 0] = v.x; w[4 * r4 + 1] = v.y; w[4 * r4 + 2] = v.z; w[4 * r4 + 3] = v.w;
   }
 }
@@ -968,6 +983,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   const int nsub = LEFT ? 1 : p.tpi;
   auto tile_m0 = [&](int64_t it, int u) -> int64_t {
     if (LEFT) return (it % p.m_tiles) * BM;
+    if (p.blockmode) return (it * p.tpi + u) * BM;
     const int64_t c = it / p.nsplit, z = it % p.nsplit;
     return ((c * p.tpc) + z * p.tpi + u) * BM;
   };
@@ -1154,15 +1170,34 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
 #pragma unroll
       for (int r = 0; r < RBX; ++r) sum[r] = 0.f;
       for (int u = 0; u < nsub && ok; ++u) {
-        float w[RBX];
-        if (!LEFT) {
-          // row (j, c) of this tile carries the weight W[j]
+        if (!LEFT && p.blockmode) {
+#pragma unroll
+          for (int r = 0; r < RBX; ++r) sum[r] = 0.f;
+        }
+        // Weights.  Left: W[o] is the same for every row of the tile; one warp
+        // stages it in shared memory before the accumulator wait.  Right: row
+        // (j, c) carries W[j]; held in registers for RBX = 32, read per
+        // 16-column chunk for RBX = 64 (register budget).
+        const float* wrow[TC_MAXM];
+        float wreg[RBX == 32 ? 32 : 1];
+        const bool weighted = p.W.nm > 0;
+        if (!LEFT && weighted) {
           const int64_t jrow = (tile_m0(it, u) + row) % p.jdim;
-          if (p.W.nm > 0) tcr_weights<RBX>(p, jrow, w);
+          tcr_rows(p, jrow, wrow);
+          if constexpr (RBX == 32) {
+            tcr_w16(p, wrow, 0, wreg);
+            tcr_w16(p, wrow, 1, wreg + 16);
+          }
         }
         for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
-          if (LEFT && p.W.nm > 0) tcr_weights<RBX>(p, o, w);
-          const bool weighted = p.W.nm > 0;
+          float* ws = red + (o & 1) * 64;
+          if (LEFT && weighted) {
+            if (warp == W_EPI && lane < RBX / 4) {
+              tcr_rows(p, o, wrow);
+              *reinterpret_cast<float4*>(ws + 4 * lane) = tcr_w4(p, wrow, 4 * lane);
+            }
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+          }
           for (int g0 = 0; g0 < p.nst; g0 += SEG_STAGES) {
             if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 27)) { ok = false; break; }
             fph ^= 1u << buf;
@@ -1186,16 +1221,41 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
 #pragma unroll
                   for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj] + t2[jj];
                 }
+                if (weighted) {
+                  float w[16];
+                  if (LEFT) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj)
-                  sum[c * 16 + jj] = weighted ? fmaf(v[jj], w[c * 16 + jj], sum[c * 16 + jj])
-                                              : sum[c * 16 + jj] + v[jj];
+                    for (int jj = 0; jj < 16; ++jj) w[jj] = ws[c * 16 + jj];
+                  } else if constexpr (RBX == 32) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) w[jj] = wreg[c * 16 + jj];
+                  } else {
+                    tcr_w16(p, wrow, c, w);
+                  }
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) sum[c * 16 + jj] = fmaf(v[jj], w[jj], sum[c * 16 + jj]);
+                } else {
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) sum[c * 16 + jj] += v[jj];
+                }
               }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
             buf ^= 1;
+          }
+        }
+        if (!LEFT && p.blockmode && ok) {
+          // this warp's 32 rows lie in one c: reduce-scatter them (lane r
+          // ends with column r) and write the block's partial row
+          const int64_t blk = (tile_m0(it, u) + q * 32) / 32;
+#pragma unroll
+          for (int h = 0; h < RBX / 32; ++h) {
+            if (32 * h < p.R) {
+              const float v = warp_reduce_scatter32(sum + 32 * h, lane);
+              if (blk < p.nblocks && 32 * h + lane < p.R) p.out[blk * p.R + 32 * h + lane] = v;
+            }
           }
         }
       }
@@ -1216,7 +1276,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
           for (int r = 0; r < RBX; ++r)
             if (r < p.R) base[r * stride] = sum[r];
         }
-      } else {
+      } else if (!p.blockmode) {
         // sum the item's rows (one output row c): reduce-scatter within the
         // warp (lane r ends with column r), then across the four warps
 #pragma unroll
@@ -1247,6 +1307,20 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   }
 }
 
+// out[c, r] = sum over the bpc consecutive 32-row blocks of c of part[b, r]
+// (fixed order, FP64 accumulation)
+__global__ void block_reduce_kernel(const float* __restrict__ part, int64_t bpc, int64_t C, int R,
+                                    float* __restrict__ out, int rowmajor) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= C * R) return;
+  const int64_t c = e / R;
+  const int r = (int)(e - c * R);
+  double s = 0.0;
+  for (int64_t b = 0; b < bpc; ++b) s += (double)part[(c * bpc + b) * R + r];
+  if (rowmajor) out[c * R + r] = (float)s;
+  else out[c + C * r] = (float)s;
+}
+
 // ---- host side -------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1264,6 +1338,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+cudaError_t launch_block_reduce(const void* part, int64_t bpc, int64_t C, int R, void* out,
+                                bool rowmajor, cudaStream_t st) {
+  const int64_t n = C * R;
+  block_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      (const float*)part, bpc, C, R, (float*)out, rowmajor ? 1 : 0);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 // Shared-memory plan: pipeline depth and whether the first Khatri-Rao
 // factor (h0_bytes) is staged in shared memory (kept only if at least four
@@ -1326,6 +1409,8 @@ struct TcrPlan {
   int64_t d_in = 0, n_out = 1, jdim = 1, rows = 0, m_tiles = 0, o_span = 1, items = 0;
   int tpc = 1, nsplit = 1;
   int64_t splits = 1;   // partial slices summed afterwards (left: outer splits, right: nsplit)
+  bool blockmode = false;
+  int64_t nblocks = 0;  // blockmode: 32-row blocks (partial rows in the workspace)
   size_t smem = 0;
 };
 
@@ -1358,9 +1443,23 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
   } else {
     if ((pl.d_in * e) % 16 != 0) return pl;
     pl.jdim = L / pl.d_in;
-    if (pl.jdim % BM != 0) return pl;
     pl.rows = pl.jdim * C;
     if (pl.rows >= (1LL << 31)) return pl;
+    if (pl.jdim % BM != 0) {
+      // block mode: every 32-row block lies in one output row c
+      if (pl.jdim % 32 != 0) return pl;
+      pl.blockmode = true;
+      pl.m_tiles = (pl.rows + BM - 1) / BM;
+      pl.nblocks = pl.rows / 32;
+      const int64_t target = std::max<int64_t>(1, pl.m_tiles / (4LL * sm_count));
+      int64_t tpi = 1;
+      for (int64_t d = 1; d <= target; ++d)
+        if (pl.m_tiles % d == 0) tpi = d;
+      pl.tpc = (int)tpi;
+      pl.nsplit = 1;
+      pl.splits = 1;
+      pl.items = pl.m_tiles / tpi;
+    } else {
     pl.m_tiles = pl.rows / BM;
     pl.tpc = (int)(pl.jdim / BM);
     // items per output row c: enough items for ~4 per SM, dividing tpc
@@ -1370,6 +1469,7 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
     pl.nsplit = ns;
     pl.splits = ns;
     pl.items = C * ns;
+    }
   }
   const size_t xst = (size_t)BM * bk * e;
   const size_t budget = 227 * 1024 - 256;
@@ -1407,7 +1507,10 @@ size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C,
                              const KrpHost& kh, int sm_count) {
   if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return 0;
   const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
-  if (pl.ok) return pl.splits > 1 ? (size_t)pl.splits * (left ? L : C) * R * sizeof(float) : 0;
+  if (pl.ok) {
+    if (pl.blockmode) return (size_t)pl.nblocks * R * sizeof(float);
+    return pl.splits > 1 ? (size_t)pl.splits * (left ? L : C) * R * sizeof(float) : 0;
+  }
   const int64_t Mdim = left ? L : C, Kdim = left ? C : L;
   const int64_t span = item_kspan(Mdim, Kdim, sm_count, stage_bk(xdt), stage_max_k(xdt));
   const int64_t splits = (Kdim + span - 1) / span;
@@ -1449,7 +1552,13 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
     p.W.dim[m - 1] = kh.dim[m];
     p.W.H[m - 1] = (const float*)kh.H[m];
   }
-  if (pl.splits > 1) {
+  p.blockmode = pl.blockmode ? 1 : 0;
+  p.nblocks = pl.nblocks;
+  if (pl.blockmode) {
+    if (work_bytes < (size_t)pl.nblocks * R * sizeof(float)) return cudaErrorInvalidValue;
+    p.out_mode = 3;
+    p.out = (float*)work;
+  } else if (pl.splits > 1) {
     if (work_bytes < (size_t)pl.splits * p.Mdim * R * sizeof(float)) return cudaErrorInvalidValue;
     p.out_mode = 2;
     p.out = (float*)work;
@@ -1497,7 +1606,10 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   k<<<grid, threads, pl.smem, st>>>(tmap, p);
   note_launches(1);
   err = cudaGetLastError();
-  if (err != cudaSuccess || pl.splits == 1) return err;
+  if (err != cudaSuccess) return err;
+  if (pl.blockmode)
+    return launch_block_reduce(work, pl.jdim / 32, C, R, out, out_rowmajor, st);
+  if (pl.splits == 1) return err;
   return launch_split_reduce(false, work, (int)pl.splits, p.Mdim, R, out, out_rowmajor, st);
 }
 

@@ -751,9 +751,51 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
 }
 
 planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH, double* loss) {
-  (void)H; (void)dH; (void)loss;
   if (!ctx) return PLANC_E_INVALID;
-  return fail(ctx, PLANC_E_UNSUPPORTED, "planc_cp_grad is not built yet");
+  if (!H || !dH) return fail(ctx, PLANC_E_INVALID, "bad arguments");
+  const int N = ctx->N, R = ctx->R;
+  for (int k = 0; k < N; ++k)
+    if (!H[k] || !dH[k]) return fail(ctx, PLANC_E_INVALID, "NULL factor or gradient pointer");
+  if (R > PLANC_MAX_NLS_R) return fail(ctx, PLANC_E_UNSUPPORTED, "cp_grad needs R <= %d", PLANC_MAX_NLS_R);
+  planc_status_t st;
+  // M^(n) of the given factors into dH[n]: the root partial MTTKRPs run once
+  // each and the multi-TTV chains are recomputed per mode (Alg. 3 with the
+  // factors held fixed), so no node is kept beyond its branch
+  const void* cur[2] = {nullptr, nullptr};
+  int cf[2] = {0, 0};
+  for (int n = 0; n < N; ++n) {
+    const int s = side_of(ctx, n);
+    if ((st = dt_mode(ctx, H, n, dH[n], &cur[s], &cf[s])) != PLANC_OK) return st;
+  }
+  for (int k = 0; k < N; ++k)
+    if ((st = gram_impl(ctx, ctx->dims[k], H[k], ctx->G + (size_t)k * R * R, nullptr, false,
+                        nullptr, nullptr)) != PLANC_OK)
+      return st;
+  if (loss) {
+    // f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1  (lambda = 1)
+    if ((st = planc_sqnorm(ctx, ctx->scal)) != PLANC_OK) return st;
+    CK(launch_fill(ctx->lam, 1.0, R, ctx->stream), "fill launch");
+    const int64_t rows = ctx->dims[N - 1];
+    const int nb = rowblocks(rows);
+    double* dotp = ctx->red + (size_t)nb * R;
+    CK(launch_dot_lambda(is_f64(ctx), rows, R, dH[N - 1], H[N - 1], ctx->lam, dotp, nb,
+                         ctx->stream),
+       "dot launch");
+    CK(launch_fit(R, ctx->G, N, ctx->lam, dotp, nb, ctx->scal, ctx->scal + 8, ctx->stream),
+       "fit launch");
+  }
+  for (int n = 0; n < N; ++n) {
+    CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->stream), "gram_hadamard launch");
+    CK(launch_cp_grad_rows(is_f64(ctx), ctx->dims[n], R, H[n], ctx->Sm, dH[n], ctx->stream),
+       "gradient launch");
+  }
+  if (loss) {
+    double h[11] = {0};
+    CK(cudaMemcpyAsync(h, ctx->scal, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    *loss = h[0] - 2.0 * h[9] + h[10];
+  }
+  return PLANC_OK;
 }
 
 }  // extern "C"

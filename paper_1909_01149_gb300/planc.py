@@ -287,7 +287,33 @@ class Context:
                     use_tc=rep.pm_tensor_cores != 0, tc_mask=rep.pm_tensor_cores)
 
     def cp_grad(self, H, dH=None):
+        """Loss ||X - [[H]]||^2 (host float) and its gradients dH (device)."""
+        self._check_H(H)
         dH = [torch.empty_like(h) for h in H] if dH is None else dH
+        self._check_H(dH)
         loss = C.c_double()
         self._check(lib.planc_cp_grad(self.h, _ptrs(H), _ptrs(dH), C.byref(loss)))
         return loss.value, dH
+
+
+class CPLoss(torch.autograd.Function):
+    """f(H^(1..N)) = ||X - [[H^(1), ..., H^(N)]]||^2 as an autograd node.
+
+    forward runs planc_cp_grad (one call yields the loss and every factor
+    gradient 2 (H^(n) S^(n) - M^(n)), the adjoint of the CP reconstruction);
+    backward returns those gradients scaled by the incoming gradient.  Usage:
+    ``loss = CPLoss.apply(context, *H)`` with H the context's factor tensors.
+    """
+
+    @staticmethod
+    def forward(fctx, context, *H):
+        loss, dH = context.cp_grad([h.detach() for h in H])
+        fctx.save_for_backward(*dH)
+        return torch.tensor(loss, dtype=torch.float64, device=H[0].device)
+
+    @staticmethod
+    def backward(fctx, g):
+        dH = fctx.saved_tensors
+        if float(g) == 1.0:
+            return (None,) + tuple(dH)
+        return (None,) + tuple(d * g.to(d.dtype) for d in dH)

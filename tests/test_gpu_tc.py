@@ -28,6 +28,10 @@ TC_CASES = [
     ((128, 8, 97, 5), 64, 2),      # R = 64 (MMA N = 192), 4-way
     ((512, 1030), 5, 1),           # N = 2: both branches are leaves
     ((40, 40, 40, 40), 16, 2),     # 4-way, L = 1600
+    # right branch in 32-row block mode (L / I_1 a multiple of 32, not of 128)
+    ((40, 96, 50), 16, 2),         # L / I_1 = 96, ragged last row tile
+    ((16, 32, 7, 9), 32, 2),       # L / I_1 = 32, 4-way
+    ((24, 160, 33), 64, 2),        # L / I_1 = 160, R = 64
 ]
 
 
