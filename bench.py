@@ -9,7 +9,7 @@ of the hot path).  value = outer iterations per second over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl planc|reference]
                   [--config c2|c3|c1|c4] [--alg hals|mu|admm|bpp|pgd]
-                  [--mode solve|pm|grad]
+                  [--mode solve|pm|grad|batch]
                   [--no-mixed] [--no-cpu-baseline]
 
 --impl reference times the FP64 NumPy oracle on the host cores (bounded
@@ -390,6 +390,58 @@ def run_grad(args, cfg):
     return out, 0
 
 
+def run_batch(args):
+    """256 uneven 3-way instances (I_n ~ U{32..160}, R ~ U{8..32}, planted + 2%
+    noise), HALS 25 outer iterations each: one planc_batch_solve call (all
+    phases batched, one CUDA graph) against a loop of per-instance solves
+    (contexts built before timing).  FP32 and BF16 storage."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    torch.cuda.set_device(0)
+    count, iters = 256, 25
+    t0 = time.time()
+    insts = synth.batch(count, data_seed=1, noise=0.02)
+    log(f"batch of {count} generated in {time.time() - t0:.1f}s")
+    H0 = [synth.init_factors(X.shape, R, 2000 + i) for i, (X, _, R) in enumerate(insts)]
+    elems = sum(int(np.prod(X.shape)) for X, _, _ in insts)
+    out = {"mode": "batch", "workload": "nncp-batch-256x3way-U32..160-R8..32-hals25",
+           "instances": count, "outer_iters_each": iters, "tensor_elements": elems}
+    for dtn, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        Xd = [torch.from_numpy(synth.flat(X)).to(dt).cuda() for X, _, _ in insts]
+        def fresh():
+            return [[torch.from_numpy(h).float().cuda() for h in H] for H in H0]
+        for _ in range(max(1, args.warmup)):
+            planc.batch_solve(Xd, fresh(), "hals", iters)
+        Hs = [fresh() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            res, rep = planc.batch_solve(Xd, Hs[k], "hals", iters)
+        torch.cuda.synchronize()
+        tb = (time.perf_counter() - t0) / args.steps
+        # per-instance loop (the single-instance API, one solve per tensor)
+        ctxs = [planc.Context(x, X.shape, R) for x, (X, _, R) in zip(Xd, insts)]
+        Hl = fresh()
+        for c, h in zip(ctxs, Hl):
+            c.solve(h, "hals", 2)
+        Hl = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, h in zip(ctxs, Hl):
+            c.solve(h, "hals", iters)
+        torch.cuda.synchronize()
+        tl = time.perf_counter() - t0
+        for c in ctxs:
+            c.close()
+        out[dtn] = {"batched_s": round(tb, 4), "loop_s": round(tl, 4),
+                    "batched_inst_iters_per_s": round(count * iters / tb, 1),
+                    "loop_inst_iters_per_s": round(count * iters / tl, 1),
+                    "speedup": round(tl / tb, 2), "launches_per_solve": rep["launches"],
+                    "max_final_rel_err": round(max(r["final"] for r in res), 6)}
+        del Xd
+    return out, 0
+
+
 def run_mixed(args):
     """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP), equal
     iterations from the same initial factors.  'fp32_same_values' stores the
@@ -502,9 +554,10 @@ def main():
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad", "batch"],
                     help="pm: time only the two partial MTTKRPs (profiling aid); "
-                         "grad: time the CP-loss gradient (config c4)")
+                         "grad: time the CP-loss gradient (config c4); "
+                         "batch: 256 uneven instances, batched vs per-instance loop")
     ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
@@ -526,6 +579,8 @@ def main():
                                                      cfg["dtype"], cfg["R"])
     if args.mode == "pm":
         out, rank = run_pm_only(args, cfg)
+    elif args.mode == "batch":
+        out, rank = run_batch(args)
     elif args.mode == "grad":
         if args.config == "c2" and not (args.dims or args.rank or args.dtype):
             cfg = dict(CONFIGS["c4"])

@@ -260,6 +260,43 @@ planc_solve_opts planc_solve_opts_default(void);
 planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,
                              double* loss);
 
+/* ---- batched solve --------------------------------------------------------- */
+
+/* One 3-way instance of planc_batch_solve.  X: device, I_1 x I_2 x I_3, mode 1
+ * fastest, F32 or BF16, borrowed.  H: three device F32 factors I_n x R
+ * row-major (in: initial factors, out: the solution, columns normalised as in
+ * planc_nncp_solve).  lambda: host R doubles or NULL (out).  rel_err_hist:
+ * host opts.iters doubles or NULL (out, eps per outer iteration). */
+typedef struct {
+  int64_t dims[3];
+  int R;
+  planc_dtype_t x_dtype;
+  const void* X;
+  void* H[3];
+  double* lambda;
+  double* rel_err_hist;
+  double rel_err;   /* out: eps after the last outer iteration */
+} planc_batch_instance;
+
+/* NNCP (Alg. 1 with the dimension tree of Alg. 3 and the normalisation and
+ * error identity of Alg. 4) of `count` independent 3-way instances of
+ * different sizes, all advanced together: each phase of an outer iteration
+ * (left partial MTTKRP, multi-TTVs, right partial MTTKRP, the fused per-mode
+ * update) is one launch over a work table of every instance's tiles, and with
+ * opts.use_graph the whole solve is one CUDA graph launch.  Tile shapes of the
+ * partial-MTTKRP launches are chosen by timing candidates on the first call
+ * for a batch of that size (cached per process).  Requirements: each I_n in
+ * 1..1024, R in 1..32, x_dtype F32 or BF16, opts.alg MU, HALS or PGD,
+ * opts.tol ignored (fixed iterations).  Workspace is allocated and freed
+ * inside the call.  cuda_stream NULL: a private stream is used.
+ * Synchronises the stream.  Errors (message in planc_last_error(NULL)): PLANC_E_INVALID,
+ * PLANC_E_SHAPE, PLANC_E_DTYPE, PLANC_E_UNSUPPORTED, PLANC_E_NOMEM,
+ * PLANC_E_CUDA, PLANC_E_TIMEOUT (a bounded wait in a kernel gave up).  (The
+ * paper solves one tensor at a time; batching is this library's extension.) */
+planc_status_t planc_batch_solve(planc_batch_instance* inst, int count,
+                                 const planc_solve_opts* opts, void* cuda_stream,
+                                 planc_report* report);
+
 /* ---- allocation-free variant --------------------------------------------- */
 
 /* alpha = ||X||^2 for a flat device buffer X of n elements of x_dtype, written

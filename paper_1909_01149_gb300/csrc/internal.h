@@ -120,6 +120,29 @@ size_t nls_scratch_doubles(int64_t rows, int R);
 cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st);
 
 // ---- fused per-mode update (S, NNLS, normalisation, Gram, error) ------------------
+// sets the message planc_last_error(NULL) returns on this thread
+void set_thread_error(const char* msg);
+
+// One instance of a batched 3-way solve, as the batched kernels read it
+// (device copy of a table built by planc_batch_solve).
+struct BatchInst {
+  const void* X;      // I1 x I2 x I3, mode 1 fastest (F32 or BF16, see xbf16)
+  int64_t I[3];
+  int R;
+  int xbf16;
+  float* H[3];        // I_n x R row-major
+  float* T;           // T^{1:2}: (I1 I2) x R, R slowest
+  float* M;           // M^(n): max I_n x R row-major
+  double* G;          // 3 x R x R
+  float* Gf;          // the same in FP32
+  double* lam;        // R
+  double* alpha;      // ||X||^2
+  double* hist;       // iters x (eps, beta, gamma)
+  int32_t* inner;     // iters x 3
+};
+cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, planc_nls_t alg,
+                              const planc_nls_opts& o, int* err, cudaStream_t st);
+int mode_batch_max_rows();
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R);
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,

@@ -1,0 +1,388 @@
+// Batched kernels for many small 3-way instances solved together: every
+// launch covers all instances through a table of work items (instance, tile),
+// and each CTA walks a contiguous run of items so that per-instance staging
+// (a factor in shared memory) is redone only when the instance changes.
+//
+// Per outer iteration (Alg. 1 with the dimension tree of Alg. 3, N = 3, S = 2):
+//   T^{1:2} = X_(1:2) H^(3)                 batch_pm_left   (first X pass)
+//   M^(1)   = T^{1:2} x_2 H^(2)             batch_contract_rest
+//   M^(2)   = T^{1:2} x_1 H^(1) (updated)    batch_contract_first
+//   M^(3)   = X_(1:2)^T (H^(2) . H^(1))      batch_pm_right  (second X pass)
+// with the fused per-mode update (kern_mode.cu) between them.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace planc {
+
+namespace {
+
+constexpr int BR = 32;  // rank padding of the batched kernels (R <= 32)
+
+__device__ __forceinline__ float ldx(const BatchInst& b, int64_t e) {
+  if (b.xbf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(b.X)[e]);
+  return __ldg(reinterpret_cast<const float*>(b.X) + e);
+}
+
+// first and one-past-last item of this CTA's contiguous run
+__device__ __forceinline__ void item_run(int nitems, int& i0, int& i1) {
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  i0 = min(nitems, (int)blockIdx.x * per);
+  i1 = min(nitems, i0 + per);
+}
+
+// rows f..f+nrow of a row-major nrow x R factor into shared memory with
+// stride BR (padding columns zero)
+__device__ __forceinline__ void stage_factor(float* dst, const float* H, int nrow, int R) {
+  for (int e = threadIdx.x; e < nrow * BR; e += blockDim.x) {
+    const int i = e / BR, r = e - (e / BR) * BR;
+    dst[e] = r < R ? H[(int64_t)i * R + r] : 0.f;
+  }
+}
+
+// ---- ||X||^2 per instance: items (b, chunk of 65536 elements) ----------------------
+__global__ void __launch_bounds__(256)
+batch_sqnorm_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
+                    int nitems, double* __restrict__ part) {
+  __shared__ double sred[8];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchInst& b = tab[items[it].x];
+    const int64_t n = b.I[0] * b.I[1] * b.I[2];
+    const int64_t e0 = (int64_t)items[it].y * 65536, e1 = min(n, e0 + 65536);
+    double acc = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const float x = ldx(b, e);
+      acc += (double)(x * x);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += sred[w];
+      part[it] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// alpha_b = sum of the partials of instance b (items of one instance are
+// consecutive: first[b] .. first[b + 1] - 1)
+__global__ void batch_sqnorm_finish_kernel(const BatchInst* __restrict__ tab, int count,
+                                           const int* __restrict__ first,
+                                           const double* __restrict__ part) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  double s = 0.0;
+  for (int i = first[b]; i < first[b + 1]; ++i) s += part[i];
+  *tab[b].alpha = s;
+}
+
+// ---- G^(n) = H^(n)T H^(n) of the initial factors, lambda = 1: items (b, n) -------
+__global__ void __launch_bounds__(256)
+batch_gram_kernel(const BatchInst* __restrict__ tab, int count) {
+  const int b = blockIdx.x / 3, n = blockIdx.x - (blockIdx.x / 3) * 3;
+  if (b >= count) return;
+  const BatchInst& in = tab[b];
+  const int R = in.R, rows = (int)in.I[n];
+  const float* H = in.H[n];
+  if (n == 0 && threadIdx.x < 32) in.lam[threadIdx.x] = 1.0;  // lambda starts at 1
+  for (int pr = threadIdx.x; pr < R * R; pr += blockDim.x) {
+    const int r = pr / R, s = pr - (pr / R) * R;
+    double g = 0.0;
+    for (int i0 = 0; i0 < rows; i0 += 32) {  // FP32 over 32 rows, FP64 across
+      float a = 0.f;
+      for (int i = i0; i < min(rows, i0 + 32); ++i)
+        a = fmaf(H[(int64_t)i * R + r], H[(int64_t)i * R + s], a);
+      g += (double)a;
+    }
+    in.G[(size_t)n * R * R + pr] = g;
+    in.Gf[(size_t)n * R * R + pr] = (float)g;
+  }
+}
+
+// ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of TL rows l) ------------
+// One thread per row l; H3 staged in shared memory (stride BR), its rows read
+// as broadcast 16-byte loads; four k steps issue their X loads together.
+template <int TL>
+__global__ void __launch_bounds__(TL)
+batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
+                     int nitems) {
+  extern __shared__ __align__(16) float bsm[];
+  int i0, i1;
+  item_run(nitems, i0, i1);
+  int cur = -1;
+  for (int it = i0; it < i1; ++it) {
+    const int bi = items[it].x;
+    const BatchInst& b = tab[bi];
+    const int64_t L = b.I[0] * b.I[1];
+    const int C = (int)b.I[2], R = b.R;
+    if (bi != cur) {
+      __syncthreads();
+      stage_factor(bsm, b.H[2], C, R);
+      __syncthreads();
+      cur = bi;
+    }
+    const int64_t l = (int64_t)items[it].y * TL + threadIdx.x;
+    const bool live = l < L;
+    float acc[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = 0.f;
+    int k = 0;
+    for (; k + 4 <= C; k += 4) {
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BR);
+#pragma unroll
+        for (int q = 0; q < BR / 4; ++q) {
+          const float4 hv = h[q];
+          acc[4 * q + 0] = fmaf(x[u], hv.x, acc[4 * q + 0]);
+          acc[4 * q + 1] = fmaf(x[u], hv.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(x[u], hv.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(x[u], hv.w, acc[4 * q + 3]);
+        }
+      }
+    }
+    for (; k < C; ++k) {
+      const float x = live ? ldx(b, l + L * k) : 0.f;
+      const float4* h = reinterpret_cast<const float4*>(bsm + k * BR);
+#pragma unroll
+      for (int q = 0; q < BR / 4; ++q) {
+        const float4 hv = h[q];
+        acc[4 * q + 0] = fmaf(x, hv.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(x, hv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(x, hv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(x, hv.w, acc[4 * q + 3]);
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+        if (r < R) b.T[l + L * r] = acc[r];
+    }
+  }
+}
+
+// Sum over the warp of v[r] for r < 32, lane r returning the total of v[r].
+__device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// ---- M^(3)[c, r] = sum_{i1, i2} X[i1, i2, c] H1[i1, r] H2[i2, r]: items (b, c) ----------
+// Threads own rows i1; for each owned i1 the inner sum over i2 runs with H2
+// from shared memory and is then weighted by H1[i1, r]; the CTA's per-thread
+// sums are reduced through warp reduce-scatters and shared memory.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+batch_pm_right_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
+                      int nitems) {
+  extern __shared__ __align__(16) float bsm[];
+  __shared__ float red[NT / 32][BR];
+  int i0, i1;
+  item_run(nitems, i0, i1);
+  int cur = -1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = i0; it < i1; ++it) {
+    const int bi = items[it].x;
+    const BatchInst& b = tab[bi];
+    const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
+    const int64_t L = (int64_t)I1 * I2;
+    const int64_t c = items[it].y;
+    if (bi != cur) {
+      __syncthreads();
+      stage_factor(bsm, b.H[1], I2, R);
+      __syncthreads();
+      cur = bi;
+    }
+    float acc[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = 0.f;
+    for (int i = threadIdx.x; i < I1; i += NT) {
+      float in[BR];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) in[r] = 0.f;
+      const int64_t base = i + L * c;
+      int j = 0;
+      for (; j + 4 <= I2; j += 4) {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = ldx(b, base + (int64_t)I1 * (j + u));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4* h = reinterpret_cast<const float4*>(bsm + (j + u) * BR);
+#pragma unroll
+          for (int q = 0; q < BR / 4; ++q) {
+            const float4 hv = h[q];
+            in[4 * q + 0] = fmaf(x[u], hv.x, in[4 * q + 0]);
+            in[4 * q + 1] = fmaf(x[u], hv.y, in[4 * q + 1]);
+            in[4 * q + 2] = fmaf(x[u], hv.z, in[4 * q + 2]);
+            in[4 * q + 3] = fmaf(x[u], hv.w, in[4 * q + 3]);
+          }
+        }
+      }
+      for (; j < I2; ++j) {
+        const float x = ldx(b, base + (int64_t)I1 * j);
+        const float4* h = reinterpret_cast<const float4*>(bsm + j * BR);
+#pragma unroll
+        for (int q = 0; q < BR / 4; ++q) {
+          const float4 hv = h[q];
+          in[4 * q + 0] = fmaf(x, hv.x, in[4 * q + 0]);
+          in[4 * q + 1] = fmaf(x, hv.y, in[4 * q + 1]);
+          in[4 * q + 2] = fmaf(x, hv.z, in[4 * q + 2]);
+          in[4 * q + 3] = fmaf(x, hv.w, in[4 * q + 3]);
+        }
+      }
+      const float* h1 = b.H[0] + (int64_t)i * R;
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+        if (r < R) acc[r] = fmaf(in[r], __ldg(h1 + r), acc[r]);
+    }
+    const float v = reduce_scatter32(acc, lane);
+    red[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < R) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+      b.M[c * R + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- M^(1)[i1, r] = sum_{i2} T[i1 + I1 i2, r] H2[i2, r]: items (b, r) -----------------
+__global__ void __launch_bounds__(128)
+batch_contract_rest_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
+                           int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchInst& b = tab[items[it].x];
+    const int r = items[it].y;
+    const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
+    const float* Tr = b.T + (int64_t)I1 * I2 * r;
+    for (int i = threadIdx.x; i < I1; i += blockDim.x) {
+      float a0 = 0.f, a1 = 0.f;
+      int j = 0;
+      for (; j + 2 <= I2; j += 2) {
+        a0 = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[1] + (int64_t)j * R + r), a0);
+        a1 = fmaf(Tr[i + (int64_t)I1 * (j + 1)], __ldg(b.H[1] + (int64_t)(j + 1) * R + r), a1);
+      }
+      if (j < I2) a0 = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[1] + (int64_t)j * R + r), a0);
+      b.M[(int64_t)i * R + r] = a0 + a1;
+    }
+  }
+}
+
+// ---- M^(2)[i2, r] = sum_{i1} T[i1 + I1 i2, r] H1[i1, r]: items (b, r) -----------------
+// one warp per i2, lanes across i1
+__global__ void __launch_bounds__(128)
+batch_contract_first_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
+                            int nitems) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchInst& b = tab[items[it].x];
+    const int r = items[it].y;
+    const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
+    const float* Tr = b.T + (int64_t)I1 * I2 * r;
+    for (int j = warp; j < I2; j += blockDim.x / 32) {
+      float a = 0.f;
+      for (int i = lane; i < I1; i += 32)
+        a = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[0] + (int64_t)i * R + r), a);
+      a = warp_sum(a);
+      if (lane == 0) b.M[(int64_t)j * R + r] = a;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_sqnorm(const BatchInst* tab, int count, const int2* items, int nitems,
+                                const int* first, double* part, int sm_count, cudaStream_t st) {
+  batch_sqnorm_kernel<<<std::min(nitems, 8 * sm_count), 256, 0, st>>>(tab, items, nitems, part);
+  batch_sqnorm_finish_kernel<<<(count + 127) / 128, 128, 0, st>>>(tab, count, first, part);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st) {
+  batch_gram_kernel<<<3 * count, 256, 0, st>>>(tab, count);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// tl: rows per item (64, 128 or 256); smem_floats: max C x 32 over the batch
+cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
+                                 int grid, size_t smem_floats, cudaStream_t st) {
+  const size_t smem = smem_floats * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  switch (tl) {
+    case 64:
+      e = cudaFuncSetAttribute(batch_pm_left_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_left_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems);
+      break;
+    case 128:
+      e = cudaFuncSetAttribute(batch_pm_left_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_left_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems);
+      break;
+    case 256:
+      e = cudaFuncSetAttribute(batch_pm_left_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_left_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// nt: threads per item (64, 128 or 256); smem_floats: max I2 x 32 over the batch
+cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
+                                  int grid, size_t smem_floats, cudaStream_t st) {
+  const size_t smem = smem_floats * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  switch (nt) {
+    case 64:
+      e = cudaFuncSetAttribute(batch_pm_right_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_right_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems);
+      break;
+    case 128:
+      e = cudaFuncSetAttribute(batch_pm_right_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_right_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems);
+      break;
+    case 256:
+      e = cudaFuncSetAttribute(batch_pm_right_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batch_pm_right_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
+                                  int sm_count, cudaStream_t st) {
+  const int grid = std::min(nitems, 16 * sm_count);
+  if (rest) batch_contract_rest_kernel<<<grid, 128, 0, st>>>(tab, items, nitems);
+  else batch_contract_first_kernel<<<grid, 128, 0, st>>>(tab, items, nitems);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace planc

@@ -194,12 +194,11 @@ struct McLayout {
 // of both are overwritten with G^(n) of the updated factor.  err: set to 10
 // if the wait for the bulk copies of M and H gives up.
 template <typename TA, int RP>
-__global__ void __launch_bounds__(MC_NT, 1)
-mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
-                    float* __restrict__ Gf, const TA* __restrict__ M, TA* __restrict__ H,
-                    double* __restrict__ lam, int alg, double mu_eps, int pgd_steps, double tiny,
-                    int32_t* __restrict__ inner, const double* __restrict__ alpha,
-                    double* __restrict__ fit_out, int* __restrict__ err) {
+__device__ __forceinline__ void mode_update_body(
+    int rows, int R, int N, int n, double* __restrict__ G, float* __restrict__ Gf,
+    const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg,
+    double mu_eps, int pgd_steps, double tiny, int32_t* __restrict__ inner,
+    const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
   extern __shared__ __align__(16) unsigned char mc_smem[];
@@ -574,6 +573,29 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
 }
 
 template <typename TA, int RP>
+__global__ void __launch_bounds__(MC_NT, 1)
+mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
+                    float* __restrict__ Gf, const TA* __restrict__ M, TA* __restrict__ H,
+                    double* __restrict__ lam, int alg, double mu_eps, int pgd_steps, double tiny,
+                    int32_t* __restrict__ inner, const double* __restrict__ alpha,
+                    double* __restrict__ fit_out, int* __restrict__ err) {
+  mode_update_body<TA, RP>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
+                           alpha, fit_out, err);
+}
+
+// Batched form: cluster b (blocks MC_CS b .. MC_CS b + MC_CS - 1) updates mode n
+// of instance b of a 3-way batch; after mode 3 it writes instance b's error
+// identity for outer iteration `it` into its history.
+__global__ void __launch_bounds__(MC_NT, 1)
+mode_cluster_batch_kernel(const BatchInst* __restrict__ tab, int n, int it, int alg,
+                          double mu_eps, int pgd_steps, int* __restrict__ err) {
+  const BatchInst& b = tab[blockIdx.x / MC_CS];
+  mode_update_body<float, 32>((int)b.I[n], b.R, 3, n, b.G, b.Gf, b.M, b.H[n], b.lam, alg, mu_eps,
+                              pgd_steps, 1e-30, b.inner + 3 * it + n, b.alpha,
+                              n == 2 ? b.hist + 3 * it : nullptr, err);
+}
+
+template <typename TA, int RP>
 cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const void* M, void* H,
                    double* lam, planc_nls_t alg, const planc_nls_opts& o, int32_t* inner,
                    const double* alpha, double* fit_out, int* err, cudaStream_t st) {
@@ -602,6 +624,32 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
 }
 
 }  // namespace
+
+cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, planc_nls_t alg,
+                              const planc_nls_opts& o, int* err, cudaStream_t st) {
+  const size_t smem = McLayout<float, 32>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(mode_cluster_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(MC_CS * count), 1, 1);
+  cfg.blockDim = dim3(MC_NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = MC_CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, mode_cluster_batch_kernel, tab, n, it, (int)alg, o.mu_eps,
+                         std::max(1, o.pgd_steps), err);
+  note_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+int mode_batch_max_rows() { return MC_CS * MC_RPC; }
 
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R) {
   return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD) && rows >= 1 &&

@@ -34,6 +34,13 @@ planc_status_t fail(planc_t ctx, planc_status_t st, const char* fmt, ...) {
   return st;
 }
 
+}  // namespace
+
+// the calling thread's context-free error message (planc_last_error(NULL))
+void planc::set_thread_error(const char* msg) { g_init_error = msg; }
+
+namespace {
+
 planc_status_t cuda_fail(planc_t ctx, cudaError_t e, const char* what) {
   return fail(ctx, PLANC_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

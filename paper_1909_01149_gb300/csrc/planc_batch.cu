@@ -1,0 +1,339 @@
+// planc_batch_solve: many independent 3-way NNCP instances advanced together.
+//
+// Every phase of an outer iteration is one launch over all instances (work
+// tables of (instance, tile) items built here); with opts.use_graph the whole
+// solve, all outer iterations included, is captured once and launched as one
+// CUDA graph.  The tile shapes of the two partial-MTTKRP launches are picked
+// by timing the candidates on the batch itself the first time a batch of that
+// size and shape sum is seen (the choice is cached for the process).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace planc {
+
+cudaError_t launch_batch_sqnorm(const BatchInst* tab, int count, const int2* items, int nitems,
+                                const int* first, double* part, int sm_count, cudaStream_t st);
+cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st);
+cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
+                                 int grid, size_t smem_floats, cudaStream_t st);
+cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
+                                  int grid, size_t smem_floats, cudaStream_t st);
+cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
+                                  int sm_count, cudaStream_t st);
+
+namespace {
+
+constexpr int kTL[3] = {64, 128, 256};
+constexpr int kNT[3] = {64, 128, 256};
+
+struct TuneKey {
+  int count;
+  long long elems, rank_sum;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(count, elems, rank_sum) < std::tie(o.count, o.elems, o.rank_sum);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;  // (left rows per item, right threads)
+
+struct Alloc {
+  void* p = nullptr;
+  ~Alloc() {
+    if (p) cudaFree(p);
+  }
+};
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+planc_status_t bfail(planc_status_t st, const char* msg) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "planc_batch_solve: %s", msg);
+  set_thread_error(buf);
+  return st;
+}
+
+}  // namespace
+
+}  // namespace planc
+
+using namespace planc;
+
+extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int count,
+                                            const planc_solve_opts* opts, void* cuda_stream,
+                                            planc_report* report) {
+  if (!inst || count < 1 || !opts) return bfail(PLANC_E_INVALID, "bad arguments");
+  const planc_solve_opts o = *opts;
+  if (o.iters < 1 || o.iters > 100000) return bfail(PLANC_E_INVALID, "iters out of range");
+  if (o.alg != PLANC_MU && o.alg != PLANC_HALS && o.alg != PLANC_PGD)
+    return bfail(PLANC_E_UNSUPPORTED, "batched solve supports MU, HALS and PGD");
+  const int maxrows = mode_batch_max_rows();
+  int64_t maxC = 1, maxI2 = 1;
+  for (int b = 0; b < count; ++b) {
+    const planc_batch_instance& in = inst[b];
+    if (!in.X || !in.H[0] || !in.H[1] || !in.H[2]) return bfail(PLANC_E_INVALID, "NULL pointer");
+    if (in.R < 1 || in.R > 32) return bfail(PLANC_E_SHAPE, "R must be 1..32");
+    for (int n = 0; n < 3; ++n)
+      if (in.dims[n] < 1 || in.dims[n] > maxrows) return bfail(PLANC_E_SHAPE, "dims must be 1..1024");
+    if (in.x_dtype != PLANC_F32 && in.x_dtype != PLANC_BF16)
+      return bfail(PLANC_E_DTYPE, "X must be F32 or BF16");
+    maxC = std::max(maxC, in.dims[2]);
+    maxI2 = std::max(maxI2, in.dims[1]);
+  }
+  // graph capture needs a stream other than the legacy default stream
+  struct OwnStream {
+    cudaStream_t s = nullptr;
+    ~OwnStream() {
+      if (s) cudaStreamDestroy(s);
+    }
+  } own;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (st == nullptr) {
+    if (cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "stream creation failed");
+    st = own.s;
+  }
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return bfail(PLANC_E_CUDA, "no device");
+  const int iters = o.iters;
+
+  // ---- workspace: per-instance arrays, work tables, instance table
+  std::vector<size_t> offT(count), offM(count), offG(count), offGf(count), offLam(count),
+      offAlpha(count), offHist(count), offInner(count);
+  size_t bytes = 0;
+  for (int b = 0; b < count; ++b) {
+    const planc_batch_instance& in = inst[b];
+    const size_t L = (size_t)in.dims[0] * in.dims[1];
+    const size_t R = in.R;
+    const size_t maxI = std::max({in.dims[0], in.dims[1], in.dims[2]});
+    offT[b] = bytes; bytes += align256(L * R * 4);
+    offM[b] = bytes; bytes += align256(maxI * R * 4);
+    offG[b] = bytes; bytes += align256(3 * R * R * 8);
+    offGf[b] = bytes; bytes += align256(3 * R * R * 4);
+    offLam[b] = bytes; bytes += align256(32 * 8);
+    offAlpha[b] = bytes; bytes += 256;
+    offHist[b] = bytes; bytes += align256((size_t)iters * 3 * 8);
+    offInner[b] = bytes; bytes += align256((size_t)iters * 3 * 4);
+  }
+  // work tables
+  std::vector<int2> sq_items, right_items, rc_items;
+  std::vector<int> sq_first(count + 1, 0);
+  for (int b = 0; b < count; ++b) {
+    const int64_t n = inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
+    sq_first[b] = (int)sq_items.size();
+    for (int64_t c = 0; c * 65536 < n; ++c) sq_items.push_back(make_int2(b, (int)c));
+    for (int64_t c = 0; c < inst[b].dims[2]; ++c) right_items.push_back(make_int2(b, (int)c));
+    for (int r = 0; r < inst[b].R; ++r) rc_items.push_back(make_int2(b, r));
+  }
+  sq_first[count] = (int)sq_items.size();
+  std::vector<int2> left_items[3];
+  for (int t = 0; t < 3; ++t)
+    for (int b = 0; b < count; ++b) {
+      const int64_t L = inst[b].dims[0] * inst[b].dims[1];
+      for (int64_t y = 0; y * kTL[t] < L; ++y) left_items[t].push_back(make_int2(b, (int)y));
+    }
+  const size_t off_tab = bytes; bytes += align256(sizeof(BatchInst) * count);
+  const size_t off_sq = bytes; bytes += align256(sizeof(int2) * sq_items.size());
+  const size_t off_sqf = bytes; bytes += align256(sizeof(int) * (count + 1));
+  const size_t off_sqp = bytes; bytes += align256(sizeof(double) * sq_items.size());
+  const size_t off_right = bytes; bytes += align256(sizeof(int2) * right_items.size());
+  const size_t off_rc = bytes; bytes += align256(sizeof(int2) * rc_items.size());
+  size_t off_left[3];
+  for (int t = 0; t < 3; ++t) {
+    off_left[t] = bytes;
+    bytes += align256(sizeof(int2) * left_items[t].size());
+  }
+  const size_t off_err = bytes; bytes += 256;
+
+  Alloc ws;
+  if (cudaMalloc(&ws.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(PLANC_E_NOMEM, "workspace allocation failed");
+  }
+  char* base = static_cast<char*>(ws.p);
+  std::vector<BatchInst> tab(count);
+  for (int b = 0; b < count; ++b) {
+    const planc_batch_instance& in = inst[b];
+    BatchInst& t = tab[b];
+    t.X = in.X;
+    for (int n = 0; n < 3; ++n) {
+      t.I[n] = in.dims[n];
+      t.H[n] = static_cast<float*>(in.H[n]);
+    }
+    t.R = in.R;
+    t.xbf16 = in.x_dtype == PLANC_BF16 ? 1 : 0;
+    t.T = reinterpret_cast<float*>(base + offT[b]);
+    t.M = reinterpret_cast<float*>(base + offM[b]);
+    t.G = reinterpret_cast<double*>(base + offG[b]);
+    t.Gf = reinterpret_cast<float*>(base + offGf[b]);
+    t.lam = reinterpret_cast<double*>(base + offLam[b]);
+    t.alpha = reinterpret_cast<double*>(base + offAlpha[b]);
+    t.hist = reinterpret_cast<double*>(base + offHist[b]);
+    t.inner = reinterpret_cast<int32_t*>(base + offInner[b]);
+  }
+  const BatchInst* d_tab = reinterpret_cast<const BatchInst*>(base + off_tab);
+  const int2* d_sq = reinterpret_cast<const int2*>(base + off_sq);
+  const int* d_sqf = reinterpret_cast<const int*>(base + off_sqf);
+  double* d_sqp = reinterpret_cast<double*>(base + off_sqp);
+  const int2* d_right = reinterpret_cast<const int2*>(base + off_right);
+  const int2* d_rc = reinterpret_cast<const int2*>(base + off_rc);
+  int* d_err = reinterpret_cast<int*>(base + off_err);
+  auto h2d = [&](size_t off, const void* src, size_t n) {
+    return cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st);
+  };
+  if (h2d(off_tab, tab.data(), sizeof(BatchInst) * count) != cudaSuccess ||
+      h2d(off_sq, sq_items.data(), sizeof(int2) * sq_items.size()) != cudaSuccess ||
+      h2d(off_sqf, sq_first.data(), sizeof(int) * (count + 1)) != cudaSuccess ||
+      h2d(off_right, right_items.data(), sizeof(int2) * right_items.size()) != cudaSuccess ||
+      h2d(off_rc, rc_items.data(), sizeof(int2) * rc_items.size()) != cudaSuccess ||
+      cudaMemsetAsync(base + off_err, 0, 256, st) != cudaSuccess)
+    return bfail(PLANC_E_CUDA, "table upload failed");
+  for (int t = 0; t < 3; ++t)
+    if (h2d(off_left[t], left_items[t].data(), sizeof(int2) * left_items[t].size()) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "table upload failed");
+  for (int b = 0; b < count; ++b)
+    if (cudaMemsetAsync(base + offHist[b], 0, (size_t)iters * 3 * 8, st) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "memset failed");
+
+  const size_t smem_left = (size_t)maxC * 32, smem_right = (size_t)maxI2 * 32;
+  if (smem_left * 4 > 200 * 1024 || smem_right * 4 > 200 * 1024)
+    return bfail(PLANC_E_SHAPE, "a mode is too long for the staged factor");
+  const int nleft[3] = {(int)left_items[0].size(), (int)left_items[1].size(),
+                        (int)left_items[2].size()};
+  const int nright = (int)right_items.size(), nrc = (int)rc_items.size();
+  auto grid_of = [&](int nitems) { return std::max(1, std::min(nitems, 8 * sms)); };
+
+  // ---- tile choice: timed candidates, cached per batch signature
+  TuneKey key{count, 0, 0};
+  for (int b = 0; b < count; ++b) {
+    key.elems += inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
+    key.rank_sum += inst[b].R;
+  }
+  int tl_idx = 1, nt_idx = 1;
+  bool tuned = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      tl_idx = it->second.first;
+      nt_idx = it->second.second;
+      tuned = true;
+    }
+  }
+  if (!tuned) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "event creation failed");
+    float best_l = 1e30f, best_r = 1e30f;
+    for (int t = 0; t < 3; ++t) {
+      const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, st);
+        cudaError_t ce = launch_batch_pm_left(d_tab, items, nleft[t], kTL[t], grid_of(nleft[t]),
+                                              smem_left, st);
+        cudaEventRecord(e1, st);
+        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+          return bfail(PLANC_E_CUDA, "tuning launch failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best_l) { best_l = ms; tl_idx = t; }
+      }
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, st);
+        cudaError_t ce = launch_batch_pm_right(d_tab, d_right, nright, kNT[t], grid_of(nright),
+                                               smem_right, st);
+        cudaEventRecord(e1, st);
+        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+          return bfail(PLANC_E_CUDA, "tuning launch failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best_r) { best_r = ms; nt_idx = t; }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = {tl_idx, nt_idx};
+  }
+  const int2* d_left = reinterpret_cast<const int2*>(base + off_left[tl_idx]);
+  const int tl = kTL[tl_idx], nt = kNT[nt_idx];
+
+  const long long c_start = launch_count();
+  // ---- the solve as a launch sequence
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t e;
+    if ((e = launch_batch_sqnorm(d_tab, count, d_sq, (int)sq_items.size(), d_sqf, d_sqp, sms, st)) != cudaSuccess) return e;
+    if ((e = launch_batch_gram(d_tab, count, st)) != cudaSuccess) return e;
+    for (int it = 0; it < iters; ++it) {
+      if ((e = launch_batch_pm_left(d_tab, d_left, nleft[tl_idx], tl, grid_of(nleft[tl_idx]), smem_left, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_contract(d_tab, d_rc, nrc, true, sms, st)) != cudaSuccess) return e;
+      if ((e = launch_mode_batch(d_tab, count, 0, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_contract(d_tab, d_rc, nrc, false, sms, st)) != cudaSuccess) return e;
+      if ((e = launch_mode_batch(d_tab, count, 1, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_right(d_tab, d_right, nright, nt, grid_of(nright), smem_right, st)) != cudaSuccess) return e;
+      if ((e = launch_mode_batch(d_tab, count, 2, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaError_t ce;
+  if (o.use_graph) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      const cudaError_t ee = enqueue();
+      ce = cudaStreamEndCapture(st, &g);
+      if (ee != cudaSuccess) ce = ee;
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ge, g, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(ge, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+  } else {
+    ce = enqueue();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  }
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(PLANC_E_CUDA, cudaGetErrorString(ce));
+  }
+  const long long launches = launch_count() - c_start;
+
+  // ---- results
+  int err = 0;
+  std::vector<double> hist((size_t)iters * 3), lam(32);
+  if (cudaMemcpy(&err, d_err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(PLANC_E_CUDA, "D2H failed");
+  double worst = 0.0;
+  for (int b = 0; b < count; ++b) {
+    if (cudaMemcpy(hist.data(), tab[b].hist, hist.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lam.data(), tab[b].lam, 32 * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "D2H failed");
+    inst[b].rel_err = hist[3 * (iters - 1)];
+    worst = std::max(worst, inst[b].rel_err);
+    if (inst[b].rel_err_hist)
+      for (int i = 0; i < iters; ++i) inst[b].rel_err_hist[i] = hist[3 * i];
+    if (inst[b].lambda)
+      for (int r = 0; r < inst[b].R; ++r) inst[b].lambda[r] = lam[r];
+  }
+  if (report) {
+    std::memset(report, 0, sizeof *report);
+    report->iters_done = iters;
+    report->rel_err = worst;
+    report->fit = 1.0 - worst;
+    report->launches = launches;
+  }
+  if (err != 0) return bfail(PLANC_E_TIMEOUT, "a bounded wait in the mode update gave up");
+  return PLANC_OK;
+}

@@ -54,6 +54,12 @@ class Report(C.Structure):
                 ("pm_tensor_cores", C.c_int)]
 
 
+class BatchInstance(C.Structure):
+    _fields_ = [("dims", C.c_int64 * 3), ("R", C.c_int), ("x_dtype", C.c_int),
+                ("X", C.c_void_p), ("H", C.c_void_p * 3), ("lambda_", C.POINTER(C.c_double)),
+                ("rel_err_hist", C.POINTER(C.c_double)), ("rel_err", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -84,6 +90,8 @@ def _load():
         "planc_nncp_solve": (I, [P, C.POINTER(SolveOpts), PP, C.POINTER(D), C.POINTER(Report)]),
         "planc_cp_grad": (I, [P, PP, PP, C.POINTER(D)]),
         "planc_sqnorm_noalloc": (I, [I, P, I64, P, P]),
+        "planc_batch_solve": (I, [C.POINTER(BatchInstance), I, C.POINTER(SolveOpts), P,
+                                  C.POINTER(Report)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -317,3 +325,53 @@ class CPLoss(torch.autograd.Function):
         if float(g) == 1.0:
             return (None,) + tuple(dH)
         return (None,) + tuple(d * g.to(d.dtype) for d in dH)
+
+
+def batch_solve(Xs, Hs, alg: str = "hals", iters: int = 25, use_graph: bool = True,
+                nls: NlsOpts | None = None, stream=None):
+    """planc_batch_solve over instances (X_b, [H1, H2, H3]_b): X_b a flat device
+    tensor (mode 1 fastest, float32 or bfloat16) whose dims come from the
+    factors, H_b three float32 device tensors I_n x R updated in place.
+    Returns one dict per instance (lam, rel_err history) and the report."""
+    if len(Xs) != len(Hs) or not Xs:
+        raise ValueError("need one factor triple per tensor")
+    arr = (BatchInstance * len(Xs))()
+    keep = []
+    for b, (X, H) in enumerate(zip(Xs, Hs)):
+        if len(H) != 3:
+            raise ValueError("batched solve is 3-way")
+        dims = [int(h.shape[0]) for h in H]
+        R = int(H[0].shape[1])
+        if X.numel() != dims[0] * dims[1] * dims[2] or X.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError(f"X[{b}] does not match its factors")
+        for k, h in enumerate(H):
+            _check_mat(h, dims[k], R, torch.float32, f"H[{b}][{k}]")
+        if not (X.is_cuda and X.is_contiguous()):
+            raise ValueError(f"X[{b}] must be a contiguous CUDA tensor")
+        lam = (C.c_double * R)()
+        hist = (C.c_double * iters)()
+        keep.append((lam, hist))
+        inst = arr[b]
+        for k in range(3):
+            inst.dims[k] = dims[k]
+            inst.H[k] = _ptr(H[k])
+        inst.R = R
+        inst.x_dtype = _DT[X.dtype]
+        inst.X = _ptr(X)
+        inst.lambda_ = C.cast(lam, C.POINTER(C.c_double))
+        inst.rel_err_hist = C.cast(hist, C.POINTER(C.c_double))
+    o = lib.planc_solve_opts_default()
+    o.alg = ALGS[alg]
+    o.iters = int(iters)
+    o.use_graph = 1 if use_graph else 0
+    if nls is not None:
+        o.nls = nls
+    rep = Report()
+    st = lib.planc_batch_solve(arr, len(Xs), C.byref(o),
+                               None if stream is None else C.c_void_p(stream.cuda_stream),
+                               C.byref(rep))
+    if st != 0:
+        raise PlancError(st, lib.planc_last_error(None).decode())
+    out = [dict(lam=list(lam), rel_err=list(hist), final=arr[b].rel_err)
+           for b, (lam, hist) in enumerate(keep)]
+    return out, dict(launches=rep.launches, rel_err=rep.rel_err)

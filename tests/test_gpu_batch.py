@@ -1,0 +1,119 @@
+"""GPU parity of the batched solve (planc_batch_solve): every instance of an
+uneven batch against the FP64 oracle on the same seeded inputs, against the
+single-instance solve, and graph replay against stream launches.
+
+Tolerances (as for the single-instance solves): FP32 storage, the relative
+error of every outer iteration within 1e-4 of the oracle's and the last one
+within 1e-5; BF16 storage, the last one within 1e-3 of the oracle run on the
+rounded tensor.  The batched solve (CUDA-core FP32 contractions) against the
+single-instance solve (3xTF32 tensor-core contractions): every outer
+iteration within 1e-5, the bar both meet against the oracle.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+from paper_1909_01149_gb300 import synth
+from helpers import planc, x_to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(count, seed, lo, hi, rlo, rhi, dt="f32"):
+    insts = synth.batch(count, data_seed=seed, noise=0.02, lo=lo, hi=hi, rlo=rlo, rhi=rhi)
+    Xd, Xs, H0 = [], [], []
+    for i, (X, _, R) in enumerate(insts):
+        xd, xs = x_to_device(X, dt)
+        Xd.append(xd)
+        Xs.append(xs)
+        H0.append(synth.init_factors(X.shape, R, 500 + i))
+    return Xd, Xs, H0
+
+
+def _dev(H0):
+    return [[torch.from_numpy(np.asarray(h, dtype=np.float32)).cuda() for h in H] for H in H0]
+
+
+def _host(H0):
+    return [[np.asarray(h, dtype=np.float32).astype(np.float64) for h in H] for H in H0]
+
+
+@pytest.mark.parametrize("alg", ["hals", "mu", "pgd"])
+def test_batch_matches_oracle_fp32(alg):
+    p = planc()
+    Xd, Xs, H0 = _instances(7, 3, 5, 60, 1, 32)
+    Hd = _dev(H0)
+    iters = 8
+    res, rep = p.batch_solve(Xd, Hd, alg, iters)
+    assert rep["launches"] > 0
+    for b, (xs, h0) in enumerate(zip(Xs, _host(H0))):
+        ref = o.nncp(xs, h0, alg, iters=iters)
+        np.testing.assert_allclose(res[b]["rel_err"], ref["rel_err"], rtol=0, atol=1e-4)
+        assert abs(res[b]["rel_err"][-1] - ref["rel_err"][-1]) <= 1e-5, b
+        assert res[b]["final"] == res[b]["rel_err"][-1]
+
+
+def test_batch_matches_single_instance_solve():
+    p = planc()
+    Xd, Xs, H0 = _instances(5, 4, 30, 160, 8, 32)
+    Hb = _dev(H0)
+    res, _ = p.batch_solve(Xd, Hb, "hals", 10)
+    for b in range(len(Xd)):
+        H = _dev([H0[b]])[0]
+        dims = tuple(h.shape[0] for h in H)
+        with p.Context(Xd[b], dims, H[0].shape[1]) as ctx:
+            single = ctx.solve(H, "hals", 10)
+        np.testing.assert_allclose(res[b]["rel_err"], single["rel_err"], rtol=0, atol=1e-5)
+        for hb, hs in zip(Hb[b], H):
+            np.testing.assert_allclose(hb.cpu().numpy(), hs.cpu().numpy(), rtol=1e-3, atol=1e-5)
+
+
+def test_batch_bf16_storage():
+    p = planc()
+    Xd, Xs, H0 = _instances(6, 5, 20, 80, 4, 24, dt="bf16")
+    res, _ = p.batch_solve(Xd, _dev(H0), "hals", 10)
+    for b, (xs, h0) in enumerate(zip(Xs, _host(H0))):
+        ref = o.nncp(xs, h0, "hals", iters=10)
+        assert abs(res[b]["rel_err"][-1] - ref["rel_err"][-1]) <= 1e-3, b
+
+
+def test_batch_graph_and_stream_agree():
+    p = planc()
+    Xd, Xs, H0 = _instances(9, 6, 8, 100, 2, 32)
+    a, _ = p.batch_solve(Xd, _dev(H0), "hals", 6, use_graph=True)
+    b, _ = p.batch_solve(Xd, _dev(H0), "hals", 6, use_graph=False)
+    for x, y in zip(a, b):
+        assert x["rel_err"] == y["rel_err"]  # same kernels, fixed reduction order
+        assert x["lam"] == y["lam"]
+
+
+def test_batch_edge_sizes():
+    """One-row modes, R = 1, R = 32 and a 1024-row mode in one batch."""
+    p = planc()
+    shapes = [((1, 7, 9), 1), ((1024, 3, 4), 2), ((16, 1, 33), 32), ((6, 5, 1), 3)]
+    Xd, Xs, H0 = [], [], []
+    for i, (dims, R) in enumerate(shapes):
+        X, _ = synth.planted(dims, R, 70 + i, noise=0.02, dtype=np.float32)
+        xd, xs = x_to_device(X, "f32")
+        Xd.append(xd)
+        Xs.append(xs)
+        H0.append(synth.init_factors(dims, R, 80 + i))
+    res, _ = p.batch_solve(Xd, _dev(H0), "hals", 5)
+    for b, (xs, h0) in enumerate(zip(Xs, _host(H0))):
+        ref = o.nncp(xs, h0, "hals", iters=5)
+        np.testing.assert_allclose(res[b]["rel_err"], ref["rel_err"], rtol=0, atol=1e-4)
+
+
+def test_batch_rejects_bad_input():
+    p = planc()
+    X = torch.rand(4 * 5 * 6, device="cuda")
+    good = [torch.rand(d, 3, device="cuda") for d in (4, 5, 6)]
+    with pytest.raises(p.PlancError):
+        p.batch_solve([X], [good], "bpp", 2)
+    with pytest.raises(p.PlancError):
+        big = [torch.rand(d, 33, device="cuda") for d in (4, 5, 6)]
+        p.batch_solve([X], [big], "hals", 2)
+    with pytest.raises(ValueError):
+        p.batch_solve([X], [good[:2]], "hals", 2)
