@@ -183,7 +183,7 @@ planc_status_t planc_mttkrp(planc_t ctx, void* const* H, int n, void* M);
 planc_status_t planc_partial_mttkrp(planc_t ctx, void* const* H, int side,
                                     void* T);
 
-/* S^(n) = G^(1) * ... * G^(n-1) * G^(n+1) * ... * G^(N) (Alg. 1 line "S").
+/* S^(n) = G^(1) * ... * G^(n-1) * G^(n+1) * ... * G^(N) (the S step of Alg. 1).
  * G: device N*R*R doubles; S: device R*R doubles.  Asynchronous. */
 planc_status_t planc_gram_hadamard(planc_t ctx, const double* G, int n,
                                    double* S);
