@@ -863,12 +863,18 @@ __device__ __forceinline__ float warp_reduce_scatter32(float* v, int lane) {
 
 // RBX: 32 or 64, the register arrays of the epilogue hold RBX columns (RB <= RBX)
 template <bool LEFT, bool F32, int RBX>
-__global__ void __launch_bounds__(F32 ? 320 : 192, 1)
+__global__ void __launch_bounds__(F32 ? 352 : 192, 1)
 pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcrParams p) {
   constexpr int BKX = F32 ? F_BK : BK;             // reduction elements per stage
   constexpr int UKX = F32 ? F_UK : UK;
   constexpr int XST = BM * BKX * (F32 ? 4 : 2);    // X stage bytes (16 KB)
   constexpr int W_EPI = F32 ? 6 : 2;               // epilogue warps (F32: converters 2..5)
+  // FP32: a second MMA warp issues the x_lo k_hi products into their own
+  // accumulator (a tcgen05.mma costs its issuing thread a fixed ~80 cycles
+  // for N <= 128, so two issuers double the MMA rate)
+  constexpr int W_MMA2 = 10;
+  // two MMA warps when the accumulators fit next to four TMEM A slots (R <= 32)
+  constexpr bool DUAL = F32 && RBX == 32;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -897,13 +903,13 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     }
     for (int a = 0; a < F_A_SLOTS; ++a) {
       mbar_init(&a_full[a], 4);
-      mbar_init(&a_empty[a], 1);
+      mbar_init(&a_empty[a], DUAL ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_full[b], DUAL ? 2 : 1);
       mbar_init(&acc_empty[b], 4);
     }
-    mbar_init(drain, 1);
+    mbar_init(drain, DUAL ? 2 : 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -972,11 +978,12 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // FP32: p.aslots TMEM slots of 64 columns (x hi | x lo), then two
-  // accumulator buffers [hi (RB) | lo (RB)]: x_hi [k_hi | k_lo] lands on both,
-  // x_lo k_hi on the lo half.  BF16: buffers of 256 columns [hi | mid | lo].
+  // accumulator buffers; BF16: buffers of 256 columns [hi | mid | lo].
   const int aslots = F32 ? p.aslots : 1;
   const uint32_t d_col0 = F32 ? (uint32_t)aslots * 64u : 0u;
-  const uint32_t d_stride = F32 ? (uint32_t)(2 * RB) : 256u;
+  // FP32 buffer: [hi: x_hi k_hi | x_hi k_lo (2 RB)] then, with two MMA warps
+  // (DUAL), [lo: x_lo k_hi (RB)]; with one, x_lo k_hi adds onto x_hi k_lo
+  const uint32_t d_stride = F32 ? (uint32_t)((DUAL ? 3 : 2) * RB) : 256u;
 
   // Work item layout.  Left: item = (128-row tile of L, range of outer
   // indices).  Right: item = (output row c, slice of its tpc row tiles).
@@ -1030,8 +1037,9 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
         }
       }
     }
-  } else if (warp == W_MMA) {
-    if (lane == 0) {
+  } else if (warp == W_MMA || (F32 && warp == W_MMA2)) {
+    if (lane == 0 && (warp == W_MMA || DUAL)) {
+      const bool lo_warp = F32 && warp == W_MMA2;
       const uint32_t id_a = F32 ? instr_desc(2u, false, false, BM, 2 * RB)
                                 : instr_desc(1u, LEFT, false, BM, 3 * RB);
       const uint32_t id_b = instr_desc(2u, false, false, BM, RB);
@@ -1050,7 +1058,8 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
               }
               eph ^= 1u << buf;
               tc_fence_after();
-              const uint32_t d = tmem + d_col0 + (uint32_t)buf * d_stride;
+              const uint32_t d =
+                  tmem + d_col0 + (uint32_t)buf * d_stride + (lo_warp ? (uint32_t)(2 * RB) : 0u);
               uint32_t acc = 0;
               const int g1 = min(p.nst, g0 + SEG_STAGES);
               for (int j = g0; j < g1; ++j) {
@@ -1065,12 +1074,21 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                 const uint32_t b0 = b_base + (uint32_t)(j * bstage);
                 if (F32) {
                   const uint32_t a_hi = tmem + (uint32_t)as * 64u;
+                  if (lo_warp) {
 #pragma unroll
-                  for (int kk = 0; kk < BKX / UKX; ++kk) {
-                    const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
-                    mma_tf32_ts(d, a_hi + kk * UKX, bd, id_a, acc);
-                    mma_tf32_ts(d + RB, a_hi + 32 + kk * UKX, bd, id_b, 1u);
-                    acc = 1;
+                    for (int kk = 0; kk < BKX / UKX; ++kk) {
+                      const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+                      mma_tf32_ts(d, a_hi + 32 + kk * UKX, bd, id_b, acc);
+                      acc = 1;
+                    }
+                  } else {
+#pragma unroll
+                    for (int kk = 0; kk < BKX / UKX; ++kk) {
+                      const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+                      mma_tf32_ts(d, a_hi + kk * UKX, bd, id_a, acc);
+                      if constexpr (!DUAL) mma_tf32_ts(d + RB, a_hi + 32 + kk * UKX, bd, id_b, 1u);
+                      acc = 1;
+                    }
                   }
                   mma_commit(&a_empty[as]);
                   if (++as == aslots) { as = 0; aph ^= 1; }
@@ -1158,7 +1176,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
         }
       }
     }
-  } else if (warp >= W_EPI) {
+  } else if (warp >= W_EPI && warp < W_EPI + 4) {
     // epilogue: drain each group into registers and apply the outer weights
     const int q = warp & 3;
     const int row = q * 32 + lane;
@@ -1207,20 +1225,21 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < RBX / 16; ++c) {
               if (c * 16 < RB) {
+                // FP32: x_hi k_hi + (x_hi k_lo + x_lo k_hi); BF16: hi + (mid + lo)
                 float v[16], t1[16];
                 tmem_ld16(taddr + c * 16, v);
                 tmem_ld16(taddr + RB + c * 16, t1);
-                if (F32) {
-                  tmem_ld_wait();
-#pragma unroll
-                  for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj];
-                } else {
+                if (!F32 || DUAL) {
                   float t2[16];
                   tmem_ld16(taddr + 2 * RB + c * 16, t2);
                   tmem_ld_wait();
 #pragma unroll
-                  for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj] + t2[jj];
+                  for (int jj = 0; jj < 16; ++jj) t1[jj] += t2[jj];
+                } else {
+                  tmem_ld_wait();
                 }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj];
                 if (weighted) {
                   float w[16];
                   if (LEFT) {
@@ -1542,7 +1561,8 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   p.tpi = pl.tpc / pl.nsplit;
   p.jdim = pl.jdim;
   p.Mdim = left ? L : C;
-  // TMEM: aslots x 64 A columns + 2 buffers x 2 RB accumulator columns <= 512
+  // TMEM: 4 A slots of 64 columns + 2 accumulator buffers of 3 RB (RB <= 32,
+  // two MMA warps) or 2 RB (RB <= 64, one) columns <= 512
   p.aslots = 4;
   p.err = err_flag;
   p.Hin = (const float*)kh.H[0];
@@ -1590,7 +1610,7 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const int threads = f32 ? 320 : 192;
+  const int threads = f32 ? 352 : 192;
   cudaError_t err;
   auto k = pl.RB <= 32
                ? (left ? (f32 ? pm_tcr_kernel<true, true, 32> : pm_tcr_kernel<true, false, 32>)
