@@ -9,7 +9,7 @@ of the hot path).  value = outer iterations per second over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl planc|reference]
                   [--config c2|c3|c1|c4] [--alg hals|mu|admm|bpp|pgd]
-                  [--mode solve|pm|grad|batch]
+                  [--mode solve|pm|grad|batch|ablation]
                   [--no-mixed] [--no-cpu-baseline]
 
 --impl reference times the FP64 NumPy oracle on the host cores (bounded
@@ -390,6 +390,46 @@ def run_grad(args, cfg):
     return out, 0
 
 
+def run_ablation(args):
+    """Dimension tree against per-mode MTTKRP: planc_mttkrp_all (two passes
+    over X) vs N planc_mttkrp calls (one pass each), same factors, same
+    kernels; 512^3 FP32 R=32 (N = 3) and 96^4 FP32 R=64 (N = 4)."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    torch.cuda.set_device(0)
+    out = {"mode": "ablation", "what": "all-mode MTTKRP at fixed factors"}
+    for key in ("c2", "c4"):
+        cfg = CONFIGS[key]
+        X, H0 = make_inputs(cfg)
+        Xd = torch.from_numpy(synth.flat(X)).float().cuda()
+        H = [torch.from_numpy(h).float().cuda() for h in H0]
+        ctx = planc.Context(Xd, cfg["dims"], cfg["R"])
+        M = [torch.empty_like(h) for h in H]
+        N = len(cfg["dims"])
+
+        def time_it(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+
+        t_dt = time_it(lambda: ctx.mttkrp_all(H, M))
+        t_pm = time_it(lambda: [ctx.mttkrp(H, n, M[n]) for n in range(N)])
+        out[cfg["workload"]] = {"N": N, "dimension_tree_ms": round(t_dt, 4),
+                                "per_mode_ms": round(t_pm, 4), "x_passes": [2, N],
+                                "speedup": round(t_pm / t_dt, 2)}
+        ctx.close()
+        del Xd
+    return out, 0
+
+
 def run_batch(args):
     """256 uneven 3-way instances (I_n ~ U{32..160}, R ~ U{8..32}, planted + 2%
     noise), HALS 25 outer iterations each: one planc_batch_solve call (all
@@ -554,10 +594,11 @@ def main():
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad", "batch", "ablation"],
                     help="pm: time only the two partial MTTKRPs (profiling aid); "
                          "grad: time the CP-loss gradient (config c4); "
-                         "batch: 256 uneven instances, batched vs per-instance loop")
+                         "batch: 256 uneven instances, batched vs per-instance loop; "
+                         "ablation: dimension tree vs per-mode MTTKRP")
     ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
@@ -581,6 +622,8 @@ def main():
         out, rank = run_pm_only(args, cfg)
     elif args.mode == "batch":
         out, rank = run_batch(args)
+    elif args.mode == "ablation":
+        out, rank = run_ablation(args)
     elif args.mode == "grad":
         if args.config == "c2" and not (args.dims or args.rank or args.dtype):
             cfg = dict(CONFIGS["c4"])

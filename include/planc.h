@@ -175,6 +175,13 @@ planc_status_t planc_sqnorm(planc_t ctx, double* alpha);
  * Errors: PLANC_E_INVALID (n out of range, NULL pointers). */
 planc_status_t planc_mttkrp(planc_t ctx, void* const* H, int n, void* M);
 
+/* M^(n) for every mode n at the same factors (the all-mode MTTKRP the
+ * dimension tree of Alg. 3 is built for): each root partial MTTKRP runs once
+ * (two passes over X for any N) and each branch's multi-TTV chain reuses its
+ * nodes mode after mode.  M: host array of N device pointers, I_n x R
+ * row-major (caller-owned).  Asynchronous.  Errors: PLANC_E_INVALID. */
+planc_status_t planc_mttkrp_all(planc_t ctx, void* const* H, void* const* M);
+
 /* Partial MTTKRP (Sec. 4.2.2) of one root branch:
  *   side 0: T^{1:S} = X_(1:S) K^{S+1:N}  ((prod_{k<S} I_k) x R)
  *   side 1: T^{S+1:N} = X_(1:S)^T K^{1:S}  ((prod_{k>=S} I_k) x R)

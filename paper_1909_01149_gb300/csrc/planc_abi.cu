@@ -450,6 +450,23 @@ planc_status_t planc_mttkrp(planc_t ctx, void* const* H, int n, void* M) {
   return dt_mode(ctx, H, n, M, &cur, &cf);
 }
 
+planc_status_t planc_mttkrp_all(planc_t ctx, void* const* H, void* const* M) {
+  if (!ctx) return PLANC_E_INVALID;
+  if (!H || !M) return fail(ctx, PLANC_E_INVALID, "H or M is NULL");
+  for (int k = 0; k < ctx->N; ++k)
+    if (!H[k] || !M[k]) return fail(ctx, PLANC_E_INVALID, "NULL factor or output pointer");
+  // one walk of the tree at fixed factors: each root partial MTTKRP once, the
+  // multi-TTV chains of a branch reuse its nodes mode after mode
+  const void* cur[2] = {nullptr, nullptr};
+  int cf[2] = {0, 0};
+  planc_status_t st;
+  for (int n = 0; n < ctx->N; ++n) {
+    const int s = side_of(ctx, n);
+    if ((st = dt_mode(ctx, H, n, M[n], &cur[s], &cf[s])) != PLANC_OK) return st;
+  }
+  return PLANC_OK;
+}
+
 planc_status_t planc_partial_mttkrp(planc_t ctx, void* const* H, int side, void* T) {
   if (!ctx) return PLANC_E_INVALID;
   if (!H || !T || (side != 0 && side != 1)) return fail(ctx, PLANC_E_INVALID, "bad arguments");
@@ -768,12 +785,7 @@ planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH, doubl
   // M^(n) of the given factors into dH[n]: the root partial MTTKRPs run once
   // each and the multi-TTV chains are recomputed per mode (Alg. 3 with the
   // factors held fixed), so no node is kept beyond its branch
-  const void* cur[2] = {nullptr, nullptr};
-  int cf[2] = {0, 0};
-  for (int n = 0; n < N; ++n) {
-    const int s = side_of(ctx, n);
-    if ((st = dt_mode(ctx, H, n, dH[n], &cur[s], &cf[s])) != PLANC_OK) return st;
-  }
+  if ((st = planc_mttkrp_all(ctx, H, dH)) != PLANC_OK) return st;
   for (int k = 0; k < N; ++k)
     if ((st = gram_impl(ctx, ctx->dims[k], H[k], ctx->G + (size_t)k * R * R, nullptr, false,
                         nullptr, nullptr)) != PLANC_OK)

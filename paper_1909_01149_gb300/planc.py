@@ -82,6 +82,7 @@ def _load():
         "planc_sqnorm": (I, [P, P]),
         "planc_mttkrp": (I, [P, PP, I, P]),
         "planc_partial_mttkrp": (I, [P, PP, I, P]),
+        "planc_mttkrp_all": (I, [P, PP, PP]),
         "planc_gram_hadamard": (I, [P, P, I, P]),
         "planc_gram": (I, [P, I64, P, P]),
         "planc_nls_update": (I, [P, I, C.POINTER(NlsOpts), I64, P, P, P, P, P]),
@@ -227,6 +228,14 @@ class Context:
             self._check_H(H, skip=n)
         M = self._empty(self.dims[n] if 0 <= n < self.N else 1) if M is None else M
         self._check(lib.planc_mttkrp(self.h, _ptrs(H), int(n), _ptr(M)))
+        return M
+
+    def mttkrp_all(self, H, M=None):
+        """M^(n) for every mode through one dimension-tree pass."""
+        self._check_H(H)
+        M = [torch.empty_like(h) for h in H] if M is None else M
+        self._check_H(M)
+        self._check(lib.planc_mttkrp_all(self.h, _ptrs(H), _ptrs(M)))
         return M
 
     def partial_mttkrp(self, H, side: int, T: torch.Tensor | None = None) -> torch.Tensor:
