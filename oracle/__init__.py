@@ -24,6 +24,17 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                       solution; capped form is deterministic)
   nls_pgd ........................... pinned (objective non-increasing; fixed
                                       point satisfies KKT)
+  nls_ucp ........................... pinned (least squares on the explicit
+                                      unfolding; ALS loss non-increasing;
+                                      exact recovery of a noiseless CP tensor)
+  nes_params ........................ pinned (closed forms for diagonal and
+                                      rotated S; kappa cap)
+  nls_nes ........................... pinned (uncapped: scipy NNLS of the plain
+                                      and the proximal problem; the strongly
+                                      convex accelerated rate bound; fixed
+                                      point stops after one step)
+  nes_extrapolate, model_error ...... pinned (explicit reconstruction of the
+                                      extrapolated, projected model)
   normalize_columns ................. pinned (norms, reconstruction unchanged)
   fit_identity ...................... pinned (explicit reconstruction residual)
   nncp .............................. pinned (noiseless planted tensor -> zero
@@ -46,6 +57,14 @@ from .nncp import (  # noqa: F401
     nls_bpp,
     nls_bpp_row,
     nls_pgd,
+    nls_ucp,
+    nes_params,
+    nls_nes,
+    nes_extrapolate,
+    model_error,
+    NES_KAPPA,
+    NES_MAX_INNER,
+    NES_TOL,
     nls_objective,
     normalize_columns,
     cp_full,

@@ -338,6 +338,113 @@ def nls_pgd(S, M, H, steps: int = 1):
     return H
 
 
+def nls_ucp(S, M):
+    """Unconstrained update (the UCP solver of Sec. 6, CP-ALS): the exact
+    minimiser of the mode-n least-squares problem ||X_(n) - H K^T||^2 with no
+    non-negativity, i.e. the solution of H S = M with S = K^T K (Alg. 1's S)
+    symmetric positive definite."""
+    S = np.asarray(S, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    return np.linalg.solve(S, M.T).T
+
+
+NES_KAPPA = 100.0     # reading: largest condition number of the proximal problem
+NES_MAX_INNER = 20    # Sec. 4.3.5: at most 20 inner iterations
+NES_TOL = 1e-3        # reading: inner stop when max|X_{k+1} - Y_k| <= tol max|X_{k+1}|
+
+
+def nes_params(S, kappa: float = NES_KAPPA):
+    """Parameters of the Nesterov-type update (Sec. 4.3.5), from the extreme
+    eigenvalues of S = A^T A (the paper defers their choice to the cited
+    method; these are this project's readings):
+      mu0, L0 = smallest / largest eigenvalue of S, clamped at 0;
+      lam_p   = the smallest proximal weight that makes the condition number
+                (L0 + lam_p) / (mu0 + lam_p) at most kappa, i.e.
+                max(0, (L0 - kappa mu0) / (kappa - 1));
+      L = L0 + lam_p, mu = mu0 + lam_p (Lipschitz and strong-convexity
+      constants of f_p); beta = (1 - sqrt(mu/L)) / (1 + sqrt(mu/L)), the
+      constant momentum of Nesterov's scheme for strongly convex f_p.
+    Returns (lam_p, L, beta); L = 0 when S = 0."""
+    ev = np.linalg.eigvalsh(np.asarray(S, dtype=np.float64))
+    mu0, L0 = max(float(ev[0]), 0.0), max(float(ev[-1]), 0.0)
+    lam_p = max(0.0, (L0 - kappa * mu0) / (kappa - 1.0))
+    L, mu = L0 + lam_p, mu0 + lam_p
+    if L <= 0.0:
+        return lam_p, 0.0, 0.0
+    sq = math.sqrt(mu / L)
+    return lam_p, L, (1.0 - sq) / (1.0 + sq)
+
+
+def nls_nes(S, M, Hstar, max_inner: int = NES_MAX_INNER, tol: float = NES_TOL,
+            return_state: bool = False):
+    """Nesterov-type update (Sec. 4.3.5, Eq. nesnls and Eq. nesinnerupd) in
+    row form (X = H, A^T A = S, A^T B = M^T):
+        f_p(H) = 1/2 tr(H S H^T) - tr(M^T H) + lam_p/2 ||H - H*||_F^2,  H >= 0,
+    with H* the warm start (the factor of the previous outer iteration).
+    Starting from X_0 = Y_0 = H*, each inner step takes
+        grad = Y_k S - M + lam_p (Y_k - H*)       (reading: the true gradient
+                                                  of f_p; the printed signs
+                                                  disagree with each other)
+        X_{k+1} = [Y_k - grad / L]_+
+        Y_{k+1} = X_{k+1} + beta (X_{k+1} - X_k)
+    and stops after the step where max|X_{k+1} - Y_k| <= tol max|X_{k+1}|
+    (reading of the paper's bounds checks: the largest projected-gradient
+    step, relative to the largest entry; one global check over all rows), or
+    after max_inner steps.  S = 0 leaves H* unchanged.
+    Returns Hhat, or (Hhat, steps) with return_state."""
+    S = np.asarray(S, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    Hs = np.array(Hstar, dtype=np.float64, copy=True)
+    lam_p, L, beta = nes_params(S)
+    if L <= 0.0:
+        return (Hs, 0) if return_state else Hs
+    X, Y, k = Hs, Hs, 0
+    while k < max_inner:
+        grad = Y @ S - M + lam_p * (Y - Hs)
+        Xn = np.maximum(0.0, Y - grad / L)
+        step = float(np.max(np.abs(Xn - Y))) if Xn.size else 0.0
+        big = float(np.max(np.abs(Xn))) if Xn.size else 0.0
+        Y = Xn + beta * (Xn - X)
+        X = Xn
+        k += 1
+        if step <= tol * big:
+            break
+    return (X, k) if return_state else X
+
+
+def nes_extrapolate(H, lam, H_prev, lam_prev, s):
+    """Outer acceleration candidate (Sec. 4.3.5, Eq. nesouterupd):
+        F_new^(n) = F_i^(n) + s (F_i^(n) - F_{i-1}^(n))   for every mode n,
+    on the model's factors with the weights absorbed into the last mode
+    (F^(n) = H^(n) for n < N, F^(N) = H^(N) diag(lam)), which is the factor the
+    last mode's update produced.  Readings: the candidate is projected onto
+    the non-negative orthant (the NNCP constraint), then every factor's
+    columns are normalised and the column norms multiplied into lam, so that
+    [[lam_new; H_new]] = [[F_new]] (zero columns stay zero).
+    Returns (H_new, lam_new)."""
+    N = len(H)
+    lam_new = None
+    H_new = []
+    for n in range(N):
+        F = H[n] * lam if n == N - 1 else H[n]
+        Fp = H_prev[n] * lam_prev if n == N - 1 else H_prev[n]
+        Fn = np.maximum(0.0, F + s * (F - Fp))
+        Hn, nu = normalize_columns(Fn)
+        H_new.append(Hn)
+        lam_new = nu if lam_new is None else lam_new * nu
+    return H_new, lam_new
+
+
+def model_error(X, H, lam, alpha):
+    """Relative error of [[lam; H]] by the identity of Sec. A.2 at the last
+    mode: one MTTKRP (the extra MTTKRP of Sec. 6's table) and the Grams."""
+    N = len(H)
+    G = [gram(h) for h in H]
+    M = mttkrp(X, H, N - 1)
+    S = gram_hadamard(G, N - 1)
+    return fit_identity(alpha, M, H[N - 1] * lam, S, G[N - 1], lam)[0]
+
+
 # ----------------------------------------------------------------------------
 # Normalisation and error (Appendix, Alg. 4)
 # ----------------------------------------------------------------------------
@@ -380,7 +487,7 @@ def fit_explicit(X, H, lam):
 
 
 def nncp(X, H_init, alg: str = "hals", iters: int = 10, tol=None,
-         record_objective: bool = False):
+         record_objective: bool = False, nes_accel: bool = True):
     """Alternating-update NNCP, Alg. 1 with Alg. 4's normalisation and error.
 
     reading: all N factors are initialised (the warm start needs H^(1) too);
@@ -388,8 +495,12 @@ def nncp(X, H_init, alg: str = "hals", iters: int = 10, tol=None,
     for mode n is H^(n) diag(lam) (the solve is for H^(n) Lambda); a fixed
     number of outer iterations is run unless tol is given.
 
+    alg "nes": the Nesterov-type update per mode and, with nes_accel, the
+    outer acceleration after every outer iteration but the first.
+
     Returns dict(H=list, lam=array, rel_err=list per outer iteration,
-    inner=list of per-call inner counts).
+    inner=list of per-call inner counts, accepted=list of the acceleration
+    decisions).
     """
     X = np.asarray(X, dtype=np.float64)
     N = X.ndim
@@ -398,8 +509,9 @@ def nncp(X, H_init, alg: str = "hals", iters: int = 10, tol=None,
     alpha = sqnorm(X)
     lam = np.ones(R)
     G = [gram(h) for h in H]
-    rel_err, inner, objective = [], [], []
-    for _ in range(iters):
+    rel_err, inner, objective, accepted = [], [], [], []
+    H_prev, lam_prev = None, None
+    for it in range(iters):
         for n in range(N):
             M = mttkrp(X, H, n)
             S = gram_hadamard(G, n)
@@ -419,6 +531,12 @@ def nncp(X, H_init, alg: str = "hals", iters: int = 10, tol=None,
             elif alg == "pgd":
                 Hhat = nls_pgd(S, M, Hhat0)
                 inner.append(1)
+            elif alg == "ucp":
+                Hhat = nls_ucp(S, M)
+                inner.append(1)
+            elif alg == "nes":
+                Hhat, k = nls_nes(S, M, Hhat0, return_state=True)
+                inner.append(k)
             else:
                 raise ValueError(alg)
             H[n], lam = normalize_columns(Hhat)
@@ -426,10 +544,26 @@ def nncp(X, H_init, alg: str = "hals", iters: int = 10, tol=None,
             if record_objective:
                 objective.append(fit_explicit(X, H, lam)[0])
         eps, _ = fit_identity(alpha, M, Hhat, S, G[N - 1], lam)
+        if alg == "nes" and nes_accel:
+            # outer acceleration (Eq. nesouterupd) from the second iteration
+            # on, with s_i = i^(1/N) (i = 1-based outer iteration); accepted
+            # only if the candidate's error is strictly lower
+            if H_prev is not None:
+                s_i = (it + 1) ** (1.0 / N)
+                Hc, lamc = nes_extrapolate(H, lam, H_prev, lam_prev, s_i)
+                eps_c = model_error(X, Hc, lamc, alpha)
+                ok = eps_c < eps
+                accepted.append(bool(ok))
+                if ok:
+                    H, lam, eps = Hc, lamc, eps_c
+                    G = [gram(h) for h in H]
+            H_prev = [h.copy() for h in H]
+            lam_prev = lam.copy()
         rel_err.append(eps)
         if tol is not None and eps <= tol:
             break
-    out = dict(H=H, lam=lam, rel_err=rel_err, inner=inner, alpha=alpha)
+    out = dict(H=H, lam=lam, rel_err=rel_err, inner=inner, alpha=alpha,
+               accepted=accepted)
     if record_objective:
         out["objective"] = objective
     return out

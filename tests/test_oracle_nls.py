@@ -169,3 +169,32 @@ def test_normalize_columns():
     np.testing.assert_allclose(np.linalg.norm(H[:, [0, 1, 3]], axis=0), 1.0)
     assert lam[2] == 0 and not H[:, 2].any()
     np.testing.assert_allclose(H * lam, Hh, rtol=1e-15)
+
+
+def test_ucp_is_the_unfolded_least_squares_solution():
+    """The UCP update solves min ||X_(n) - H K^T|| (least squares on the
+    explicit unfolding and Khatri-Rao product, not the normal equations)."""
+    rng = np.random.default_rng(21)
+    dims, R = (7, 6, 8), 4
+    X = rng.random(dims)
+    H = [rng.random((d, R)) for d in dims]
+    for n in range(3):
+        K = o.krp_except(H, n)
+        ref, *_ = np.linalg.lstsq(K, o.unfold(X, n).T, rcond=None)
+        S = o.gram_hadamard([o.gram(h) for h in H], n)
+        np.testing.assert_allclose(o.nls_ucp(S, o.mttkrp(X, H, n)), ref.T, rtol=1e-9, atol=1e-12)
+
+
+def test_ucp_als_objective_non_increasing_and_exact_recovery():
+    """CP-ALS: each block update is the exact block minimiser, so the loss
+    never increases; on a noiseless rank-R tensor it converges to zero."""
+    rng = np.random.default_rng(22)
+    dims, R = (9, 8, 7), 3
+    # zero-mean factors (well-conditioned S; UCP has no sign constraint)
+    A = [rng.standard_normal((d, R)) for d in dims]
+    X = o.cp_full(A)
+    H0 = [a + 0.2 * rng.standard_normal(a.shape) for a in A]
+    res = o.nncp(X, H0, "ucp", iters=60, record_objective=True)
+    obj = res["objective"]
+    assert all(b <= a * (1 + 1e-10) + 1e-14 for a, b in zip(obj, obj[1:]))
+    assert res["rel_err"][-1] < 1e-6
