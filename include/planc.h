@@ -57,10 +57,24 @@ typedef enum {
 
 typedef enum { PLANC_F64 = 0, PLANC_F32 = 1, PLANC_BF16 = 2, PLANC_F16 = 3 } planc_dtype_t;
 
-/* NNLS-Update choices of Sec. 4.3 (MU, HALS, BPP, ADMM) plus projected
- * gradient (PGD), the project's gradient-driven option. */
+/* NNLS-Update choices of Sec. 4.3 (MU, HALS, BPP, ADMM, NES) plus projected
+ * gradient (PGD), the project's gradient-driven option, and UCP, the
+ * unconstrained update of Sec. 6 (CP-ALS: H S = M solved exactly, no
+ * non-negativity; a non-positive Cholesky pivot of S reports
+ * PLANC_E_NUMERIC at the end of a solve).
+ * NES is the Nesterov-type update of Sec. 4.3.5 (Eq. nesnls, Eq.
+ * nesinnerupd): accelerated projected gradient on the proximal problem
+ * 1/2 tr(H S H^T) - tr(M^T H) + lam_p/2 ||H - H*||^2 (H* the warm start),
+ * with lam_p, the step 1/L and the momentum beta taken from the extreme
+ * eigenvalues mu0, L0 of S: lam_p = max(0, (L0 - 100 mu0) / 99) (condition
+ * number at most 100), L = L0 + lam_p, beta = (1 - sqrt(q)) / (1 + sqrt(q)),
+ * q = (mu0 + lam_p) / L; it stops after the step where
+ * max|X_{k+1} - Y_k| <= nes_tol max|X_{k+1}| over the whole factor, or after
+ * nes_max_inner steps.  In planc_nncp_solve it adds the outer acceleration
+ * of Eq. nesouterupd (see planc_solve_opts.nes_accel). */
 typedef enum {
-  PLANC_MU = 0, PLANC_HALS = 1, PLANC_BPP = 2, PLANC_ADMM = 3, PLANC_PGD = 4
+  PLANC_MU = 0, PLANC_HALS = 1, PLANC_BPP = 2, PLANC_ADMM = 3, PLANC_PGD = 4, PLANC_UCP = 5,
+  PLANC_NES = 6
 } planc_nls_t;
 
 /* Tuning of the NNLS updates; planc_nls_opts_default() fills the values the
@@ -71,6 +85,8 @@ typedef struct {
   double admm_tol;      /* ADMM primal/dual stopping ratio: 1e-2 */
   int bpp_max_iter;     /* BPP exchange cap; <= 0 means 10 * R */
   int pgd_steps;        /* projected-gradient steps per update: 1 */
+  int nes_max_inner;    /* Nesterov inner steps cap (Sec. 4.3.5): 20, <= 64 */
+  double nes_tol;       /* Nesterov stopping ratio: 1e-3 */
 } planc_nls_opts;
 
 /* Options of planc_nncp_solve. */
@@ -81,6 +97,12 @@ typedef struct {
   planc_nls_opts nls;
   int use_graph;        /* 1: replay each outer iteration as a CUDA graph */
   int profile;          /* 1: time the partial-MTTKRP launches with events */
+  int nes_accel;        /* alg NES: 1 (default) adds the outer acceleration of
+                           Eq. nesouterupd after every outer iteration i >= 2:
+                           F_new = [F_i + s_i (F_i - F_{i-1})]_+ for every
+                           factor (lambda absorbed into the last mode),
+                           s_i = i^(1/N), accepted iff its relative error
+                           (one extra MTTKRP) is lower than iteration i's */
 } planc_solve_opts;
 
 /* Result record of planc_nncp_solve (host memory). */
@@ -98,6 +120,9 @@ typedef struct {
   long long launches;   /* kernels this call launched (graph replays included) */
   int pm_tensor_cores;  /* bit 0 / bit 1: left / right partial MTTKRP ran on
                            the tcgen05 tensor-core path */
+  int32_t* accel_hist;  /* optional host array, length >= opts.iters: 1 where
+                           the outer acceleration was accepted (NES) */
+  int accel_accepted;   /* number of accepted outer accelerations */
 } planc_report;
 
 typedef struct planc_ctx* planc_t;
@@ -207,12 +232,14 @@ planc_status_t planc_gram(planc_t ctx, int64_t rows, const void* H, double* G);
  *   alg  MU (Eq. muupd, one step), HALS (Eq. halsupd, one sweep in column
  *        order), BPP (Eq. snls, exact NNLS per row, FP64 passive-set
  *        Cholesky), ADMM (Eq. admmupd, FP64 Cholesky of S + rho I, U reset
- *        to zero), PGD (projected gradient).
+ *        to zero), NES (see planc_nls_t; eigenvalues of S in FP64), PGD
+ *        (projected gradient), UCP (H = M S^{-1}).
  *   opts may be NULL (defaults).
  *   aux  ADMM dual U (device rows x R) to use and return, or NULL for the
  *        library's zero-initialised scratch; ignored by other algorithms.
- *   inner_iters  device int32 or NULL: ADMM steps taken / max BPP exchanges
- *        over rows (1 for MU, HALS; pgd_steps for PGD).
+ *   inner_iters  device int32 or NULL: ADMM / NES steps taken / max BPP
+ *        exchanges over rows (1 for MU, HALS, UCP; pgd_steps for PGD; 0 for
+ *        NES when S = 0, which leaves H unchanged).
  * Asynchronous.  A BPP row that hits the exchange cap returns its current
  * clipped iterate (no error).  Errors: PLANC_E_INVALID, PLANC_E_SHAPE
  * (rows > the largest mode of the context). */

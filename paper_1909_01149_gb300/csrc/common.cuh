@@ -11,6 +11,7 @@
 #define PLANC_MAX_R 256
 #define PLANC_MAX_NLS_R 64
 #define PLANC_MAX_ADMM_STEPS 64
+#define PLANC_MAX_NES_STEPS 64
 
 namespace planc {
 

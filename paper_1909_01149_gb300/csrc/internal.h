@@ -99,6 +99,25 @@ cudaError_t launch_cp_grad_rows(bool f64, int64_t rows, int R, const void* H, co
                                 void* G, cudaStream_t st);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st);
 
+// outer acceleration of the Nesterov-type solve: every factor of the model,
+// concatenated (element e of the whole belongs to mode n with
+// off[n] <= e < off[n+1])
+struct AccelModes {
+  int N, R;
+  int64_t off[PLANC_MAX_N + 1];
+  void* H[PLANC_MAX_N];   // current iterate (normalised; lambda separate)
+  void* Hp[PLANC_MAX_N];  // previous outer iterate
+  void* Hc[PLANC_MAX_N];  // candidate
+};
+cudaError_t launch_accel_extrapolate(bool f64, const AccelModes& t, const double* lam,
+                                     const double* lam_prev, const int* counter, cudaStream_t st);
+cudaError_t launch_accel_finish(bool f64, const AccelModes& t, const double* nu, double* lam_c,
+                                cudaStream_t st);
+cudaError_t launch_accel_select(bool f64, const AccelModes& t, double* scal, const int* counter,
+                                int32_t* hist, int cap, int* flags, double* lam, double* lam_prev,
+                                const double* lam_c, double* G, float* Gf, const double* Gc,
+                                cudaStream_t st);
+
 // ---- NNLS updates (Sec. 4.3) ---------------------------------------------------
 struct NlsArgs {
   planc_nls_t alg;
@@ -109,7 +128,8 @@ struct NlsArgs {
   const void* M;          // rows x R
   void* H;                // rows x R, in/out
   const double* lambda;   // warm-start column scale (NULL = none)
-  void* U;                // ADMM dual (rows x R)
+  void* U;                // ADMM dual / Nesterov Y (rows x R)
+  void* V;                // Nesterov H* (rows x R)
   bool U_zero;            // ADMM: start from U = 0 (else read U)
   int32_t* inner;         // device int or NULL
   double* scratch;        // FP64 scratch (>= nls_scratch_doubles)
@@ -177,7 +197,16 @@ struct planc_ctx {
   size_t tc_bytes = 0;
   int* tc_err = nullptr;                 // tcgen05 bounded-wait error flag
   void* Mbuf = nullptr;                  // max_dim x R
-  void* Ubuf = nullptr;                  // ADMM dual, max_dim x R
+  void* Ubuf = nullptr;                  // ADMM dual / Nesterov Y, max_dim x R
+  void* Vbuf = nullptr;                  // Nesterov H*, max_dim x R
+  // outer acceleration (Nesterov-type solve)
+  void* Hprev[PLANC_MAX_N] = {};         // previous outer iterate
+  void* Hcand[PLANC_MAX_N] = {};         // candidate
+  double* lam_prev = nullptr;            // R
+  double* lam_cand = nullptr;            // R
+  double* nu = nullptr;                  // N x R candidate column norms
+  double* Gc = nullptr;                  // N x R x R candidate Grams
+  int32_t* accel_hist = nullptr;         // per outer iteration: accepted
   double* G = nullptr;                   // N x R x R
   float* Gf = nullptr;                   // the same Grams rounded to FP32
   double* Sm = nullptr;                  // R x R

@@ -406,4 +406,130 @@ cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---- outer acceleration of the Nesterov-type solve (Sec. 4.3.5, Eq. nesouterupd) ----
+namespace {
+
+__device__ __forceinline__ int accel_mode(const AccelModes& t, int64_t e) {
+  int n = 0;
+  while (n + 1 < t.N && e >= t.off[n + 1]) ++n;
+  return n;
+}
+
+// Hc^(n) = [F^(n) + s (F^(n) - F_prev^(n))]_+ with F^(N) = H^(N) diag(lam),
+// s = i^(1/N), i = 1 + the number of completed outer iterations.
+template <typename TA>
+__global__ void __launch_bounds__(256)
+accel_extrapolate_kernel(AccelModes t, const double* __restrict__ lam,
+                         const double* __restrict__ lam_prev, const int* __restrict__ counter) {
+  const double s = pow((double)(*counter + 1), 1.0 / t.N);
+  const int64_t total = t.off[t.N];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = accel_mode(t, e);
+    const int64_t idx = e - t.off[n];
+    double F = (double)((const TA*)t.H[n])[idx];
+    double Fp = (double)((const TA*)t.Hp[n])[idx];
+    if (n == t.N - 1) {
+      const int r = (int)(idx % t.R);
+      F *= lam[r];
+      Fp *= lam_prev[r];
+    }
+    const double c = fma(s, F - Fp, F);
+    ((TA*)t.Hc[n])[idx] = (TA)(c > 0.0 ? c : 0.0);
+  }
+}
+
+// lam_c[r] = prod_n nu^(n)_r (the candidate's column norms, mode order)
+__global__ void accel_lam_kernel(const double* __restrict__ nu, int N, int R,
+                                 double* __restrict__ lam_c) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double p = nu[r];
+  for (int n = 1; n < N; ++n) p *= nu[(size_t)n * R + r];
+  lam_c[r] = p;
+}
+
+// accept iff an earlier iterate exists and the candidate's error is lower
+__global__ void accel_decide_kernel(double* __restrict__ scal, const int* __restrict__ counter,
+                                    int32_t* __restrict__ hist, int cap, int* __restrict__ flags) {
+  const int it = *counter;
+  const bool acc = it >= 1 && scal[16] < scal[8];
+  scal[24] = acc ? 1.0 : 0.0;
+  if (it < cap) hist[it] = acc ? 1 : 0;
+  if (acc) {
+    flags[6] += 1;
+    scal[8] = scal[16];
+    scal[9] = scal[17];
+    scal[10] = scal[18];
+  }
+}
+
+// the accepted iterate becomes the current and the previous one
+template <typename TA>
+__global__ void __launch_bounds__(256)
+accel_select_kernel(AccelModes t, double* __restrict__ lam, double* __restrict__ lam_prev,
+                    const double* __restrict__ lam_c, double* __restrict__ G,
+                    float* __restrict__ Gf, const double* __restrict__ Gc,
+                    const double* __restrict__ scal) {
+  const bool acc = scal[24] != 0.0;
+  const int64_t total = t.off[t.N];
+  const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = tid0; e < total; e += stride) {
+    const int n = accel_mode(t, e);
+    const int64_t idx = e - t.off[n];
+    TA v = acc ? ((const TA*)t.Hc[n])[idx] : ((const TA*)t.H[n])[idx];
+    if (acc) ((TA*)t.H[n])[idx] = v;
+    ((TA*)t.Hp[n])[idx] = v;
+  }
+  for (int64_t r = tid0; r < t.R; r += stride) {
+    const double l = acc ? lam_c[r] : lam[r];
+    lam[r] = l;
+    lam_prev[r] = l;
+  }
+  if (acc)
+    for (int64_t e = tid0; e < (int64_t)t.N * t.R * t.R; e += stride) {
+      G[e] = Gc[e];
+      Gf[e] = (float)Gc[e];
+    }
+}
+
+int accel_blocks(const AccelModes& t) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((t.off[t.N] + 255) / 256, 592));
+}
+
+}  // namespace
+
+cudaError_t launch_accel_extrapolate(bool f64, const AccelModes& t, const double* lam,
+                                     const double* lam_prev, const int* counter, cudaStream_t st) {
+  if (f64)
+    accel_extrapolate_kernel<double><<<accel_blocks(t), 256, 0, st>>>(t, lam, lam_prev, counter);
+  else
+    accel_extrapolate_kernel<float><<<accel_blocks(t), 256, 0, st>>>(t, lam, lam_prev, counter);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accel_finish(bool f64, const AccelModes& t, const double* nu, double* lam_c,
+                                cudaStream_t st) {
+  accel_lam_kernel<<<(t.R + 63) / 64, 64, 0, st>>>(nu, t.N, t.R, lam_c);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accel_select(bool f64, const AccelModes& t, double* scal, const int* counter,
+                                int32_t* hist, int cap, int* flags, double* lam, double* lam_prev,
+                                const double* lam_c, double* G, float* Gf, const double* Gc,
+                                cudaStream_t st) {
+  accel_decide_kernel<<<1, 1, 0, st>>>(scal, counter, hist, cap, flags);
+  if (f64)
+    accel_select_kernel<double><<<accel_blocks(t), 256, 0, st>>>(t, lam, lam_prev, lam_c, G, Gf,
+                                                                 Gc, scal);
+  else
+    accel_select_kernel<float><<<accel_blocks(t), 256, 0, st>>>(t, lam, lam_prev, lam_c, G, Gf,
+                                                                Gc, scal);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
 }  // namespace planc

@@ -1,6 +1,7 @@
-// NNLS-Update kernels (Sec. 4.3): MU, HALS, ADMM, BPP and projected
-// gradient, all in the row form of Eq. nls (rows of Hhat are independent,
-// given S = K^T K and M = X_(n) K).
+// NNLS-Update kernels (Sec. 4.3): MU, HALS, ADMM, BPP, the Nesterov-type
+// update, projected gradient and the unconstrained update, all in the row
+// form of Eq. nls (rows of Hhat are independent, given S = K^T K and
+// M = X_(n) K).
 //
 // MU, HALS, ADMM steps and PGD keep one row per thread with the row in
 // registers (R padded to RP in {16, 32, 64}) and S (or the ADMM inverse) in
@@ -159,8 +160,10 @@ nls_pgd_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
 // (R x R, FP64), then W as TA, then per-step per-block norm partials.
 constexpr int ADMM_W = 8;
 
+// ucp != 0: no shift (rho = 0), W = S^{-1} for the unconstrained update
 __global__ void __launch_bounds__(256)
-admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64) {
+admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64,
+                 int ucp) {
   extern __shared__ double sm[];
   double* A = sm;             // R x R: S + rho I, then its Cholesky factor (lower)
   double* Li = sm + R * R;    // R x R: L^{-1} (lower)
@@ -171,7 +174,7 @@ admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, 
     double tr = 0.0;
     for (int r = 0; r < R; ++r) tr += S[r * R + r];
     // reading: rho = trace(S) / R; an all-zero S (no information) uses rho = 1
-    s_rho = tr > 0.0 ? tr / R : 1.0;
+    s_rho = ucp ? 0.0 : (tr > 0.0 ? tr / R : 1.0);
     s_bad = 0;
   }
   __syncthreads();
@@ -439,6 +442,316 @@ __global__ void set_int_kernel(int32_t* p, int v, int n) {
   if (i < n) p[i] = v;
 }
 
+// ---- UCP (unconstrained, Sec. 6): Hhat = M S^{-1}, one row per thread ----------------
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+nls_ucp_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ H,
+               const double* __restrict__ scr, int* __restrict__ flags) {
+  __shared__ TA Ws[RP * RP];
+  const TA* Wt = (const TA*)(scr + ADMM_W + R * R);
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+    const int i = e / RP, j = e - i * RP;
+    Ws[e] = (i < R && j < R) ? Wt[i * R + j] : TA(0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && scr[1] != 0.0 && flags) atomicAdd(flags + 1, 1);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  TA m[RP];
+#pragma unroll
+  for (int k = 0; k < RP; ++k) m[k] = k < R ? M[i * R + k] : TA(0);
+  for (int r = 0; r < R; ++r) {
+    TA acc = TA(0);
+#pragma unroll
+    for (int k = 0; k < RP; ++k) acc = fma(m[k], Ws[k * RP + r], acc);
+    H[i * R + r] = acc;
+  }
+}
+
+// ---- Nesterov-type update (Sec. 4.3.5, Eq. nesnls / Eq. nesinnerupd) ------------------
+// Parameters from the extreme eigenvalues mu0, L0 of S (readings): the
+// proximal weight lam_p = max(0, (L0 - kappa mu0) / (kappa - 1)) caps the
+// condition number of f_p at kappa; L = L0 + lam_p, mu = mu0 + lam_p,
+// beta = (1 - sqrt(mu/L)) / (1 + sqrt(mu/L)).  With P = I - (S + lam_p I)/L
+// and b = (M + lam_p H*)/L one step is X_{k+1} = [Y_k P + b]_+ (the gradient
+// step of f_p at Y_k), Y_{k+1} = X_{k+1} + beta (X_{k+1} - X_k).
+// scr: [0] lam_p, [1] L, [2] beta, [3] 1/L, [4] lam_p/L, [5] 1 if L == 0;
+// scr + ADMM_W: P (FP64, R x R), then P as TA; then the step partials.
+constexpr double kNesKappa = 100.0;
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x, from the
+// signs of its leading principal minors (Sturm sequence, division-free with
+// power-of-two rescaling).
+__device__ int sturm_below(const double* d, const double* e2, int n, double x) {
+  double pm = 1.0, p = d[0] - x;
+  int c = (p < 0.0) ? 1 : 0;
+  if (p == 0.0) { c = 1; p = -1e-300; }
+  for (int i = 1; i < n; ++i) {
+    double q = fma(d[i] - x, p, -e2[i - 1] * pm);
+    pm = p;
+    p = q;
+    const bool change = (p == 0.0) ? true : ((p < 0.0) != (pm < 0.0));
+    if (p == 0.0) p = pm < 0.0 ? 1e-300 : -1e-300;
+    c += change ? 1 : 0;
+    const double a = fabs(p);
+    if (a > 0x1p+400) { p *= 0x1p-400; pm *= 0x1p-400; }
+    else if (a < 0x1p-400 && fabs(pm) < 0x1p-400) { p *= 0x1p+400; pm *= 0x1p+400; }
+  }
+  return c;
+}
+
+// One warp narrows [lo, hi] around the smallest (want_max = 0) or largest
+// eigenvalue: 32 Sturm counts per round, 13 rounds (33^13 > 2^65).
+__device__ double warp_extreme_eig(const double* d, const double* e2, int n, double lo, double hi,
+                                   bool want_max) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 13; ++round) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + w * (lane + 1);
+    const int c = sturm_below(d, e2, n, x);
+    const bool past = want_max ? (c >= n) : (c >= 1);
+    const unsigned m = __ballot_sync(0xffffffffu, past);
+    const double xs = __shfl_sync(0xffffffffu, x, m ? (__ffs(m) - 1) : 0);
+    const double xp = __shfl_sync(0xffffffffu, x, m ? max(__ffs(m) - 2, 0) : 31);
+    if (m == 0) {
+      lo = xp;
+    } else {
+      if (__ffs(m) > 1) lo = xp;
+      hi = xs;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// One CTA of 256 threads: S -> tridiagonal (Householder, FP64), the two
+// extreme eigenvalues (warps 0 and 1), the step parameters and P.
+__global__ void __launch_bounds__(256)
+nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64,
+                double kappa) {
+  extern __shared__ double nsm[];
+  double* A = nsm;              // R x R working copy of S
+  double* v = A + R * R;        // Householder vector
+  double* pw = v + 64;          // p, then w
+  double* d = pw + 64;          // diagonal
+  double* e2 = d + 64;          // squared off-diagonal
+  __shared__ double s_sig, s_tau, s_K, s_ev[2];
+  __shared__ int s_skip;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < R * R; e += nt) A[e] = S[e];
+  __syncthreads();
+  for (int k = 0; k + 2 < R; ++k) {
+    const int m = R - k - 1;  // x = A[k+1.., k]
+    if (tid < 32) {
+      double ss = 0.0;
+      for (int i = tid + 1; i < m; i += 32) {
+        const double x = A[(k + 1 + i) * R + k];
+        ss = fma(x, x, ss);
+      }
+      ss = warp_sum(ss);
+      if (tid == 0) {
+        const double x0 = A[(k + 1) * R + k];
+        if (ss == 0.0) {
+          s_skip = 1;
+          s_sig = x0;
+        } else {
+          const double alpha = sqrt(fma(x0, x0, ss));
+          const double sig = x0 >= 0.0 ? -alpha : alpha;
+          const double v0 = x0 - sig;
+          s_sig = sig;
+          s_tau = 2.0 / fma(v0, v0, ss);
+          s_skip = 0;
+          v[0] = v0;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_skip) {
+      if (tid == 0) e2[k] = s_sig * s_sig;
+      __syncthreads();
+      continue;
+    }
+    for (int i = 1 + tid; i < m; i += nt) v[i] = A[(k + 1 + i) * R + k];
+    __syncthreads();
+    // p = tau A_sub v: four threads per row
+    const double tau = s_tau;
+    {
+      const int i = tid >> 2, q = tid & 3;
+      double acc = 0.0;
+      if (i < m)
+        for (int j = q; j < m; j += 4) acc = fma(A[(k + 1 + i) * R + k + 1 + j], v[j], acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (i < m && q == 0) pw[i] = tau * acc;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double vp = 0.0;
+      for (int i = tid; i < m; i += 32) vp = fma(v[i], pw[i], vp);
+      vp = warp_sum(vp);
+      if (tid == 0) s_K = 0.5 * tau * vp;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) pw[i] = fma(-s_K, v[i], pw[i]);  // w = p - K v
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e - i * m;
+      double& a = A[(k + 1 + i) * R + k + 1 + j];
+      a = fma(-v[i], pw[j], fma(-pw[i], v[j], a));
+    }
+    if (tid == 0) e2[k] = s_sig * s_sig;
+    __syncthreads();
+  }
+  for (int i = tid; i < R; i += nt) d[i] = A[i * R + i];
+  if (tid == 0 && R >= 2) {
+    const double x = A[(R - 1) * R + R - 2];
+    e2[R - 2] = x * x;
+  }
+  __syncthreads();
+  // Gershgorin interval; the tridiagonal is scaled by its bound g (so the
+  // Sturm minors stay in range), then the two extremes are found
+  __shared__ double s_g;
+  if (tid == 0) {
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < R; ++i) {
+      double rad = 0.0;
+      if (i > 0) rad += sqrt(e2[i - 1]);
+      if (i + 1 < R) rad += sqrt(e2[i]);
+      lo = fmin(lo, d[i] - rad);
+      hi = fmax(hi, d[i] + rad);
+    }
+    s_g = fmax(fabs(lo), fabs(hi));
+  }
+  __syncthreads();
+  const double g = s_g;
+  if (g > 0.0) {
+    for (int i = tid; i < R; i += nt) {
+      d[i] /= g;
+      if (i + 1 < R) e2[i] /= g * g;
+    }
+  }
+  __syncthreads();
+  if (tid < 64) {
+    double ev = 0.0;
+    if (g > 0.0) {
+      // scaled spectrum lies in [-1, 1]
+      ev = g * warp_extreme_eig(d, e2, R, -1.0 - 1e-12, 1.0 + 1e-12, tid >= 32);
+    }
+    if ((tid & 31) == 0) s_ev[tid >> 5] = ev;
+  }
+  __syncthreads();
+  const double mu0 = fmax(s_ev[0], 0.0), L0 = fmax(s_ev[1], 0.0);
+  const double lam_p = fmax(0.0, (L0 - kappa * mu0) / (kappa - 1.0));
+  const double L = L0 + lam_p, mu = mu0 + lam_p;
+  const bool skip = !(L > 0.0);
+  if (tid == 0) {
+    const double sq = skip ? 1.0 : sqrt(mu / L);
+    scr[0] = lam_p;
+    scr[1] = L;
+    scr[2] = skip ? 0.0 : (1.0 - sq) / (1.0 + sq);
+    scr[3] = skip ? 0.0 : 1.0 / L;
+    scr[4] = skip ? 0.0 : lam_p / L;
+    scr[5] = skip ? 1.0 : 0.0;
+  }
+  double* P = scr + ADMM_W;
+  for (int e = tid; e < R * R; e += nt) {
+    const int i = e / R, j = e - i * R;
+    double x = 0.0;
+    if (!skip) x = (i == j ? 1.0 : 0.0) - (S[e] + (i == j ? lam_p : 0.0)) / L;
+    P[e] = x;
+    if (wtf_f64) ((double*)(P + R * R))[e] = x;
+    else ((float*)(P + R * R))[e] = (float)x;
+  }
+}
+
+// Inner step k (0-based) of at most kmax, one row per thread.  H holds X_k
+// (the warm start before step 0) and receives X_{k+1}; Y holds Y_k; Hs keeps
+// H* = H diag(lam), written by step 0.  part: per block and step, the largest
+// |X_{k+1} - Y_k| and the largest |X_{k+1}|; a step runs only if no earlier
+// step met max|X_{j+1} - Y_j| <= tol max|X_{j+1}|.
+template <typename TA, int RP>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+nes_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ H,
+                TA* __restrict__ Y, TA* __restrict__ Hs, const double* __restrict__ lam,
+                const double* __restrict__ scr, double* __restrict__ part, int nblk, int k,
+                double tol, int32_t* __restrict__ inner) {
+  extern __shared__ __align__(16) unsigned char nes_smem[];
+  TA* Ps = reinterpret_cast<TA*>(nes_smem);  // RP x RP
+  TA* yv = Ps + RP * RP;                     // RP x ROWS_PER_CTA
+  __shared__ int s_stop;
+  const int tid = threadIdx.x;
+  const bool skip = scr[5] != 0.0;
+  if (tid == 0) {
+    int stop = (skip && k > 0) ? 1 : 0;
+    for (int j = 0; j < k && !stop; ++j) {
+      double a = 0.0, b = 0.0;
+      const double* pj = part + (int64_t)j * nblk * 2;
+      for (int bl = 0; bl < nblk; ++bl) {
+        a = fmax(a, pj[bl * 2 + 0]);
+        b = fmax(b, pj[bl * 2 + 1]);
+      }
+      if (a <= tol * b) stop = 1;
+    }
+    s_stop = stop;
+  }
+  const TA* Pt = (const TA*)(scr + ADMM_W + R * R);
+  for (int e = tid; e < RP * RP; e += blockDim.x) {
+    const int i = e / RP, j = e - i * RP;
+    Ps[e] = (i < R && j < R) ? Pt[i * R + j] : TA(0);
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+  TA dmax = TA(0), xmax = TA(0);
+  if (i < rows) {
+    TA y[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      TA t = TA(0);
+      if (r < R) {
+        if (k == 0) {
+          t = H[i * R + r];
+          if (lam) t = (TA)((double)t * lam[r]);
+          Hs[i * R + r] = t;
+        } else {
+          t = Y[i * R + r];
+        }
+      }
+      y[r] = t;
+      rowv(yv, r) = t;
+    }
+    if (skip) {  // S = 0: H* unchanged
+      for (int r = 0; r < R; ++r) H[i * R + r] = rowv(yv, r);
+    } else {
+      const TA invL = (TA)scr[3], lpL = (TA)scr[4], beta = (TA)scr[2];
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const TA yr = rowv(yv, r);
+        const TA hs = k == 0 ? yr : Hs[i * R + r];
+        const TA xo = k == 0 ? yr : H[i * R + r];
+        const TA b = fma(M[i * R + r], invL, hs * lpL);
+        TA xn = dot_row<TA, RP>(y, Ps + r * RP) + b;  // P symmetric
+        xn = xn > TA(0) ? xn : TA(0);
+        H[i * R + r] = xn;
+        Y[i * R + r] = fma(beta, xn - xo, xn);
+        const TA dd = xn > yr ? xn - yr : yr - xn;
+        dmax = dd > dmax ? dd : dmax;
+        xmax = xn > xmax ? xn : xmax;
+      }
+    }
+  }
+  double a = (double)dmax, b = (double)xmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if (tid == 0) {
+    part[((int64_t)k * nblk + blockIdx.x) * 2 + 0] = a;
+    part[((int64_t)k * nblk + blockIdx.x) * 2 + 1] = b;
+    if (blockIdx.x == 0 && inner) *inner = skip ? 0 : k + 1;
+  }
+}
+
 template <typename TA, int RP>
 cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
   const int blocks = (int)((a.rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
@@ -464,7 +777,7 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
       size_t smem = 2 * (size_t)a.R * a.R * sizeof(double);
       cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-      admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8);
+      admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, 0);
       note_launches(1);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -482,6 +795,39 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
+    }
+    case PLANC_NES: {
+      const size_t psm = ((size_t)a.R * a.R + 4 * 64) * sizeof(double);
+      cudaFuncSetAttribute(nes_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)psm);
+      nes_prep_kernel<<<1, 256, psm, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, kNesKappa);
+      note_launches(1);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      double* part = a.scratch + ADMM_W + 2 * (size_t)a.R * a.R;
+      const int kmax = std::min(PLANC_MAX_NES_STEPS, std::max(1, a.opts.nes_max_inner));
+      const size_t ssm = (size_t)(RP * RP + RP * ROWS_PER_CTA) * sizeof(TA);
+      cudaFuncSetAttribute(nes_step_kernel<TA, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ssm);
+      for (int k = 0; k < kmax; ++k) {
+        nes_step_kernel<TA, RP><<<blocks, ROWS_PER_CTA, ssm, st>>>(
+            a.rows, a.R, M, H, (TA*)a.U, (TA*)a.V, a.lambda, a.scratch, part, blocks, k,
+            a.opts.nes_tol, a.inner);
+        note_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    case PLANC_UCP: {
+      size_t smem = 2 * (size_t)a.R * a.R * sizeof(double);
+      cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, 1);
+      nls_ucp_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(a.rows, a.R, M, H, a.scratch,
+                                                             a.flags);
+      note_launches(2);
+      break;
     }
     default:
       return cudaErrorInvalidValue;
@@ -506,7 +852,7 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
     note_launches(1);
     return cudaGetLastError();
   }
-  if (a.inner && a.alg != PLANC_ADMM) {
+  if (a.inner && a.alg != PLANC_ADMM && a.alg != PLANC_NES) {
     int v = a.alg == PLANC_PGD ? std::max(1, a.opts.pgd_steps) : 1;
     set_int_kernel<<<1, 32, 0, st>>>(a.inner, v, 1);
     note_launches(1);
@@ -520,7 +866,9 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
 
 size_t nls_scratch_doubles(int64_t rows, int R) {
   int64_t blocks = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
-  return ADMM_W + 2 * (size_t)R * R + (size_t)PLANC_MAX_ADMM_STEPS * blocks * 4 + 64;
+  const size_t per_block = std::max<size_t>((size_t)PLANC_MAX_ADMM_STEPS * 4,
+                                             (size_t)PLANC_MAX_NES_STEPS * 2);
+  return ADMM_W + 2 * (size_t)R * R + per_block * blocks + 64;
 }
 
 cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st) {

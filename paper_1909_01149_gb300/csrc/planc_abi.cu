@@ -196,6 +196,8 @@ planc_nls_opts planc_nls_opts_default(void) {
   o.admm_tol = 1e-2;
   o.bpp_max_iter = 0;
   o.pgd_steps = 1;
+  o.nes_max_inner = 20;
+  o.nes_tol = 1e-3;
   return o;
 }
 
@@ -207,6 +209,7 @@ planc_solve_opts planc_solve_opts_default(void) {
   o.nls = planc_nls_opts_default();
   o.use_graph = 1;
   o.profile = 0;
+  o.nes_accel = 1;
   return o;
 }
 
@@ -333,6 +336,16 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   add(64 * sizeof(int));                    // tc_err
   add((size_t)ctx->max_dim * R * fs);       // Mbuf
   add((size_t)ctx->max_dim * R * fs);       // Ubuf
+  add((size_t)ctx->max_dim * R * fs);       // Vbuf
+  for (int k = 0; k < N; ++k) {
+    add((size_t)dims[k] * R * fs);          // Hprev[k]
+    add((size_t)dims[k] * R * fs);          // Hcand[k]
+  }
+  add((size_t)R * 8);                       // lam_prev
+  add((size_t)R * 8);                       // lam_cand
+  add((size_t)N * R * 8);                   // nu
+  add((size_t)N * R * R * 8);               // Gc
+  add((size_t)(ctx->hist_cap / 3) * 4);     // accel_hist
   add((size_t)N * R * R * 8);               // G
   add((size_t)N * R * R * 4);               // G in FP32
   add((size_t)R * R * 8);                   // S
@@ -360,6 +373,16 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
   ctx->tc_err = (int*)carve(p, 64 * sizeof(int));
   ctx->Mbuf = carve(p, (size_t)ctx->max_dim * R * fs);
   ctx->Ubuf = carve(p, (size_t)ctx->max_dim * R * fs);
+  ctx->Vbuf = carve(p, (size_t)ctx->max_dim * R * fs);
+  for (int k = 0; k < N; ++k) {
+    ctx->Hprev[k] = carve(p, (size_t)dims[k] * R * fs);
+    ctx->Hcand[k] = carve(p, (size_t)dims[k] * R * fs);
+  }
+  ctx->lam_prev = (double*)carve(p, (size_t)R * 8);
+  ctx->lam_cand = (double*)carve(p, (size_t)R * 8);
+  ctx->nu = (double*)carve(p, (size_t)N * R * 8);
+  ctx->Gc = (double*)carve(p, (size_t)N * R * R * 8);
+  ctx->accel_hist = (int32_t*)carve(p, (size_t)(ctx->hist_cap / 3) * 4);
   ctx->G = (double*)carve(p, (size_t)N * R * R * 8);
   ctx->Gf = (float*)carve(p, (size_t)N * R * R * 4);
   ctx->Sm = (double*)carve(p, (size_t)R * R * 8);
@@ -522,7 +545,7 @@ planc_status_t planc_nls_update(planc_t ctx, planc_nls_t alg, const planc_nls_op
                                 int32_t* inner_iters) {
   if (!ctx) return PLANC_E_INVALID;
   if (!S || !M || !H || rows < 1) return fail(ctx, PLANC_E_INVALID, "bad arguments");
-  if ((int)alg < 0 || (int)alg > 4) return fail(ctx, PLANC_E_INVALID, "unknown NNLS algorithm");
+  if ((int)alg < 0 || (int)alg > 6) return fail(ctx, PLANC_E_INVALID, "unknown NNLS algorithm");
   if (ctx->R > PLANC_MAX_NLS_R) return fail(ctx, PLANC_E_UNSUPPORTED, "NNLS needs R <= %d", PLANC_MAX_NLS_R);
   if (rows > ctx->max_dim) return fail(ctx, PLANC_E_SHAPE, "rows > largest mode");
   NlsArgs a;
@@ -536,6 +559,7 @@ planc_status_t planc_nls_update(planc_t ctx, planc_nls_t alg, const planc_nls_op
   a.lambda = nullptr;
   a.U = aux ? aux : ctx->Ubuf;
   a.U_zero = aux == nullptr;
+  a.V = ctx->Vbuf;
   a.inner = inner_iters;
   a.scratch = ctx->nls_scr;
   a.flags = ctx->flags;
@@ -590,6 +614,51 @@ __global__ void record_kernel(const double* __restrict__ fit3, double* __restric
   *counter = it + 1;
 }
 
+// Outer acceleration of the Nesterov-type solve (Sec. 4.3.5, Eq. nesouterupd),
+// after the error of the iteration is in scal[8]: the candidate
+// [F_i + s_i (F_i - F_{i-1})]_+ (lambda absorbed into the last mode), its
+// normalisation (column norms multiplied into lambda_c) and Grams, one
+// MTTKRP for its last mode, its error by the identity of Alg. 4 in
+// scal[16], then the decision (never on the first iteration, which only
+// stores the previous iterate) and the copy of the accepted iterate into
+// H, lambda, G and the previous iterate.
+planc_status_t accelerate(planc_t ctx, void* const* H, const int* counter) {
+  const int N = ctx->N, R = ctx->R;
+  const bool f64 = is_f64(ctx);
+  AccelModes t;
+  t.N = N;
+  t.R = R;
+  t.off[0] = 0;
+  for (int k = 0; k < N; ++k) {
+    t.off[k + 1] = t.off[k] + ctx->dims[k] * R;
+    t.H[k] = H[k];
+    t.Hp[k] = ctx->Hprev[k];
+    t.Hc[k] = ctx->Hcand[k];
+  }
+  CK(launch_accel_extrapolate(f64, t, ctx->lam, ctx->lam_prev, counter, ctx->stream),
+     "extrapolate launch");
+  planc_status_t st;
+  for (int k = 0; k < N; ++k)
+    if ((st = gram_impl(ctx, ctx->dims[k], ctx->Hcand[k], ctx->Gc + (size_t)k * R * R,
+                        ctx->nu + (size_t)k * R, true, nullptr, nullptr)) != PLANC_OK)
+      return st;
+  CK(launch_accel_finish(f64, t, ctx->nu, ctx->lam_cand, ctx->stream), "lambda launch");
+  const void* cur = nullptr;
+  int cf = 0;
+  if ((st = dt_mode(ctx, ctx->Hcand, N - 1, ctx->Mbuf, &cur, &cf)) != PLANC_OK) return st;
+  const int64_t rows = ctx->dims[N - 1];
+  const int nb = rowblocks(rows);
+  double* dotp = ctx->red + (size_t)nb * R;
+  CK(launch_dot_lambda(f64, rows, R, ctx->Mbuf, ctx->Hcand[N - 1], ctx->lam_cand, dotp, nb,
+                       ctx->stream), "dot launch");
+  CK(launch_fit(R, ctx->Gc, N, ctx->lam_cand, dotp, nb, ctx->scal, ctx->scal + 16, ctx->stream),
+     "fit launch");
+  CK(launch_accel_select(f64, t, ctx->scal, counter, ctx->accel_hist, ctx->hist_cap / 3,
+                         ctx->flags, ctx->lam, ctx->lam_prev, ctx->lam_cand, ctx->G, ctx->Gf,
+                         ctx->Gc, ctx->stream), "select launch");
+  return PLANC_OK;
+}
+
 // One outer iteration (Alg. 1 "for n = 1 to N" with Alg. 4's normalisation
 // and error).  Every pointer it touches is fixed across iterations, so the
 // whole sequence can be captured once as a CUDA graph and replayed.
@@ -623,6 +692,7 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
     a.lambda = ctx->lam;  // warm start H^(n) diag(lambda)
     a.U = ctx->Ubuf;
     a.U_zero = true;
+    a.V = ctx->Vbuf;
     a.inner = inner_now + n;
     a.scratch = ctx->nls_scr;
     a.flags = ctx->flags;
@@ -645,6 +715,9 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
       CK(launch_fit(R, ctx->G, N, ctx->lam, dotp, nb, ctx->scal, ctx->scal + 8, ctx->stream),
          "fit launch");
   }
+  if (o.alg == PLANC_NES && o.nes_accel &&
+      (st = accelerate(ctx, H, counter)) != PLANC_OK)
+    return st;
   record_kernel<<<1, 1, 0, ctx->stream>>>(ctx->scal + 8, ctx->hist, inner_now, ctx->inner, N,
                                           counter, ctx->hist_cap / 3);
   note_launches(1);
@@ -664,7 +737,7 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   for (int k = 0; k < ctx->N; ++k)
     if (!H[k]) return fail(ctx, PLANC_E_INVALID, "H[%d] is NULL", k);
   if (o.iters < 0) return fail(ctx, PLANC_E_INVALID, "iters < 0");
-  if ((int)o.alg < 0 || (int)o.alg > 4) return fail(ctx, PLANC_E_INVALID, "unknown NNLS algorithm");
+  if ((int)o.alg < 0 || (int)o.alg > 6) return fail(ctx, PLANC_E_INVALID, "unknown NNLS algorithm");
   if (ctx->R > PLANC_MAX_NLS_R) return fail(ctx, PLANC_E_UNSUPPORTED, "solve needs R <= %d", PLANC_MAX_NLS_R);
   const int N = ctx->N, R = ctx->R;
   const int cap_iters = std::min(ctx->hist_cap / 3, (ctx->inner_cap - PLANC_MAX_N) / N);
@@ -682,6 +755,7 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
       return st;
   CK(cudaMemsetAsync(ctx->flags, 0, 16 * sizeof(int), ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->hist, 0, (size_t)ctx->hist_cap * 8, ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->accel_hist, 0, (size_t)(ctx->hist_cap / 3) * 4, ctx->stream), "memset");
 
   ctx->profiling = o.profile != 0;
   ctx->ev_used = 0;
@@ -733,12 +807,15 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   // results
   std::vector<double> hist((size_t)3 * std::max(done, 1), 0.0);
   std::vector<int32_t> inner((size_t)N * std::max(done, 1), 0);
+  std::vector<int32_t> accel((size_t)std::max(done, 1), 0);
   int flags[16];
   if (lambda) CK(cudaMemcpyAsync(lambda, ctx->lam, R * 8, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
   if (done > 0) {
     CK(cudaMemcpyAsync(hist.data(), ctx->hist, (size_t)3 * done * 8, cudaMemcpyDeviceToHost,
                        ctx->stream), "D2H");
     CK(cudaMemcpyAsync(inner.data(), ctx->inner, (size_t)N * done * 4, cudaMemcpyDeviceToHost,
+                       ctx->stream), "D2H");
+    CK(cudaMemcpyAsync(accel.data(), ctx->accel_hist, (size_t)done * 4, cudaMemcpyDeviceToHost,
                        ctx->stream), "D2H");
   }
   int tc_err = 0;
@@ -755,6 +832,9 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
     if (report->inner_hist)
       for (int i = 0; i < done * N; ++i) report->inner_hist[i] = inner[i];
     report->bpp_unconverged = flags[0];
+    report->accel_accepted = flags[6];
+    if (report->accel_hist)
+      for (int i = 0; i < done; ++i) report->accel_hist[i] = accel[i];
     report->launches = launches;
     report->pm_tensor_cores = (ctx->use_tc[0] ? 1 : 0) | (ctx->use_tc[1] ? 2 : 0);
     report->pm_ms = 0.f;
@@ -770,7 +850,8 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   if (tc_err != 0)
     return fail(ctx, PLANC_E_TIMEOUT,
                 "a pipeline wait gave up (code %d: 1-3 partial MTTKRP, 10 mode update)", tc_err);
-  if (flags[1] != 0) return fail(ctx, PLANC_E_NUMERIC, "BPP met a non-positive pivot in %d rows", flags[1]);
+  if (flags[1] != 0)
+    return fail(ctx, PLANC_E_NUMERIC, "a Cholesky factorisation met a non-positive pivot (%d)", flags[1]);
   return PLANC_OK;
 }
 

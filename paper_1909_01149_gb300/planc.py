@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libplanc.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "planc.h")
 
 F64, F32, BF16, F16 = 0, 1, 2, 3
-ALGS = {"mu": 0, "hals": 1, "bpp": 2, "admm": 3, "pgd": 4}
+ALGS = {"mu": 0, "hals": 1, "bpp": 2, "admm": 3, "pgd": 4, "ucp": 5, "nes": 6}
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 
@@ -37,12 +37,14 @@ class PlancError(RuntimeError):
 class NlsOpts(C.Structure):
     _fields_ = [("mu_eps", C.c_double), ("admm_max_inner", C.c_int),
                 ("admm_tol", C.c_double), ("bpp_max_iter", C.c_int),
-                ("pgd_steps", C.c_int)]
+                ("pgd_steps", C.c_int), ("nes_max_inner", C.c_int),
+                ("nes_tol", C.c_double)]
 
 
 class SolveOpts(C.Structure):
     _fields_ = [("alg", C.c_int), ("iters", C.c_int), ("tol", C.c_double),
-                ("nls", NlsOpts), ("use_graph", C.c_int), ("profile", C.c_int)]
+                ("nls", NlsOpts), ("use_graph", C.c_int), ("profile", C.c_int),
+                ("nes_accel", C.c_int)]
 
 
 class Report(C.Structure):
@@ -51,7 +53,8 @@ class Report(C.Structure):
                 ("inner_hist", C.POINTER(C.c_int32)),
                 ("bpp_unconverged", C.c_int), ("pm_ms", C.c_float),
                 ("pm_launches", C.c_int), ("launches", C.c_longlong),
-                ("pm_tensor_cores", C.c_int)]
+                ("pm_tensor_cores", C.c_int), ("accel_hist", C.POINTER(C.c_int32)),
+                ("accel_accepted", C.c_int)]
 
 
 class BatchInstance(C.Structure):
@@ -280,8 +283,10 @@ class Context:
         return e.value, f.value
 
     def solve(self, H, alg: str = "hals", iters: int = 10, tol: float = 0.0,
-              use_graph: bool = True, profile: bool = False, nls: NlsOpts | None = None):
+              use_graph: bool = True, profile: bool = False, nls: NlsOpts | None = None,
+              nes_accel: bool = True):
         o = lib.planc_solve_opts_default()
+        o.nes_accel = 1 if nes_accel else 0
         o.alg = ALGS[alg]
         o.iters = int(iters)
         o.tol = float(tol)
@@ -296,12 +301,15 @@ class Context:
         rep = Report()
         rep.rel_err_hist = C.cast(hist, C.POINTER(C.c_double))
         rep.inner_hist = C.cast(inner, C.POINTER(C.c_int32))
+        accel = (C.c_int32 * max(1, iters))()
+        rep.accel_hist = C.cast(accel, C.POINTER(C.c_int32))
         self._check(lib.planc_nncp_solve(self.h, C.byref(o), _ptrs(H), lam, C.byref(rep)))
         n = rep.iters_done
         return dict(lam=list(lam), rel_err=list(hist[:n]), inner=list(inner[:n * self.N]),
                     iters=n, fit=rep.fit, bpp_unconverged=rep.bpp_unconverged,
                     pm_ms=rep.pm_ms, pm_launches=rep.pm_launches, launches=rep.launches,
-                    use_tc=rep.pm_tensor_cores != 0, tc_mask=rep.pm_tensor_cores)
+                    use_tc=rep.pm_tensor_cores != 0, tc_mask=rep.pm_tensor_cores,
+                    accepted=[bool(a) for a in accel[:n]], accel_accepted=rep.accel_accepted)
 
     def cp_grad(self, H, dH=None):
         """Loss ||X - [[H]]||^2 (host float) and its gradients dH (device)."""

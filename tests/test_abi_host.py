@@ -88,3 +88,16 @@ def test_dimension_tree_has_two_pms_and_every_leaf(N):
         if N - S == 1:
             leaves.add(N)
         assert leaves == set(range(1, N + 1))
+
+
+def test_option_defaults_cross_the_abi():
+    """The binding's ctypes mirrors of the option structs agree with the C
+    layout: the library's defaults read back field by field."""
+    planc = _planc()
+    n = planc.lib.planc_nls_opts_default()
+    assert (n.mu_eps, n.admm_max_inner, n.admm_tol, n.bpp_max_iter, n.pgd_steps,
+            n.nes_max_inner, n.nes_tol) == (1e-16, 5, 1e-2, 0, 1, 20, 1e-3)
+    s = planc.lib.planc_solve_opts_default()
+    assert (s.alg, s.iters, s.tol, s.use_graph, s.profile, s.nes_accel) == (1, 10, 0.0, 1, 0, 1)
+    assert s.nls.nes_max_inner == 20 and s.nls.nes_tol == 1e-3
+    assert planc.ALGS["nes"] == 6 and planc.ALGS["ucp"] == 5
