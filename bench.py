@@ -430,6 +430,54 @@ def run_ablation(args):
     return out, 0
 
 
+def run_algs(args, cfg):
+    """Every update algorithm on one workload (the per-iteration comparison
+    of Sec. 6): outer iterations/s, the partial-MTTKRP share measured with
+    events, average inner steps and the final relative error."""
+    import torch
+    from paper_1909_01149_gb300 import planc, synth
+    torch.cuda.set_device(0)
+    X, H0 = make_inputs(cfg)
+    dt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cfg["dtype"]]
+    fdt = torch.float64 if cfg["dtype"] == "f64" else torch.float32
+    Xd = torch.from_numpy(synth.flat(X)).to(dt).cuda()
+    H0d = [torch.from_numpy(h).to(fdt).cuda() for h in H0]
+    H = [h.clone() for h in H0d]
+    stream = torch.cuda.current_stream()
+    ctx = planc.Context(Xd, cfg["dims"], cfg["R"], stream=stream)
+    iters = min(cfg["iters"], 20)
+    out = {"mode": "algs", "workload": cfg["workload"], "outer_iters_per_step": iters}
+    for alg in ("mu", "hals", "pgd", "ucp", "admm", "bpp", "nes"):
+        def step(profile=False):
+            for h, h0 in zip(H, H0d):
+                h.copy_(h0)
+            return ctx.solve(H, alg=alg, iters=iters, use_graph=not profile, profile=profile)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_it = e0.elapsed_time(e1) / (args.steps * iters)
+        prof = step(profile=True)
+        torch.cuda.synchronize()
+        entry = {"iter_per_s": round(1e3 / ms_it, 2), "ms_per_iter": round(ms_it, 4),
+                 "pm_ms_per_iter": round(prof["pm_ms"] / iters, 4),
+                 "avg_inner": round(float(np.mean(res["inner"])), 2),
+                 "final_rel_err": res["rel_err"][-1],
+                 "launches_per_iter": round(res["launches"] / iters, 1)}
+        if alg == "nes":
+            entry["accel_accepted"] = res["accel_accepted"]
+        out[alg] = entry
+        log(alg, entry)
+    ctx.close()
+    return out, 0
+
+
 def run_batch(args):
     """256 uneven 3-way instances (I_n ~ U{32..160}, R ~ U{8..32}, planted + 2%
     noise), HALS 25 outer iterations each: one planc_batch_solve call (all
@@ -594,19 +642,24 @@ def main():
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "pm", "grad", "batch", "ablation"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "pm", "grad", "batch", "ablation", "algs"],
                     help="pm: time only the two partial MTTKRPs (profiling aid); "
                          "grad: time the CP-loss gradient (config c4); "
                          "batch: 256 uneven instances, batched vs per-instance loop; "
-                         "ablation: dimension tree vs per-mode MTTKRP")
+                         "ablation: dimension tree vs per-mode MTTKRP; "
+                         "algs: every update algorithm on one workload")
     ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
+    ap.add_argument("--iters", type=int, default=None, help="override outer iterations per step")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3
     cfg = dict(CONFIGS[args.config])
+    if args.iters:
+        cfg["iters"] = args.iters
     if args.dims or args.rank or args.dtype:
         if args.dims:
             cfg["dims"] = tuple(int(v) for v in args.dims.split(","))
@@ -624,6 +677,8 @@ def main():
         out, rank = run_batch(args)
     elif args.mode == "ablation":
         out, rank = run_ablation(args)
+    elif args.mode == "algs":
+        out, rank = run_algs(args, cfg)
     elif args.mode == "grad":
         if args.config == "c2" and not (args.dims or args.rank or args.dtype):
             cfg = dict(CONFIGS["c4"])

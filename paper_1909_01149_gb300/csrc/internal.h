@@ -137,6 +137,10 @@ struct NlsArgs {
   bool f64;
 };
 size_t nls_scratch_doubles(int64_t rows, int R);
+// Nesterov-type update parameters from S into scr: [0] lam_p, [1] L,
+// [2] beta, [3] 1/L, [4] lam_p/L, [5] 1 if S = 0; P in the factor precision
+// at scr + 8 + R^2
+cudaError_t launch_nes_prep(bool f64, const double* S, int R, double* scr, cudaStream_t st);
 cudaError_t launch_nls(const NlsArgs& a, cudaStream_t st);
 
 // ---- fused per-mode update (S, NNLS, normalisation, Gram, error) ------------------
@@ -163,11 +167,12 @@ struct BatchInst {
 cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, planc_nls_t alg,
                               const planc_nls_opts& o, int* err, cudaStream_t st);
 int mode_batch_max_rows();
-bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R);
+bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64);
+// nes_scr: the Nesterov parameters (launch_nes_prep) when alg is NES
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, int* err, cudaStream_t st);
+                              double* fit_out, int* err, const double* nes_scr, cudaStream_t st);
 
 // ---- PM-right / mTTV split reductions -------------------------------------------
 cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,
@@ -227,6 +232,10 @@ struct planc_ctx {
   bool use_tc[2] = {false, false};
   bool fused_modes = true;
   size_t node_elems = 0;
+
+  // side stream for work that overlaps the MTTKRP (fork / join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // profiling (partial-MTTKRP launches)
   bool profiling = false;

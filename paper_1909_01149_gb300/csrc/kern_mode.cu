@@ -2,7 +2,9 @@
 // Alg. 4 that follows the MTTKRP for mode n,
 //   S^(n) = Hadamard of the other Grams,
 //   Hhat  = NNLS-Update(S^(n), M^(n)) with warm start H^(n) diag(lambda)
-//           (MU, Eq. muupd; HALS, Eq. halsupd; projected gradient),
+//           (MU, Eq. muupd; HALS, Eq. halsupd; projected gradient; the
+//           Nesterov-type steps of Eq. nesinnerupd, with the per-step stop
+//           test reduced over the cluster),
 //   lambda_r = ||Hhat(:, r)||, H^(n) = Hhat diag(lambda)^{-1}, G^(n) = H^T H,
 //   and after the last mode the error identity of Sec. A.2,
 // in a single launch of one thread-block cluster.
@@ -186,7 +188,8 @@ struct McLayout {
   static constexpr size_t oBeta = oGs + sizeof(double) * MC_CS * NPO;
   static constexpr size_t oGam = oBeta + sizeof(double) * MC_CS;
   static constexpr size_t oRed = oGam + sizeof(double) * MC_CS;
-  static constexpr size_t bytes = oRed + sizeof(double) * RED;
+  static constexpr size_t oNes = oRed + sizeof(double) * RED;  // [parity][src CTA][2]
+  static constexpr size_t bytes = oNes + sizeof(double) * 2 * MC_CS * 2;
   static_assert(MC_NT % RP == 0 && MC_NT == MC_RPC && NPO <= MC_NT, "one row / pair per thread");
 };
 
@@ -198,7 +201,8 @@ __device__ __forceinline__ void mode_update_body(
     int rows, int R, int N, int n, double* __restrict__ G, float* __restrict__ Gf,
     const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg,
     double mu_eps, int pgd_steps, double tiny, int32_t* __restrict__ inner,
-    const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err) {
+    const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err,
+    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
   extern __shared__ __align__(16) unsigned char mc_smem[];
@@ -212,6 +216,7 @@ __device__ __forceinline__ void mode_update_body(
   double* beta_slot = reinterpret_cast<double*>(mc_smem + L::oBeta);  // [src CTA] (CTA 0)
   double* gam_slot = reinterpret_cast<double*>(mc_smem + L::oGam);    // [src CTA] (CTA 0)
   double* red = reinterpret_cast<double*>(mc_smem + L::oRed);
+  double* nes_slot = reinterpret_cast<double*>(mc_smem + L::oNes);
   __shared__ double s_lam[RP], s_il[RP];
   __shared__ TA s_lamt[RP], s_inv[RP];
   __shared__ TA s_rinv[RP];  // 1 / S(r, r), or 0 where S(r, r) <= tiny (column kept)
@@ -431,6 +436,92 @@ __device__ __forceinline__ void mode_update_body(
       }
     }
   }
+  int nes_steps = 0;
+  // (compiled only where the fused path takes NES: FP32, or FP64 with R <= 16)
+  constexpr bool kNes = sizeof(TA) == 4 || RP <= 16;
+  if (kNes && alg == PLANC_NES) {
+    // P = I - (S + lam_p I) / L over Ss (S is not read again); parameters
+    // from the extreme eigenvalues of S (written to nes_scr beforehand)
+    const bool skip = nes_scr[5] != 0.0;
+    const TA lp = (TA)nes_scr[0], invL = (TA)nes_scr[3], lpL = (TA)nes_scr[4];
+    const TA nbeta = (TA)nes_scr[2];
+    for (int e = t; e < RP * RP; e += MC_NT) {
+      const int i = e / RP, k = e - i * RP;
+      TA pv = TA(0);
+      if (i < R && k < R) pv = (i == k ? TA(1) : TA(0)) - (Ss[e] + (i == k ? lp : TA(0))) * invL;
+      Ss[e] = pv;
+    }
+    __syncthreads();
+    // X_0 = Y_0 = H* (the warm start), b = (M + lam_p H*) / L; padding
+    // columns and rows stay zero throughout
+    TA y[RP], x[RP], b[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      x[r] = h[r];
+      y[r] = h[r];
+      b[r] = fma(m[r], invL, h[r] * lpL);
+    }
+    cluster_wait();  // pairs with the arrive at kernel start: every CTA is running
+    if (!skip) {
+      for (int k = 0; k < nes_kmax; ++k) {
+        TA nx[RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const TA z = srow_dot<RP>(y, s_base + (uint32_t)(r * RP * sizeof(TA))) + b[r];
+          nx[r] = z > TA(0) ? z : TA(0);  // P symmetric: row r is column r
+        }
+        TA dmax = TA(0), xmax = TA(0);
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const TA dd = nx[r] > y[r] ? nx[r] - y[r] : y[r] - nx[r];
+          dmax = dd > dmax ? dd : dmax;
+          xmax = nx[r] > xmax ? nx[r] : xmax;
+          y[r] = fma(nbeta, nx[r] - x[r], nx[r]);
+          x[r] = nx[r];
+        }
+        double da = (double)dmax, xa = (double)xmax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          da = fmax(da, __shfl_xor_sync(0xffffffffu, da, o));
+          xa = fmax(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+        }
+        if ((t & 31) == 0) {
+          red[(t >> 5) * 2 + 0] = da;
+          red[(t >> 5) * 2 + 1] = xa;
+        }
+        __syncthreads();
+        double* sl = nes_slot + (k & 1) * MC_CS * 2;
+        if (t < MC_CS) {  // thread d pushes this CTA's maxima to CTA d
+          double a = red[0], bx = red[1];
+          for (int w = 1; w < MC_NT / 32; ++w) {
+            a = fmax(a, red[w * 2 + 0]);
+            bx = fmax(bx, red[w * 2 + 1]);
+          }
+          st_cluster(sl + c * 2 + 0, (uint32_t)t, a);
+          st_cluster(sl + c * 2 + 1, (uint32_t)t, bx);
+        }
+        cluster_arrive();
+        cluster_wait();
+        double a = 0.0, bx = 0.0;  // the same slots in the same order in every CTA
+#pragma unroll
+        for (int src = 0; src < MC_CS; ++src) {
+          a = fmax(a, sl[src * 2 + 0]);
+          bx = fmax(bx, sl[src * 2 + 1]);
+        }
+        ++nes_steps;
+        if (a <= nes_tol * bx) break;
+      }
+    }
+    cluster_arrive_relaxed();  // re-pairs with the wait before the Gram exchange
+#pragma unroll
+    for (int r = 0; r < RP; ++r) h[r] = x[r];
+#pragma unroll
+    for (int g = 0; g < S::GR; ++g) {  // M again from shared memory (for <M, Hhat>)
+      const TA* ms = Ms + S::gidx(t, g);
+#pragma unroll
+      for (int u = 0; u < S::VPG; ++u) m[g * S::VPG + u] = ms[u];
+    }
+  }
   // Hhat row into shared memory (padding rows stay zero); <M, Hhat> partial
   TA beta_t = TA(0);
 #pragma unroll
@@ -545,7 +636,9 @@ __device__ __forceinline__ void mode_update_body(
       gam = (r == s ? 1.0 : 2.0) * sv * gh;
     }
   }
-  if (c == 0 && t == 0 && inner) *inner = alg == PLANC_PGD ? pgd_steps : 1;
+  if (c == 0 && t == 0 && inner)
+    *inner = alg == PLANC_PGD ? pgd_steps
+             : alg == PLANC_NES ? (nes_scr[5] != 0.0 ? 0 : nes_steps) : 1;
   if (!fit_out) return;  // uniform over the cluster: no remote access follows
   gam = warp_sum(gam);
   if ((t & 31) == 0) red[4 + (t >> 5)] = gam;
@@ -578,9 +671,10 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     float* __restrict__ Gf, const TA* __restrict__ M, TA* __restrict__ H,
                     double* __restrict__ lam, int alg, double mu_eps, int pgd_steps, double tiny,
                     int32_t* __restrict__ inner, const double* __restrict__ alpha,
-                    double* __restrict__ fit_out, int* __restrict__ err) {
+                    double* __restrict__ fit_out, int* __restrict__ err,
+                    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
   mode_update_body<TA, RP>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
-                           alpha, fit_out, err);
+                           alpha, fit_out, err, nes_scr, nes_kmax, nes_tol);
 }
 
 // Batched form: cluster b (blocks MC_CS b .. MC_CS b + MC_CS - 1) updates mode n
@@ -592,13 +686,14 @@ mode_cluster_batch_kernel(const BatchInst* __restrict__ tab, int n, int it, int 
   const BatchInst& b = tab[blockIdx.x / MC_CS];
   mode_update_body<float, 32>((int)b.I[n], b.R, 3, n, b.G, b.Gf, b.M, b.H[n], b.lam, alg, mu_eps,
                               pgd_steps, 1e-30, b.inner + 3 * it + n, b.alpha,
-                              n == 2 ? b.hist + 3 * it : nullptr, err);
+                              n == 2 ? b.hist + 3 * it : nullptr, err, nullptr, 0, 0.0);
 }
 
 template <typename TA, int RP>
 cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const void* M, void* H,
                    double* lam, planc_nls_t alg, const planc_nls_opts& o, int32_t* inner,
-                   const double* alpha, double* fit_out, int* err, cudaStream_t st) {
+                   const double* alpha, double* fit_out, int* err, const double* nes_scr,
+                   cudaStream_t st) {
   const size_t smem = McLayout<TA, RP>::bytes;
   auto kern = mode_cluster_kernel<TA, RP>;
   cudaError_t e =
@@ -618,7 +713,8 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, kern, rows, R, N, n, G, Gf, (const TA*)M, (TA*)H, lam, (int)alg,
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
-                         inner, alpha, fit_out, err);
+                         inner, alpha, fit_out, err, nes_scr,
+                         std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)), o.nes_tol);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -651,25 +747,31 @@ cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, pl
 
 int mode_batch_max_rows() { return MC_CS * MC_RPC; }
 
-bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R) {
-  return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD) && rows >= 1 &&
+bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
+  // the Nesterov steps hold four row vectors in registers: FP64 up to R = 16
+  const bool nes_ok = alg == PLANC_NES && (!f64 || R <= 16);
+  return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD || nes_ok) && rows >= 1 &&
          rows <= (int64_t)MC_CS * MC_RPC && R <= 32;
 }
 
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, int* err, cudaStream_t st) {
+                              double* fit_out, int* err, const double* nes_scr, cudaStream_t st) {
   const int r = (int)rows;
   double* Gw = const_cast<double*>(G);
   if (f64) {
     if (R <= 16)
-      return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
-    return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
+      return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
+                                nes_scr, st);
+    return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
+                              nes_scr, st);
   }
   if (R <= 16)
-    return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
-  return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err, st);
+    return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
+                             nes_scr, st);
+  return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
+                           nes_scr, st);
 }
 
 }  // namespace planc

@@ -225,6 +225,39 @@ admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, 
   if (tid == 0) { scr[0] = s_rho; scr[1] = s_bad; }
 }
 
+// Stop test of an iterative update at the start of launch k (one warp per
+// block; every block decides the same): flags[j] != 0 records that launch j
+// stopped; otherwise the block partials of step k-1 decide.  Launch 0 clears
+// the flags; a launch that stops sets its own, so later launches need only
+// one read.  part_k1 points at step k-1's partials (stride words per block).
+template <bool MAX>
+__device__ __forceinline__ bool step_stop(int k, double* flags, const double* part_k1, int nblk,
+                                          int stride, double tol, bool extra) {
+  const int lane = threadIdx.x & 31;
+  if (k == 0) {
+    if (blockIdx.x == 0)
+      for (int j = lane; j < 64; j += 32) flags[j] = 0.0;
+    return false;
+  }
+  bool stop = extra || flags[k - 1] != 0.0;
+  if (!stop) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int bl = lane; bl < nblk; bl += 32)
+      for (int q = 0; q < stride; ++q)
+        v[q] = MAX ? fmax(v[q], part_k1[bl * stride + q]) : v[q] + part_k1[bl * stride + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double w = __shfl_xor_sync(0xffffffffu, v[q], o);
+        v[q] = MAX ? fmax(v[q], w) : v[q] + w;
+      }
+    stop = MAX ? (v[0] <= tol * v[1]) : (v[0] < tol * v[1] && v[2] < tol * v[3]);
+  }
+  if (stop && blockIdx.x == 0 && lane == 0) flags[k] = 1.0;
+  return stop;
+}
+
 // step k of at most kmax; part holds 4 norms per block per step
 template <typename TA, int RP>
 __global__ void __launch_bounds__(ROWS_PER_CTA)
@@ -236,28 +269,18 @@ admm_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__
   TA* Ws = reinterpret_cast<TA*>(admm_smem);   // RP x RP
   TA* hv = Ws + RP * RP;                          // RP x ROWS_PER_CTA
   TA* uv = hv + RP * ROWS_PER_CTA;                // RP x ROWS_PER_CTA
-  __shared__ int s_stop;
   __shared__ double s_red[4][ROWS_PER_CTA];
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    int stop = 0;
-    for (int j = 0; j < k && !stop; ++j) {
-      double a = 0, b = 0, c = 0, d = 0;
-      const double* pj = part + (int64_t)j * nblk * 4;
-      for (int bl = 0; bl < nblk; ++bl) {
-        a += pj[bl * 4 + 0]; b += pj[bl * 4 + 1]; c += pj[bl * 4 + 2]; d += pj[bl * 4 + 3];
-      }
-      if (a < tol * b && c < tol * d) stop = 1;
-    }
-    s_stop = stop;
-  }
+  const bool stop = step_stop<false>(k, part + (int64_t)PLANC_MAX_ADMM_STEPS * nblk * 4,
+                                     part + (int64_t)(k > 0 ? k - 1 : 0) * nblk * 4, nblk, 4,
+                                     tol, false);
   const TA* Wt = (const TA*)(scr + ADMM_W + R * R);
   for (int e = tid; e < RP * RP; e += blockDim.x) {
     int i = e / RP, j = e - i * RP;
     Ws[e] = (i < R && j < R) ? Wt[i * R + j] : TA(0);
   }
   __syncthreads();
-  if (s_stop) return;
+  if (stop) return;
   const TA rho = (TA)scr[0];
   int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
   TA n_pr = TA(0), n_h = TA(0), n_du = TA(0), n_u = TA(0);
@@ -476,43 +499,62 @@ nls_ucp_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ H
 // and b = (M + lam_p H*)/L one step is X_{k+1} = [Y_k P + b]_+ (the gradient
 // step of f_p at Y_k), Y_{k+1} = X_{k+1} + beta (X_{k+1} - X_k).
 // scr: [0] lam_p, [1] L, [2] beta, [3] 1/L, [4] lam_p/L, [5] 1 if L == 0;
-// scr + ADMM_W: P (FP64, R x R), then P as TA; then the step partials.
+// scr + ADMM_W + R^2: P in the factor precision; then the step partials.
 constexpr double kNesKappa = 100.0;
+
+// Precision traits of the parameter computation: FP64 for FP64 factors, FP32
+// for FP32 factors (the FP64 pipe of this GPU makes the dependent chains of
+// the reduction and of the Sturm counts ~50x slower than in FP32).
+template <typename CT> struct NesCT;
+template <> struct NesCT<double> {
+  static constexpr int rounds = 13;        // 33^13 > 2^65
+  static constexpr double tiny = 1e-300;
+  static constexpr double big = 0x1p+400, small = 0x1p-400;
+  static constexpr double pad = 1e-12;
+};
+template <> struct NesCT<float> {
+  static constexpr int rounds = 6;         // 33^6 > 2^30
+  static constexpr float tiny = 1e-30f;
+  static constexpr float big = 0x1p+60f, small = 0x1p-60f;
+  static constexpr float pad = 1e-5f;
+};
 
 // Number of eigenvalues of the symmetric tridiagonal (d, e) below x, from the
 // signs of its leading principal minors (Sturm sequence, division-free with
 // power-of-two rescaling).
-__device__ int sturm_below(const double* d, const double* e2, int n, double x) {
-  double pm = 1.0, p = d[0] - x;
-  int c = (p < 0.0) ? 1 : 0;
-  if (p == 0.0) { c = 1; p = -1e-300; }
+template <typename CT>
+__device__ int sturm_below(const CT* d, const CT* e2, int n, CT x) {
+  using T = NesCT<CT>;
+  CT pm = CT(1), p = d[0] - x;
+  int c = (p < CT(0)) ? 1 : 0;
+  if (p == CT(0)) { c = 1; p = -T::tiny; }
   for (int i = 1; i < n; ++i) {
-    double q = fma(d[i] - x, p, -e2[i - 1] * pm);
+    CT q = fma(d[i] - x, p, -e2[i - 1] * pm);
     pm = p;
     p = q;
-    const bool change = (p == 0.0) ? true : ((p < 0.0) != (pm < 0.0));
-    if (p == 0.0) p = pm < 0.0 ? 1e-300 : -1e-300;
+    const bool change = (p == CT(0)) ? true : ((p < CT(0)) != (pm < CT(0)));
+    if (p == CT(0)) p = pm < CT(0) ? T::tiny : -T::tiny;
     c += change ? 1 : 0;
-    const double a = fabs(p);
-    if (a > 0x1p+400) { p *= 0x1p-400; pm *= 0x1p-400; }
-    else if (a < 0x1p-400 && fabs(pm) < 0x1p-400) { p *= 0x1p+400; pm *= 0x1p+400; }
+    const CT a = fabs(p);
+    if (a > T::big) { p *= T::small; pm *= T::small; }
+    else if (a < T::small && fabs(pm) < T::small) { p *= T::big; pm *= T::big; }
   }
   return c;
 }
 
 // One warp narrows [lo, hi] around the smallest (want_max = 0) or largest
-// eigenvalue: 32 Sturm counts per round, 13 rounds (33^13 > 2^65).
-__device__ double warp_extreme_eig(const double* d, const double* e2, int n, double lo, double hi,
-                                   bool want_max) {
+// eigenvalue: 32 Sturm counts per round.
+template <typename CT>
+__device__ CT warp_extreme_eig(const CT* d, const CT* e2, int n, CT lo, CT hi, bool want_max) {
   const int lane = threadIdx.x & 31;
-  for (int round = 0; round < 13; ++round) {
-    const double w = (hi - lo) / 33.0;
-    const double x = lo + w * (lane + 1);
-    const int c = sturm_below(d, e2, n, x);
+  for (int round = 0; round < NesCT<CT>::rounds; ++round) {
+    const CT w = (hi - lo) / CT(33);
+    const CT x = lo + w * CT(lane + 1);
+    const int c = sturm_below<CT>(d, e2, n, x);
     const bool past = want_max ? (c >= n) : (c >= 1);
     const unsigned m = __ballot_sync(0xffffffffu, past);
-    const double xs = __shfl_sync(0xffffffffu, x, m ? (__ffs(m) - 1) : 0);
-    const double xp = __shfl_sync(0xffffffffu, x, m ? max(__ffs(m) - 2, 0) : 31);
+    const CT xs = __shfl_sync(0xffffffffu, x, m ? (__ffs(m) - 1) : 0);
+    const CT xp = __shfl_sync(0xffffffffu, x, m ? max(__ffs(m) - 2, 0) : 31);
     if (m == 0) {
       lo = xp;
     } else {
@@ -520,123 +562,115 @@ __device__ double warp_extreme_eig(const double* d, const double* e2, int n, dou
       hi = xs;
     }
   }
-  return 0.5 * (lo + hi);
+  return CT(0.5) * (lo + hi);
 }
 
-// One CTA of 256 threads: S -> tridiagonal (Householder, FP64), the two
-// extreme eigenvalues (warps 0 and 1), the step parameters and P.
-__global__ void __launch_bounds__(256)
-nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64,
-                double kappa) {
-  extern __shared__ double nsm[];
-  double* A = nsm;              // R x R working copy of S
-  double* v = A + R * R;        // Householder vector
-  double* pw = v + 64;          // p, then w
-  double* d = pw + 64;          // diagonal
-  double* e2 = d + 64;          // squared off-diagonal
-  __shared__ double s_sig, s_tau, s_K, s_ev[2];
-  __shared__ int s_skip;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < R * R; e += nt) A[e] = S[e];
+// Two warps: warp 0 reduces S to tridiagonal form (Householder, lanes own
+// rows for A v and columns for the rank-2 update, warp-synchronous: no
+// block-wide barrier per column), then warps 0 and 1 find the smallest and
+// the largest eigenvalue; thread 0 writes the step parameters and all 64
+// threads P, in precision CT.
+template <typename CT>
+__global__ void __launch_bounds__(64)
+nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, double kappa) {
+  extern __shared__ __align__(16) unsigned char nes_prep_smem[];
+  CT* A = reinterpret_cast<CT*>(nes_prep_smem);  // R x R working copy of S
+  CT* v = A + R * R;        // Householder vector
+  CT* w = v + 64;           // w = p - K v
+  CT* d = w + 64;           // diagonal
+  CT* e2 = d + 64;          // squared off-diagonal
+  __shared__ double s_ev[2];
+  __shared__ CT s_g;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < R * R; e += 64) A[e] = (CT)S[e];
   __syncthreads();
-  for (int k = 0; k + 2 < R; ++k) {
-    const int m = R - k - 1;  // x = A[k+1.., k]
-    if (tid < 32) {
-      double ss = 0.0;
-      for (int i = tid + 1; i < m; i += 32) {
-        const double x = A[(k + 1 + i) * R + k];
+  if (tid < 32) {
+    for (int k = 0; k + 2 < R; ++k) {
+      const int m = R - k - 1;  // x = A[k+1.., k]
+      CT ss = CT(0);
+      for (int i = lane + 1; i < m; i += 32) {
+        const CT x = A[(k + 1 + i) * R + k];
         ss = fma(x, x, ss);
       }
       ss = warp_sum(ss);
-      if (tid == 0) {
-        const double x0 = A[(k + 1) * R + k];
-        if (ss == 0.0) {
-          s_skip = 1;
-          s_sig = x0;
-        } else {
-          const double alpha = sqrt(fma(x0, x0, ss));
-          const double sig = x0 >= 0.0 ? -alpha : alpha;
-          const double v0 = x0 - sig;
-          s_sig = sig;
-          s_tau = 2.0 / fma(v0, v0, ss);
-          s_skip = 0;
-          v[0] = v0;
-        }
+      const CT x0 = A[(k + 1) * R + k];
+      if (ss == CT(0)) {  // already reduced
+        if (lane == 0) e2[k] = x0 * x0;
+        __syncwarp();
+        continue;
       }
-    }
-    __syncthreads();
-    if (s_skip) {
-      if (tid == 0) e2[k] = s_sig * s_sig;
-      __syncthreads();
-      continue;
-    }
-    for (int i = 1 + tid; i < m; i += nt) v[i] = A[(k + 1 + i) * R + k];
-    __syncthreads();
-    // p = tau A_sub v: four threads per row
-    const double tau = s_tau;
-    {
-      const int i = tid >> 2, q = tid & 3;
-      double acc = 0.0;
-      if (i < m)
-        for (int j = q; j < m; j += 4) acc = fma(A[(k + 1 + i) * R + k + 1 + j], v[j], acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (i < m && q == 0) pw[i] = tau * acc;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      double vp = 0.0;
-      for (int i = tid; i < m; i += 32) vp = fma(v[i], pw[i], vp);
+      const CT alpha = sqrt(fma(x0, x0, ss));
+      const CT sig = x0 >= CT(0) ? -alpha : alpha;
+      const CT v0 = x0 - sig;
+      const CT tau = CT(2) / fma(v0, v0, ss);
+      for (int i = lane; i < m; i += 32) v[i] = i == 0 ? v0 : A[(k + 1 + i) * R + k];
+      __syncwarp();
+      // p = tau A_sub v: lane owns rows lane, lane + 32
+      CT p0 = CT(0), p1 = CT(0);
+      const int i0 = lane, i1 = lane + 32;
+      const CT* r0 = A + (k + 1 + i0) * R + k + 1;
+      const CT* r1 = A + (k + 1 + i1) * R + k + 1;
+      for (int j = 0; j < m; ++j) {
+        const CT vj = v[j];
+        if (i0 < m) p0 = fma(r0[j], vj, p0);
+        if (i1 < m) p1 = fma(r1[j], vj, p1);
+      }
+      p0 *= tau;
+      p1 *= tau;
+      CT vp = (i0 < m ? v[i0] * p0 : CT(0)) + (i1 < m ? v[i1] * p1 : CT(0));
       vp = warp_sum(vp);
-      if (tid == 0) s_K = 0.5 * tau * vp;
+      const CT K = CT(0.5) * tau * vp;
+      if (i0 < m) w[i0] = fma(-K, v[i0], p0);
+      if (i1 < m) w[i1] = fma(-K, v[i1], p1);
+      __syncwarp();
+      // A_sub -= v w^T + w v^T: lane owns columns lane, lane + 32
+      const CT vc0 = i0 < m ? v[i0] : CT(0), wc0 = i0 < m ? w[i0] : CT(0);
+      const CT vc1 = i1 < m ? v[i1] : CT(0), wc1 = i1 < m ? w[i1] : CT(0);
+      for (int i = 0; i < m; ++i) {
+        const CT vi = v[i], wi = w[i];
+        CT* row = A + (k + 1 + i) * R + k + 1;
+        if (i0 < m) row[i0] = fma(-vi, wc0, fma(-wi, vc0, row[i0]));
+        if (i1 < m) row[i1] = fma(-vi, wc1, fma(-wi, vc1, row[i1]));
+      }
+      if (lane == 0) e2[k] = sig * sig;
+      __syncwarp();
     }
-    __syncthreads();
-    for (int i = tid; i < m; i += nt) pw[i] = fma(-s_K, v[i], pw[i]);  // w = p - K v
-    __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e / m, j = e - i * m;
-      double& a = A[(k + 1 + i) * R + k + 1 + j];
-      a = fma(-v[i], pw[j], fma(-pw[i], v[j], a));
+    for (int i = lane; i < R; i += 32) d[i] = A[i * R + i];
+    if (lane == 0 && R >= 2) {
+      const CT x = A[(R - 1) * R + R - 2];
+      e2[R - 2] = x * x;
     }
-    if (tid == 0) e2[k] = s_sig * s_sig;
-    __syncthreads();
-  }
-  for (int i = tid; i < R; i += nt) d[i] = A[i * R + i];
-  if (tid == 0 && R >= 2) {
-    const double x = A[(R - 1) * R + R - 2];
-    e2[R - 2] = x * x;
-  }
-  __syncthreads();
-  // Gershgorin interval; the tridiagonal is scaled by its bound g (so the
-  // Sturm minors stay in range), then the two extremes are found
-  __shared__ double s_g;
-  if (tid == 0) {
-    double lo = d[0], hi = d[0];
-    for (int i = 0; i < R; ++i) {
-      double rad = 0.0;
+    __syncwarp();
+    // Gershgorin bound g; the tridiagonal is scaled by 1/g (so the Sturm
+    // minors stay in range and the spectrum lies in [-1, 1])
+    CT lo = CT(0), hi = CT(0);
+    for (int i = lane; i < R; i += 32) {
+      CT rad = CT(0);
       if (i > 0) rad += sqrt(e2[i - 1]);
       if (i + 1 < R) rad += sqrt(e2[i]);
-      lo = fmin(lo, d[i] - rad);
-      hi = fmax(hi, d[i] + rad);
+      lo = i == lane ? d[i] - rad : fmin(lo, d[i] - rad);
+      hi = i == lane ? d[i] + rad : fmax(hi, d[i] + rad);
     }
-    s_g = fmax(fabs(lo), fabs(hi));
+    CT g = lane < R ? fmax(fabs(lo), fabs(hi)) : CT(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    __syncwarp();
+    if (g > CT(0))
+      for (int i = lane; i < R; i += 32) {
+        d[i] /= g;
+        if (i + 1 < R) e2[i] /= g * g;
+      }
+    if (lane == 0) s_g = g;
   }
   __syncthreads();
-  const double g = s_g;
-  if (g > 0.0) {
-    for (int i = tid; i < R; i += nt) {
-      d[i] /= g;
-      if (i + 1 < R) e2[i] /= g * g;
-    }
-  }
-  __syncthreads();
-  if (tid < 64) {
+  const CT g = s_g;
+  {
     double ev = 0.0;
-    if (g > 0.0) {
-      // scaled spectrum lies in [-1, 1]
-      ev = g * warp_extreme_eig(d, e2, R, -1.0 - 1e-12, 1.0 + 1e-12, tid >= 32);
+    if (g > CT(0)) {
+      const CT lim = CT(1) + NesCT<CT>::pad;
+      ev = (double)g * (double)warp_extreme_eig<CT>(d, e2, R, -lim, lim, tid >= 32);
     }
-    if ((tid & 31) == 0) s_ev[tid >> 5] = ev;
+    if (lane == 0) s_ev[tid >> 5] = ev;
   }
   __syncthreads();
   const double mu0 = fmax(s_ev[0], 0.0), L0 = fmax(s_ev[1], 0.0);
@@ -652,22 +686,27 @@ nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, i
     scr[4] = skip ? 0.0 : lam_p / L;
     scr[5] = skip ? 1.0 : 0.0;
   }
-  double* P = scr + ADMM_W;
-  for (int e = tid; e < R * R; e += nt) {
+  // P = I - (S + lam_p I) / L, kept in the factor precision after scr + ADMM_W + R^2
+  const CT invL = skip ? CT(0) : (CT)(1.0 / L), lp = (CT)lam_p;
+  CT* Pt = reinterpret_cast<CT*>(scr + ADMM_W + R * R);
+  for (int e = tid; e < R * R; e += 64) {
     const int i = e / R, j = e - i * R;
-    double x = 0.0;
-    if (!skip) x = (i == j ? 1.0 : 0.0) - (S[e] + (i == j ? lam_p : 0.0)) / L;
-    P[e] = x;
-    if (wtf_f64) ((double*)(P + R * R))[e] = x;
-    else ((float*)(P + R * R))[e] = (float)x;
+    CT x = CT(0);
+    if (!skip) x = (i == j ? CT(1) : CT(0)) - ((CT)S[e] + (i == j ? lp : CT(0))) * invL;
+    Pt[e] = x;
   }
 }
 
-// Inner step k (0-based) of at most kmax, one row per thread.  H holds X_k
-// (the warm start before step 0) and receives X_{k+1}; Y holds Y_k; Hs keeps
-// H* = H diag(lam), written by step 0.  part: per block and step, the largest
-// |X_{k+1} - Y_k| and the largest |X_{k+1}|; a step runs only if no earlier
-// step met max|X_{j+1} - Y_j| <= tol max|X_{j+1}|.
+// Inner step k (0-based) of at most kmax.  H holds X_k (the warm start
+// before step 0) and receives X_{k+1}; Y holds Y_k; Hs keeps
+// H* = H diag(lam), written by step 0.  part: per block and step, the
+// largest |X_{k+1} - Y_k| and the largest |X_{k+1}|; a step runs only if no
+// earlier step met max|X_{j+1} - Y_j| <= tol max|X_{j+1}|.  A block (one
+// warp) owns 32 consecutive rows: they are staged in shared memory with
+// coalesced loads (stride-33 columns, no bank conflicts), each thread then
+// updates its row, and the results leave with coalesced stores.
+constexpr int NES_LD = ROWS_PER_CTA + 1;
+
 template <typename TA, int RP>
 __global__ void __launch_bounds__(ROWS_PER_CTA)
 nes_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ H,
@@ -676,68 +715,68 @@ nes_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__ 
                 double tol, int32_t* __restrict__ inner) {
   extern __shared__ __align__(16) unsigned char nes_smem[];
   TA* Ps = reinterpret_cast<TA*>(nes_smem);  // RP x RP
-  TA* yv = Ps + RP * RP;                     // RP x ROWS_PER_CTA
-  __shared__ int s_stop;
+  TA* yv = Ps + RP * RP;                     // Y_k, then Y_{k+1}   (column r at r * NES_LD)
+  TA* xv = yv + RP * NES_LD;                 // X_k, then X_{k+1}
+  TA* bv = xv + RP * NES_LD;                 // b = (M + lam_p H*) / L
   const int tid = threadIdx.x;
   const bool skip = scr[5] != 0.0;
-  if (tid == 0) {
-    int stop = (skip && k > 0) ? 1 : 0;
-    for (int j = 0; j < k && !stop; ++j) {
-      double a = 0.0, b = 0.0;
-      const double* pj = part + (int64_t)j * nblk * 2;
-      for (int bl = 0; bl < nblk; ++bl) {
-        a = fmax(a, pj[bl * 2 + 0]);
-        b = fmax(b, pj[bl * 2 + 1]);
-      }
-      if (a <= tol * b) stop = 1;
-    }
-    s_stop = stop;
-  }
+  const bool stop = step_stop<true>(k, part + (int64_t)PLANC_MAX_NES_STEPS * nblk * 2,
+                                    part + (int64_t)(k > 0 ? k - 1 : 0) * nblk * 2, nblk, 2,
+                                    tol, skip);
   const TA* Pt = (const TA*)(scr + ADMM_W + R * R);
   for (int e = tid; e < RP * RP; e += blockDim.x) {
     const int i = e / RP, j = e - i * RP;
     Ps[e] = (i < R && j < R) ? Pt[i * R + j] : TA(0);
   }
   __syncthreads();
-  if (s_stop) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+  if (stop) return;
+  const int64_t i0 = (int64_t)blockIdx.x * ROWS_PER_CTA;
+  const int nr = (int)min((int64_t)ROWS_PER_CTA, rows - i0);
+  const int64_t g0 = i0 * R;
+  const int ne = nr * R;
+  const TA invL = (TA)scr[3], lpL = (TA)scr[4], beta = (TA)scr[2];
+  for (int e = tid; e < ne; e += ROWS_PER_CTA) {
+    const int row = e / R, col = e - row * R;
+    TA y, xo, hs;
+    if (k == 0) {
+      TA h = H[g0 + e];
+      if (lam) h = (TA)((double)h * lam[col]);
+      Hs[g0 + e] = h;
+      y = xo = hs = h;
+    } else {
+      y = Y[g0 + e];
+      xo = H[g0 + e];
+      hs = Hs[g0 + e];
+    }
+    yv[col * NES_LD + row] = y;
+    xv[col * NES_LD + row] = xo;
+    bv[col * NES_LD + row] = fma(M[g0 + e], invL, hs * lpL);
+  }
+  __syncwarp();
   TA dmax = TA(0), xmax = TA(0);
-  if (i < rows) {
+  if (tid < nr && !skip) {
     TA y[RP];
 #pragma unroll
-    for (int r = 0; r < RP; ++r) {
-      TA t = TA(0);
-      if (r < R) {
-        if (k == 0) {
-          t = H[i * R + r];
-          if (lam) t = (TA)((double)t * lam[r]);
-          Hs[i * R + r] = t;
-        } else {
-          t = Y[i * R + r];
-        }
-      }
-      y[r] = t;
-      rowv(yv, r) = t;
-    }
-    if (skip) {  // S = 0: H* unchanged
-      for (int r = 0; r < R; ++r) H[i * R + r] = rowv(yv, r);
-    } else {
-      const TA invL = (TA)scr[3], lpL = (TA)scr[4], beta = (TA)scr[2];
+    for (int r = 0; r < RP; ++r) y[r] = r < R ? yv[r * NES_LD + tid] : TA(0);
 #pragma unroll 1
-      for (int r = 0; r < R; ++r) {
-        const TA yr = rowv(yv, r);
-        const TA hs = k == 0 ? yr : Hs[i * R + r];
-        const TA xo = k == 0 ? yr : H[i * R + r];
-        const TA b = fma(M[i * R + r], invL, hs * lpL);
-        TA xn = dot_row<TA, RP>(y, Ps + r * RP) + b;  // P symmetric
-        xn = xn > TA(0) ? xn : TA(0);
-        H[i * R + r] = xn;
-        Y[i * R + r] = fma(beta, xn - xo, xn);
-        const TA dd = xn > yr ? xn - yr : yr - xn;
-        dmax = dd > dmax ? dd : dmax;
-        xmax = xn > xmax ? xn : xmax;
-      }
+    for (int r = 0; r < R; ++r) {
+      TA xn = dot_row<TA, RP>(y, Ps + r * RP) + bv[r * NES_LD + tid];  // P symmetric
+      xn = xn > TA(0) ? xn : TA(0);
+      const TA xo = xv[r * NES_LD + tid];
+      const TA yr = yv[r * NES_LD + tid];
+      xv[r * NES_LD + tid] = xn;
+      yv[r * NES_LD + tid] = fma(beta, xn - xo, xn);
+      const TA dd = xn > yr ? xn - yr : yr - xn;
+      dmax = dd > dmax ? dd : dmax;
+      xmax = xn > xmax ? xn : xmax;
     }
+  }
+  __syncwarp();
+  // S = 0 leaves H* (the staged X_0) in place
+  for (int e = tid; e < ne; e += ROWS_PER_CTA) {
+    const int row = e / R, col = e - row * R;
+    H[g0 + e] = xv[col * NES_LD + row];
+    if (!skip) Y[g0 + e] = yv[col * NES_LD + row];
   }
   double a = (double)dmax, b = (double)xmax;
 #pragma unroll
@@ -797,16 +836,11 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
       return cudaSuccess;
     }
     case PLANC_NES: {
-      const size_t psm = ((size_t)a.R * a.R + 4 * 64) * sizeof(double);
-      cudaFuncSetAttribute(nes_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)psm);
-      nes_prep_kernel<<<1, 256, psm, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, kNesKappa);
-      note_launches(1);
-      cudaError_t e = cudaGetLastError();
+      cudaError_t e = launch_nes_prep(sizeof(TA) == 8, a.S, a.R, a.scratch, st);
       if (e != cudaSuccess) return e;
       double* part = a.scratch + ADMM_W + 2 * (size_t)a.R * a.R;
       const int kmax = std::min(PLANC_MAX_NES_STEPS, std::max(1, a.opts.nes_max_inner));
-      const size_t ssm = (size_t)(RP * RP + RP * ROWS_PER_CTA) * sizeof(TA);
+      const size_t ssm = (size_t)(RP * RP + 3 * RP * NES_LD) * sizeof(TA);
       cudaFuncSetAttribute(nes_step_kernel<TA, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ssm);
       for (int k = 0; k < kmax; ++k) {
@@ -863,6 +897,22 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_nes_prep(bool f64, const double* S, int R, double* scr, cudaStream_t st) {
+  if (f64) {
+    const size_t psm = ((size_t)R * R + 4 * 64) * sizeof(double);
+    cudaFuncSetAttribute(nes_prep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)psm);
+    nes_prep_kernel<double><<<1, 64, psm, st>>>(S, R, scr, kNesKappa);
+  } else {
+    const size_t psm = ((size_t)R * R + 4 * 64) * sizeof(float);
+    cudaFuncSetAttribute(nes_prep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)psm);
+    nes_prep_kernel<float><<<1, 64, psm, st>>>(S, R, scr, kNesKappa);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 size_t nls_scratch_doubles(int64_t rows, int R) {
   int64_t blocks = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;

@@ -406,6 +406,9 @@ planc_status_t planc_init(planc_t* out, int N, const int64_t* dims, int R, planc
 planc_status_t planc_destroy(planc_t ctx) {
   if (!ctx) return PLANC_OK;
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ws) cudaFree(ctx->ws);
   delete ctx;
   return PLANC_OK;
@@ -671,12 +674,32 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   planc_status_t st;
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
+    const bool fused = ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R, is_f64(ctx));
+    const bool fork = fused && o.alg == PLANC_NES && ctx->side;
+    if (fork) {
+      // S^(n) and the Nesterov parameters (eigenvalues of S^(n)) need only the
+      // Grams: they run on the side stream while the MTTKRP of mode n runs
+      CK(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork record");
+      CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
+      CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->side), "gram_hadamard launch");
+      CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, ctx->side), "NES prep launch");
+      CK(cudaEventRecord(ctx->ev_join, ctx->side), "join record");
+    }
     if ((st = dt_mode(ctx, H, n, ctx->Mbuf, &cur[s], &cf[s])) != PLANC_OK) return st;
     const bool last = n == N - 1;
-    if (ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R)) {
+    if (fused) {
+      if (o.alg == PLANC_NES) {
+        if (fork) {
+          CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
+        } else {
+          CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->stream), "gram_hadamard launch");
+          CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, ctx->stream), "NES prep launch");
+        }
+      }
       // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after mode N)
-      CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n], ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
-                           last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->stream),
+      CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n],
+                           ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
+                           last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->nls_scr, ctx->stream),
          "fused mode update launch");
       continue;
     }
@@ -757,6 +780,11 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   CK(cudaMemsetAsync(ctx->hist, 0, (size_t)ctx->hist_cap * 8, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->accel_hist, 0, (size_t)(ctx->hist_cap / 3) * 4, ctx->stream), "memset");
 
+  if (o.alg == PLANC_NES && ctx->side == nullptr && ctx->stream != nullptr) {
+    CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "side stream");
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event create");
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event create");
+  }
   ctx->profiling = o.profile != 0;
   ctx->ev_used = 0;
   if (ctx->profiling) {
