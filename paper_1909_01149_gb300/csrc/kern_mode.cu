@@ -52,6 +52,15 @@ __device__ __forceinline__ void st_cluster(const double* local, uint32_t rank, d
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(d), "d"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_cluster_t(const double* local, uint32_t rank, double v) {
+  st_cluster(local, rank, v);
+}
+__device__ __forceinline__ void st_cluster_t(const float* local, uint32_t rank, float v) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(d), "f"(v) : "memory");
+}
+
 // d = sum_k h[k] * S[r][k] with S row r read by explicit vector shared-memory
 // loads at the point of use (keeps the compiler from holding all of S in
 // registers when the column loop is unrolled).
@@ -479,37 +488,41 @@ __device__ __forceinline__ void mode_update_body(
           y[r] = fma(nbeta, nx[r] - x[r], nx[r]);
           x[r] = nx[r];
         }
-        double da = (double)dmax, xa = (double)xmax;
+        // maxima in the factor precision (max is exact: no FP64 work per
+        // step for FP32 factors); only the final test in FP64
+        TA da = dmax, xa = xmax;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          da = fmax(da, __shfl_xor_sync(0xffffffffu, da, o));
-          xa = fmax(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+          const TA u = __shfl_xor_sync(0xffffffffu, da, o), v = __shfl_xor_sync(0xffffffffu, xa, o);
+          da = u > da ? u : da;
+          xa = v > xa ? v : xa;
         }
+        TA* redt = reinterpret_cast<TA*>(red);
         if ((t & 31) == 0) {
-          red[(t >> 5) * 2 + 0] = da;
-          red[(t >> 5) * 2 + 1] = xa;
+          redt[(t >> 5) * 2 + 0] = da;
+          redt[(t >> 5) * 2 + 1] = xa;
         }
         __syncthreads();
-        double* sl = nes_slot + (k & 1) * MC_CS * 2;
+        TA* sl = reinterpret_cast<TA*>(nes_slot) + (k & 1) * MC_CS * 2;
         if (t < MC_CS) {  // thread d pushes this CTA's maxima to CTA d
-          double a = red[0], bx = red[1];
+          TA a = redt[0], bx = redt[1];
           for (int w = 1; w < MC_NT / 32; ++w) {
-            a = fmax(a, red[w * 2 + 0]);
-            bx = fmax(bx, red[w * 2 + 1]);
+            a = redt[w * 2 + 0] > a ? redt[w * 2 + 0] : a;
+            bx = redt[w * 2 + 1] > bx ? redt[w * 2 + 1] : bx;
           }
-          st_cluster(sl + c * 2 + 0, (uint32_t)t, a);
-          st_cluster(sl + c * 2 + 1, (uint32_t)t, bx);
+          st_cluster_t(sl + c * 2 + 0, (uint32_t)t, a);
+          st_cluster_t(sl + c * 2 + 1, (uint32_t)t, bx);
         }
         cluster_arrive();
         cluster_wait();
-        double a = 0.0, bx = 0.0;  // the same slots in the same order in every CTA
+        TA a = TA(0), bx = TA(0);  // the same slots in the same order in every CTA
 #pragma unroll
         for (int src = 0; src < MC_CS; ++src) {
-          a = fmax(a, sl[src * 2 + 0]);
-          bx = fmax(bx, sl[src * 2 + 1]);
+          a = sl[src * 2 + 0] > a ? sl[src * 2 + 0] : a;
+          bx = sl[src * 2 + 1] > bx ? sl[src * 2 + 1] : bx;
         }
         ++nes_steps;
-        if (a <= nes_tol * bx) break;
+        if ((double)a <= nes_tol * (double)bx) break;
       }
     }
     cluster_arrive_relaxed();  // re-pairs with the wait before the Gram exchange
