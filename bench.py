@@ -525,7 +525,23 @@ def run_batch(args):
                     "batched_inst_iters_per_s": round(count * iters / tb, 1),
                     "loop_inst_iters_per_s": round(count * iters / tl, 1),
                     "speedup": round(tl / tb, 2), "launches_per_solve": rep["launches"],
-                    "max_final_rel_err": round(max(r["final"] for r in res), 6)}
+                    "max_final_rel_err": round(max(r["final"] for r in res), 6),
+                    "schedule": rep["schedule"]}
+        # each rank blocking forced (same tiles): 0 pads every rank to 32
+        per = {}
+        for sched in ("0,0", "1,1", "2,2"):
+            os.environ["PLANC_BATCH_RANK_BLOCKING"] = sched
+            planc.batch_solve(Xd, fresh(), "hals", iters)
+            Hs = [fresh() for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                planc.batch_solve(Xd, Hs[k], "hals", iters)
+            torch.cuda.synchronize()
+            per[{"0,0": "pad32", "1,1": "classes16_32", "2,2": "classes8_16_32"}[sched]] = round(
+                (time.perf_counter() - t0) / args.steps, 4)
+        os.environ.pop("PLANC_BATCH_RANK_BLOCKING", None)
+        out[dtn]["batched_s_by_rank_blocking"] = per
         del Xd
     return out, 0
 

@@ -19,7 +19,16 @@ namespace planc {
 
 namespace {
 
-constexpr int BR = 32;  // rank padding of the batched kernels (R <= 32)
+constexpr int BR = 32;  // widest rank class of the batched kernels (R <= 32)
+
+// Rank blocking: an instance's partial MTTKRPs run with its rank padded to
+// the smallest class of the schedule that holds it (sched 0: 32; 1: 16, 32;
+// 2: 8, 16, 32), so small ranks do not pay for 32 columns.
+__device__ __forceinline__ int rank_class(int R, int sched) {
+  if (sched >= 2 && R <= 8) return 8;
+  if (sched >= 1 && R <= 16) return 16;
+  return 32;
+}
 
 __device__ __forceinline__ float ldx(const BatchInst& b, int64_t e) {
   if (b.xbf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(b.X)[e]);
@@ -34,10 +43,11 @@ __device__ __forceinline__ void item_run(int nitems, int& i0, int& i1) {
 }
 
 // rows f..f+nrow of a row-major nrow x R factor into shared memory with
-// stride BR (padding columns zero)
-__device__ __forceinline__ void stage_factor(float* dst, const float* H, int nrow, int R) {
-  for (int e = threadIdx.x; e < nrow * BR; e += blockDim.x) {
-    const int i = e / BR, r = e - (e / BR) * BR;
+// stride BRC (padding columns zero)
+__device__ __forceinline__ void stage_factor(float* dst, const float* H, int nrow, int R,
+                                             int BRC) {
+  for (int e = threadIdx.x; e < nrow * BRC; e += blockDim.x) {
+    const int i = e / BRC, r = e - (e / BRC) * BRC;
     dst[e] = r < R ? H[(int64_t)i * R + r] : 0.f;
   }
 }
@@ -104,12 +114,56 @@ batch_gram_kernel(const BatchInst* __restrict__ tab, int count) {
 }
 
 // ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of TL rows l) ------------
-// One thread per row l; H3 staged in shared memory (stride BR), its rows read
-// as broadcast 16-byte loads; four k steps issue their X loads together.
+// One thread per row l; H3 staged in shared memory (stride BRC, the rank
+// class), its rows read as broadcast 16-byte loads; four k steps issue their
+// X loads together.
+template <int BRC>
+__device__ __forceinline__ void left_row(const BatchInst& b, int64_t l, bool live, int64_t L,
+                                         int C, int R, const float* bsm) {
+  float acc[BRC];
+#pragma unroll
+  for (int r = 0; r < BRC; ++r) acc[r] = 0.f;
+  int k = 0;
+  for (; k + 4 <= C; k += 4) {
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BRC);
+#pragma unroll
+      for (int q = 0; q < BRC / 4; ++q) {
+        const float4 hv = h[q];
+        acc[4 * q + 0] = fmaf(x[u], hv.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(x[u], hv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(x[u], hv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(x[u], hv.w, acc[4 * q + 3]);
+      }
+    }
+  }
+  for (; k < C; ++k) {
+    const float x = live ? ldx(b, l + L * k) : 0.f;
+    const float4* h = reinterpret_cast<const float4*>(bsm + k * BRC);
+#pragma unroll
+    for (int q = 0; q < BRC / 4; ++q) {
+      const float4 hv = h[q];
+      acc[4 * q + 0] = fmaf(x, hv.x, acc[4 * q + 0]);
+      acc[4 * q + 1] = fmaf(x, hv.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(x, hv.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(x, hv.w, acc[4 * q + 3]);
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int r = 0; r < BRC; ++r)
+      if (r < R) b.T[l + L * r] = acc[r];
+  }
+}
+
 template <int TL>
 __global__ void __launch_bounds__(TL)
 batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                     int nitems) {
+                     int nitems, int sched) {
   extern __shared__ __align__(16) float bsm[];
   int i0, i1;
   item_run(nitems, i0, i1);
@@ -119,52 +173,18 @@ batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__
     const BatchInst& b = tab[bi];
     const int64_t L = b.I[0] * b.I[1];
     const int C = (int)b.I[2], R = b.R;
+    const int cls = rank_class(R, sched);
     if (bi != cur) {
       __syncthreads();
-      stage_factor(bsm, b.H[2], C, R);
+      stage_factor(bsm, b.H[2], C, R, cls);
       __syncthreads();
       cur = bi;
     }
     const int64_t l = (int64_t)items[it].y * TL + threadIdx.x;
     const bool live = l < L;
-    float acc[BR];
-#pragma unroll
-    for (int r = 0; r < BR; ++r) acc[r] = 0.f;
-    int k = 0;
-    for (; k + 4 <= C; k += 4) {
-      float x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BR);
-#pragma unroll
-        for (int q = 0; q < BR / 4; ++q) {
-          const float4 hv = h[q];
-          acc[4 * q + 0] = fmaf(x[u], hv.x, acc[4 * q + 0]);
-          acc[4 * q + 1] = fmaf(x[u], hv.y, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(x[u], hv.z, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(x[u], hv.w, acc[4 * q + 3]);
-        }
-      }
-    }
-    for (; k < C; ++k) {
-      const float x = live ? ldx(b, l + L * k) : 0.f;
-      const float4* h = reinterpret_cast<const float4*>(bsm + k * BR);
-#pragma unroll
-      for (int q = 0; q < BR / 4; ++q) {
-        const float4 hv = h[q];
-        acc[4 * q + 0] = fmaf(x, hv.x, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(x, hv.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(x, hv.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(x, hv.w, acc[4 * q + 3]);
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int r = 0; r < BR; ++r)
-        if (r < R) b.T[l + L * r] = acc[r];
-    }
+    if (cls == 8) left_row<8>(b, l, live, L, C, R, bsm);
+    else if (cls == 16) left_row<16>(b, l, live, L, C, R, bsm);
+    else left_row<32>(b, l, live, L, C, R, bsm);
   }
 }
 
@@ -184,13 +204,66 @@ __device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
 }
 
 // ---- M^(3)[c, r] = sum_{i1, i2} X[i1, i2, c] H1[i1, r] H2[i2, r]: items (b, c) ----------
-// Threads own rows i1; for each owned i1 the inner sum over i2 runs with H2
-// from shared memory and is then weighted by H1[i1, r]; the CTA's per-thread
-// sums are reduced through warp reduce-scatters and shared memory.
+// Threads own (i1, range of i2); for each the inner sum over i2 runs with H2
+// from shared memory (stride BRC, the rank class) and is then weighted by
+// H1[i1, r]; the CTA's per-thread sums are reduced through warp
+// reduce-scatters and shared memory.
+template <int NT, int BRC>
+__device__ __forceinline__ void right_sums(const BatchInst& b, int64_t c, int I1, int I2,
+                                           int64_t L, int R, const float* bsm, float* acc) {
+  // units (i1, g): thread groups g = 0..ng-1 split the i2 range of each i1 so
+  // that short modes (I1 < NT) still occupy every thread; consecutive threads
+  // take consecutive i1 (coalesced X loads)
+  const int ng = max(1, NT / I1);
+  const int js = (I2 + ng - 1) / ng;  // i2 per group
+  for (int u = threadIdx.x; u < I1 * ng; u += NT) {
+    const int i = u % I1, g = u / I1;
+    const int ja = g * js, jb = min(I2, ja + js);
+    float in[BRC];
+#pragma unroll
+    for (int r = 0; r < BRC; ++r) in[r] = 0.f;
+    const int64_t base = i + L * c;
+    int j = ja;
+    for (; j + 4 <= jb; j += 4) {
+      float x[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[v] = ldx(b, base + (int64_t)I1 * (j + v));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float4* h = reinterpret_cast<const float4*>(bsm + (j + v) * BRC);
+#pragma unroll
+        for (int q = 0; q < BRC / 4; ++q) {
+          const float4 hv = h[q];
+          in[4 * q + 0] = fmaf(x[v], hv.x, in[4 * q + 0]);
+          in[4 * q + 1] = fmaf(x[v], hv.y, in[4 * q + 1]);
+          in[4 * q + 2] = fmaf(x[v], hv.z, in[4 * q + 2]);
+          in[4 * q + 3] = fmaf(x[v], hv.w, in[4 * q + 3]);
+        }
+      }
+    }
+    for (; j < jb; ++j) {
+      const float x = ldx(b, base + (int64_t)I1 * j);
+      const float4* h = reinterpret_cast<const float4*>(bsm + j * BRC);
+#pragma unroll
+      for (int q = 0; q < BRC / 4; ++q) {
+        const float4 hv = h[q];
+        in[4 * q + 0] = fmaf(x, hv.x, in[4 * q + 0]);
+        in[4 * q + 1] = fmaf(x, hv.y, in[4 * q + 1]);
+        in[4 * q + 2] = fmaf(x, hv.z, in[4 * q + 2]);
+        in[4 * q + 3] = fmaf(x, hv.w, in[4 * q + 3]);
+      }
+    }
+    const float* h1 = b.H[0] + (int64_t)i * R;
+#pragma unroll
+    for (int r = 0; r < BRC; ++r)
+      if (r < R) acc[r] = fmaf(in[r], __ldg(h1 + r), acc[r]);
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT)
 batch_pm_right_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                      int nitems) {
+                      int nitems, int sched) {
   extern __shared__ __align__(16) float bsm[];
   __shared__ float red[NT / 32][BR];
   int i0, i1;
@@ -203,55 +276,19 @@ batch_pm_right_kernel(const BatchInst* __restrict__ tab, const int2* __restrict_
     const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
     const int64_t L = (int64_t)I1 * I2;
     const int64_t c = items[it].y;
+    const int cls = rank_class(R, sched);
     if (bi != cur) {
       __syncthreads();
-      stage_factor(bsm, b.H[1], I2, R);
+      stage_factor(bsm, b.H[1], I2, R, cls);
       __syncthreads();
       cur = bi;
     }
     float acc[BR];
 #pragma unroll
     for (int r = 0; r < BR; ++r) acc[r] = 0.f;
-    for (int i = threadIdx.x; i < I1; i += NT) {
-      float in[BR];
-#pragma unroll
-      for (int r = 0; r < BR; ++r) in[r] = 0.f;
-      const int64_t base = i + L * c;
-      int j = 0;
-      for (; j + 4 <= I2; j += 4) {
-        float x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = ldx(b, base + (int64_t)I1 * (j + u));
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4* h = reinterpret_cast<const float4*>(bsm + (j + u) * BR);
-#pragma unroll
-          for (int q = 0; q < BR / 4; ++q) {
-            const float4 hv = h[q];
-            in[4 * q + 0] = fmaf(x[u], hv.x, in[4 * q + 0]);
-            in[4 * q + 1] = fmaf(x[u], hv.y, in[4 * q + 1]);
-            in[4 * q + 2] = fmaf(x[u], hv.z, in[4 * q + 2]);
-            in[4 * q + 3] = fmaf(x[u], hv.w, in[4 * q + 3]);
-          }
-        }
-      }
-      for (; j < I2; ++j) {
-        const float x = ldx(b, base + (int64_t)I1 * j);
-        const float4* h = reinterpret_cast<const float4*>(bsm + j * BR);
-#pragma unroll
-        for (int q = 0; q < BR / 4; ++q) {
-          const float4 hv = h[q];
-          in[4 * q + 0] = fmaf(x, hv.x, in[4 * q + 0]);
-          in[4 * q + 1] = fmaf(x, hv.y, in[4 * q + 1]);
-          in[4 * q + 2] = fmaf(x, hv.z, in[4 * q + 2]);
-          in[4 * q + 3] = fmaf(x, hv.w, in[4 * q + 3]);
-        }
-      }
-      const float* h1 = b.H[0] + (int64_t)i * R;
-#pragma unroll
-      for (int r = 0; r < BR; ++r)
-        if (r < R) acc[r] = fmaf(in[r], __ldg(h1 + r), acc[r]);
-    }
+    if (cls == 8) right_sums<NT, 8>(b, c, I1, I2, L, R, bsm, acc);
+    else if (cls == 16) right_sums<NT, 16>(b, c, I1, I2, L, R, bsm, acc);
+    else right_sums<NT, 32>(b, c, I1, I2, L, R, bsm, acc);
     const float v = reduce_scatter32(acc, lane);
     red[warp][lane] = v;
     __syncthreads();
@@ -324,23 +361,24 @@ cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// tl: rows per item (64, 128 or 256); smem_floats: max C x 32 over the batch
+// tl: rows per item (64, 128 or 256); smem_floats: max C x 32 over the batch;
+// sched: rank-class schedule (see rank_class)
 cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
-                                 int grid, size_t smem_floats, cudaStream_t st) {
+                                 int grid, size_t smem_floats, int sched, cudaStream_t st) {
   const size_t smem = smem_floats * sizeof(float);
   cudaError_t e = cudaSuccess;
   switch (tl) {
     case 64:
       e = cudaFuncSetAttribute(batch_pm_left_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_left_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems, sched);
       break;
     case 128:
       e = cudaFuncSetAttribute(batch_pm_left_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_left_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems, sched);
       break;
     case 256:
       e = cudaFuncSetAttribute(batch_pm_left_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_left_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems, sched);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -350,23 +388,24 @@ cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int ni
   return cudaGetLastError();
 }
 
-// nt: threads per item (64, 128 or 256); smem_floats: max I2 x 32 over the batch
+// nt: threads per item (64, 128 or 256); smem_floats: max I2 x 32 over the batch;
+// sched: rank-class schedule (see rank_class)
 cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
-                                  int grid, size_t smem_floats, cudaStream_t st) {
+                                  int grid, size_t smem_floats, int sched, cudaStream_t st) {
   const size_t smem = smem_floats * sizeof(float);
   cudaError_t e = cudaSuccess;
   switch (nt) {
     case 64:
       e = cudaFuncSetAttribute(batch_pm_right_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_right_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems, sched);
       break;
     case 128:
       e = cudaFuncSetAttribute(batch_pm_right_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_right_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems, sched);
       break;
     case 256:
       e = cudaFuncSetAttribute(batch_pm_right_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems);
+      if (e == cudaSuccess) batch_pm_right_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems, sched);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -24,9 +25,9 @@ cudaError_t launch_batch_sqnorm(const BatchInst* tab, int count, const int2* ite
                                 const int* first, double* part, int sm_count, cudaStream_t st);
 cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st);
 cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
-                                 int grid, size_t smem_floats, cudaStream_t st);
+                                 int grid, size_t smem_floats, int sched, cudaStream_t st);
 cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
-                                  int grid, size_t smem_floats, cudaStream_t st);
+                                  int grid, size_t smem_floats, int sched, cudaStream_t st);
 cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
                                   int sm_count, cudaStream_t st);
 
@@ -42,8 +43,15 @@ struct TuneKey {
     return std::tie(count, elems, rank_sum) < std::tie(o.count, o.elems, o.rank_sum);
   }
 };
+// the schedule of the two partial MTTKRPs: tile candidate indices and rank
+// blocking (0: every rank padded to 32; 1: classes 16, 32; 2: 8, 16, 32)
+struct TuneChoice {
+  int tl = 1, nt = 1, sched_left = 2, sched_right = 2;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune;  // (left rows per item, right threads)
+std::map<TuneKey, TuneChoice> g_tune;
+thread_local TuneChoice t_last_choice;
+constexpr int kSchedules = 3;
 
 struct Alloc {
   void* p = nullptr;
@@ -125,20 +133,26 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     offHist[b] = bytes; bytes += align256((size_t)iters * 3 * 8);
     offInner[b] = bytes; bytes += align256((size_t)iters * 3 * 4);
   }
-  // work tables
+  // work tables; the partial-MTTKRP tables list the instances in rank order,
+  // so that a CTA's contiguous run of items stays within one rank class
+  std::vector<int> by_rank(count);
+  for (int b = 0; b < count; ++b) by_rank[b] = b;
+  std::stable_sort(by_rank.begin(), by_rank.end(),
+                   [&](int a, int b) { return inst[a].R < inst[b].R; });
   std::vector<int2> sq_items, right_items, rc_items;
   std::vector<int> sq_first(count + 1, 0);
   for (int b = 0; b < count; ++b) {
     const int64_t n = inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
     sq_first[b] = (int)sq_items.size();
     for (int64_t c = 0; c * 65536 < n; ++c) sq_items.push_back(make_int2(b, (int)c));
-    for (int64_t c = 0; c < inst[b].dims[2]; ++c) right_items.push_back(make_int2(b, (int)c));
     for (int r = 0; r < inst[b].R; ++r) rc_items.push_back(make_int2(b, r));
   }
+  for (int b : by_rank)
+    for (int64_t c = 0; c < inst[b].dims[2]; ++c) right_items.push_back(make_int2(b, (int)c));
   sq_first[count] = (int)sq_items.size();
   std::vector<int2> left_items[3];
   for (int t = 0; t < 3; ++t)
-    for (int b = 0; b < count; ++b) {
+    for (int b : by_rank) {
       const int64_t L = inst[b].dims[0] * inst[b].dims[1];
       for (int64_t y = 0; y * kTL[t] < L; ++y) left_items[t].push_back(make_int2(b, (int)y));
     }
@@ -213,20 +227,21 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   const int nright = (int)right_items.size(), nrc = (int)rc_items.size();
   auto grid_of = [&](int nitems) { return std::max(1, std::min(nitems, 8 * sms)); };
 
-  // ---- tile choice: timed candidates, cached per batch signature
+  // ---- schedule: every (tile, rank blocking) candidate of each partial
+  // MTTKRP timed on this batch (second of two runs), cached per batch
+  // signature
   TuneKey key{count, 0, 0};
   for (int b = 0; b < count; ++b) {
     key.elems += inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
     key.rank_sum += inst[b].R;
   }
-  int tl_idx = 1, nt_idx = 1;
+  TuneChoice ch;
   bool tuned = false;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      tl_idx = it->second.first;
-      nt_idx = it->second.second;
+      ch = it->second;
       tuned = true;
     }
   }
@@ -235,38 +250,48 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "event creation failed");
     float best_l = 1e30f, best_r = 1e30f;
-    for (int t = 0; t < 3; ++t) {
-      const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
+    auto time_it = [&](auto&& launch, float& ms) -> bool {
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, st);
-        cudaError_t ce = launch_batch_pm_left(d_tab, items, nleft[t], kTL[t], grid_of(nleft[t]),
-                                              smem_left, st);
+        const cudaError_t ce = launch();
         cudaEventRecord(e1, st);
-        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-          return bfail(PLANC_E_CUDA, "tuning launch failed");
-        float ms = 0.f;
+        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return false;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0 && ms < best_l) { best_l = ms; tl_idx = t; }
       }
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaEventRecord(e0, st);
-        cudaError_t ce = launch_batch_pm_right(d_tab, d_right, nright, kNT[t], grid_of(nright),
-                                               smem_right, st);
-        cudaEventRecord(e1, st);
-        if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-          return bfail(PLANC_E_CUDA, "tuning launch failed");
+      return true;
+    };
+    for (int t = 0; t < 3; ++t)
+      for (int sc = 0; sc < kSchedules; ++sc) {
+        const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0 && ms < best_r) { best_r = ms; nt_idx = t; }
+        if (!time_it([&] { return launch_batch_pm_left(d_tab, items, nleft[t], kTL[t],
+                                                       grid_of(nleft[t]), smem_left, sc, st); }, ms))
+          return bfail(PLANC_E_CUDA, "tuning launch failed");
+        if (ms < best_l) { best_l = ms; ch.tl = t; ch.sched_left = sc; }
+        if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, nright, kNT[t],
+                                                        grid_of(nright), smem_right, sc, st); }, ms))
+          return bfail(PLANC_E_CUDA, "tuning launch failed");
+        if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
       }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = {tl_idx, nt_idx};
+    g_tune[key] = ch;
   }
+  // PLANC_BATCH_RANK_BLOCKING="l,r" forces the rank blocking of the two
+  // kernels (tests compare every schedule; the tile choice stays tuned)
+  if (const char* env = std::getenv("PLANC_BATCH_RANK_BLOCKING")) {
+    int l = -1, r = -1;
+    if (std::sscanf(env, "%d,%d", &l, &r) == 2 && l >= 0 && l < kSchedules && r >= 0 &&
+        r < kSchedules) {
+      ch.sched_left = l;
+      ch.sched_right = r;
+    }
+  }
+  t_last_choice = ch;
+  const int tl_idx = ch.tl;
   const int2* d_left = reinterpret_cast<const int2*>(base + off_left[tl_idx]);
-  const int tl = kTL[tl_idx], nt = kNT[nt_idx];
+  const int tl = kTL[tl_idx], nt = kNT[ch.nt];
 
   const long long c_start = launch_count();
   // ---- the solve as a launch sequence
@@ -275,12 +300,12 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     if ((e = launch_batch_sqnorm(d_tab, count, d_sq, (int)sq_items.size(), d_sqf, d_sqp, sms, st)) != cudaSuccess) return e;
     if ((e = launch_batch_gram(d_tab, count, st)) != cudaSuccess) return e;
     for (int it = 0; it < iters; ++it) {
-      if ((e = launch_batch_pm_left(d_tab, d_left, nleft[tl_idx], tl, grid_of(nleft[tl_idx]), smem_left, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_left(d_tab, d_left, nleft[tl_idx], tl, grid_of(nleft[tl_idx]), smem_left, ch.sched_left, st)) != cudaSuccess) return e;
       if ((e = launch_batch_contract(d_tab, d_rc, nrc, true, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 0, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
       if ((e = launch_batch_contract(d_tab, d_rc, nrc, false, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 1, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
-      if ((e = launch_batch_pm_right(d_tab, d_right, nright, nt, grid_of(nright), smem_right, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_right(d_tab, d_right, nright, nt, grid_of(nright), smem_right, ch.sched_right, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 2, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -335,5 +360,15 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     report->launches = launches;
   }
   if (err != 0) return bfail(PLANC_E_TIMEOUT, "a bounded wait in the mode update gave up");
+  return PLANC_OK;
+}
+
+extern "C" planc_status_t planc_batch_schedule(int* out) {
+  if (!out) return PLANC_E_INVALID;
+  const planc::TuneChoice& c = planc::t_last_choice;
+  out[0] = planc::kTL[c.tl];
+  out[1] = planc::kNT[c.nt];
+  out[2] = c.sched_left;
+  out[3] = c.sched_right;
   return PLANC_OK;
 }

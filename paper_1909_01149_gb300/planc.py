@@ -96,6 +96,7 @@ def _load():
         "planc_sqnorm_noalloc": (I, [I, P, I64, P, P]),
         "planc_batch_solve": (I, [C.POINTER(BatchInstance), I, C.POINTER(SolveOpts), P,
                                   C.POINTER(Report)]),
+        "planc_batch_schedule": (I, [C.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -391,4 +392,8 @@ def batch_solve(Xs, Hs, alg: str = "hals", iters: int = 25, use_graph: bool = Tr
         raise PlancError(st, lib.planc_last_error(None).decode())
     out = [dict(lam=list(lam), rel_err=list(hist), final=arr[b].rel_err)
            for b, (lam, hist) in enumerate(keep)]
-    return out, dict(launches=rep.launches, rel_err=rep.rel_err)
+    sched = (C.c_int * 4)()
+    lib.planc_batch_schedule(sched)
+    return out, dict(launches=rep.launches, rel_err=rep.rel_err,
+                     schedule=dict(left_rows=sched[0], right_threads=sched[1],
+                                   left_rank_blocking=sched[2], right_rank_blocking=sched[3]))

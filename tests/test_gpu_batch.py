@@ -117,3 +117,34 @@ def test_batch_rejects_bad_input():
         p.batch_solve([X], [big], "hals", 2)
     with pytest.raises(ValueError):
         p.batch_solve([X], [good[:2]], "hals", 2)
+
+
+def test_batch_rank_blocking_schedules_agree(monkeypatch):
+    """Every rank blocking (all ranks padded to 32; classes 16/32; classes
+    8/16/32) gives bit-identical results (padding columns are separate
+    accumulators), and matches the oracle."""
+    p = planc()
+    Xd, Xs, H0 = _instances(8, 7, 12, 90, 1, 32)
+    outs = []
+    for sched in ("0,0", "1,1", "2,2"):
+        monkeypatch.setenv("PLANC_BATCH_RANK_BLOCKING", sched)
+        res, rep = p.batch_solve(Xd, _dev(H0), "hals", 5)
+        assert rep["schedule"]["left_rank_blocking"] == int(sched[0])
+        assert rep["schedule"]["right_rank_blocking"] == int(sched[2])
+        outs.append(res)
+    for a, b in zip(outs[0], outs[1]):
+        assert a["rel_err"] == b["rel_err"]
+    for a, b in zip(outs[0], outs[2]):
+        assert a["rel_err"] == b["rel_err"]
+    for b, (xs, h0) in enumerate(zip(Xs, _host(H0))):
+        ref = o.nncp(xs, h0, "hals", iters=5)
+        np.testing.assert_allclose(outs[2][b]["rel_err"], ref["rel_err"], rtol=0, atol=1e-4)
+
+
+def test_batch_schedule_is_reported():
+    p = planc()
+    Xd, _, H0 = _instances(4, 8, 10, 40, 2, 30)
+    _, rep = p.batch_solve(Xd, _dev(H0), "hals", 2)
+    sch = rep["schedule"]
+    assert sch["left_rows"] in (64, 128, 256) and sch["right_threads"] in (64, 128, 256)
+    assert sch["left_rank_blocking"] in (0, 1, 2) and sch["right_rank_blocking"] in (0, 1, 2)
