@@ -20,6 +20,7 @@ namespace planc {
 namespace {
 
 constexpr int BR = 32;  // widest rank class of the batched kernels (R <= 32)
+constexpr int KU = 8;   // X loads a thread keeps in flight in the partial MTTKRPs
 
 // Rank blocking: an instance's partial MTTKRPs run with its rank padded to
 // the smallest class of the schedule that holds it (sched 0: 32; 1: 16, 32;
@@ -115,7 +116,7 @@ batch_gram_kernel(const BatchInst* __restrict__ tab, int count) {
 
 // ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of TL rows l) ------------
 // One thread per row l; H3 staged in shared memory (stride BRC, the rank
-// class), its rows read as broadcast 16-byte loads; four k steps issue their
+// class), its rows read as broadcast 16-byte loads; KU k steps issue their
 // X loads together.
 template <int BRC>
 __device__ __forceinline__ void left_row(const BatchInst& b, int64_t l, bool live, int64_t L,
@@ -124,12 +125,12 @@ __device__ __forceinline__ void left_row(const BatchInst& b, int64_t l, bool liv
 #pragma unroll
   for (int r = 0; r < BRC; ++r) acc[r] = 0.f;
   int k = 0;
-  for (; k + 4 <= C; k += 4) {
-    float x[4];
+  for (; k + KU <= C; k += KU) {
+    float x[KU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
+    for (int u = 0; u < KU; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < KU; ++u) {
       const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BRC);
 #pragma unroll
       for (int q = 0; q < BRC / 4; ++q) {
@@ -224,12 +225,12 @@ __device__ __forceinline__ void right_sums(const BatchInst& b, int64_t c, int I1
     for (int r = 0; r < BRC; ++r) in[r] = 0.f;
     const int64_t base = i + L * c;
     int j = ja;
-    for (; j + 4 <= jb; j += 4) {
-      float x[4];
+    for (; j + KU <= jb; j += KU) {
+      float x[KU];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) x[v] = ldx(b, base + (int64_t)I1 * (j + v));
+      for (int v = 0; v < KU; ++v) x[v] = ldx(b, base + (int64_t)I1 * (j + v));
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < KU; ++v) {
         const float4* h = reinterpret_cast<const float4*>(bsm + (j + v) * BRC);
 #pragma unroll
         for (int q = 0; q < BRC / 4; ++q) {
