@@ -334,7 +334,8 @@ planc_status_t planc_batch_solve(planc_batch_instance* inst, int count,
 /* The schedule the most recent planc_batch_solve on the calling thread used
  * for its two partial MTTKRPs, as chosen by timing every candidate on the
  * first call for a batch signature: out[0] rows per left-branch work item
- * (64, 128, 256), out[1] threads per right-branch item (64, 128, 256),
+ * (128, 256, 512: two per thread), out[1] threads per right-branch item
+ * (64, 128, 256),
  * out[2] / out[3] the rank blocking of the left / right kernel (0: every
  * instance padded to rank 32; 1: classes 16 and 32; 2: classes 8, 16 and
  * 32; an instance runs in the smallest class that holds its rank).  The

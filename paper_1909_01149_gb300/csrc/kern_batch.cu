@@ -114,51 +114,103 @@ batch_gram_kernel(const BatchInst* __restrict__ tab, int count) {
   }
 }
 
-// ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of TL rows l) ------------
-// One thread per row l; H3 staged in shared memory (stride BRC, the rank
-// class), its rows read as broadcast 16-byte loads; KU k steps issue their
-// X loads together.
-template <int BRC>
-__device__ __forceinline__ void left_row(const BatchInst& b, int64_t l, bool live, int64_t L,
-                                         int C, int R, const float* bsm) {
-  float acc[BRC];
+// ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of 2 TL rows l) ----------
+// Each thread computes two adjacent rows l0, l0 + 1 (l0 even): both share
+// every read of H3's row k (staged in shared memory with stride BRC, the rank
+// class, read as broadcast 16-byte loads), and when L is even the two X
+// values arrive in one load (float2 / bf16x2).  KU k steps issue their X
+// loads together.
+template <bool BF16>
+__device__ __forceinline__ void ldx2(const void* X, int64_t e, bool pair, bool live0,
+                                     bool live1, float& a, float& b) {
+  if (BF16) {
+    const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(X) + e;
+    if (pair && live1) {
+      const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+      a = __low2float(v);
+      b = __high2float(v);
+    } else {
+      a = live0 ? __bfloat162float(p[0]) : 0.f;
+      b = live1 ? __bfloat162float(p[1]) : 0.f;
+    }
+  } else {
+    const float* p = reinterpret_cast<const float*>(X) + e;
+    if (pair && live1) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+      a = v.x;
+      b = v.y;
+    } else {
+      a = live0 ? __ldg(p) : 0.f;
+      b = live1 ? __ldg(p + 1) : 0.f;
+    }
+  }
+}
+
+template <int BRC, bool BF16>
+__device__ __forceinline__ void left_rows2(const BatchInst& b, int64_t l0, int64_t L, int C,
+                                           int R, const float* bsm) {
+  const bool live0 = l0 < L, live1 = l0 + 1 < L;
+  // l0 even: X[l0 + L k] starts an aligned pair for every k when L is even
+  // and X itself is aligned to a pair
+  const bool pair = (L & 1) == 0 &&
+                    (reinterpret_cast<uintptr_t>(b.X) & (BF16 ? 3u : 7u)) == 0;
+  float a0[BRC], a1[BRC];
 #pragma unroll
-  for (int r = 0; r < BRC; ++r) acc[r] = 0.f;
-  int k = 0;
-  for (; k + KU <= C; k += KU) {
-    float x[KU];
+  for (int r = 0; r < BRC; ++r) { a0[r] = 0.f; a1[r] = 0.f; }
+  if (live0) {
+    int k = 0;
+    for (; k + KU <= C; k += KU) {
+      float x0[KU], x1[KU];
 #pragma unroll
-    for (int u = 0; u < KU; ++u) x[u] = live ? ldx(b, l + L * (k + u)) : 0.f;
+      for (int u = 0; u < KU; ++u) ldx2<BF16>(b.X, l0 + L * (k + u), pair, live0, live1, x0[u], x1[u]);
 #pragma unroll
-    for (int u = 0; u < KU; ++u) {
-      const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BRC);
+      for (int u = 0; u < KU; ++u) {
+        const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BRC);
+#pragma unroll
+        for (int q = 0; q < BRC / 4; ++q) {
+          const float4 hv = h[q];
+          a0[4 * q + 0] = fmaf(x0[u], hv.x, a0[4 * q + 0]);
+          a0[4 * q + 1] = fmaf(x0[u], hv.y, a0[4 * q + 1]);
+          a0[4 * q + 2] = fmaf(x0[u], hv.z, a0[4 * q + 2]);
+          a0[4 * q + 3] = fmaf(x0[u], hv.w, a0[4 * q + 3]);
+          a1[4 * q + 0] = fmaf(x1[u], hv.x, a1[4 * q + 0]);
+          a1[4 * q + 1] = fmaf(x1[u], hv.y, a1[4 * q + 1]);
+          a1[4 * q + 2] = fmaf(x1[u], hv.z, a1[4 * q + 2]);
+          a1[4 * q + 3] = fmaf(x1[u], hv.w, a1[4 * q + 3]);
+        }
+      }
+    }
+    for (; k < C; ++k) {
+      float x0, x1;
+      ldx2<BF16>(b.X, l0 + L * k, pair, live0, live1, x0, x1);
+      const float4* h = reinterpret_cast<const float4*>(bsm + k * BRC);
 #pragma unroll
       for (int q = 0; q < BRC / 4; ++q) {
         const float4 hv = h[q];
-        acc[4 * q + 0] = fmaf(x[u], hv.x, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(x[u], hv.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(x[u], hv.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(x[u], hv.w, acc[4 * q + 3]);
+        a0[4 * q + 0] = fmaf(x0, hv.x, a0[4 * q + 0]);
+        a0[4 * q + 1] = fmaf(x0, hv.y, a0[4 * q + 1]);
+        a0[4 * q + 2] = fmaf(x0, hv.z, a0[4 * q + 2]);
+        a0[4 * q + 3] = fmaf(x0, hv.w, a0[4 * q + 3]);
+        a1[4 * q + 0] = fmaf(x1, hv.x, a1[4 * q + 0]);
+        a1[4 * q + 1] = fmaf(x1, hv.y, a1[4 * q + 1]);
+        a1[4 * q + 2] = fmaf(x1, hv.z, a1[4 * q + 2]);
+        a1[4 * q + 3] = fmaf(x1, hv.w, a1[4 * q + 3]);
       }
     }
   }
-  for (; k < C; ++k) {
-    const float x = live ? ldx(b, l + L * k) : 0.f;
-    const float4* h = reinterpret_cast<const float4*>(bsm + k * BRC);
 #pragma unroll
-    for (int q = 0; q < BRC / 4; ++q) {
-      const float4 hv = h[q];
-      acc[4 * q + 0] = fmaf(x, hv.x, acc[4 * q + 0]);
-      acc[4 * q + 1] = fmaf(x, hv.y, acc[4 * q + 1]);
-      acc[4 * q + 2] = fmaf(x, hv.z, acc[4 * q + 2]);
-      acc[4 * q + 3] = fmaf(x, hv.w, acc[4 * q + 3]);
+  for (int r = 0; r < BRC; ++r)
+    if (r < R) {
+      if (live0) b.T[l0 + L * r] = a0[r];
+      if (live1) b.T[l0 + 1 + L * r] = a1[r];
     }
-  }
-  if (live) {
-#pragma unroll
-    for (int r = 0; r < BRC; ++r)
-      if (r < R) b.T[l + L * r] = acc[r];
-  }
+}
+
+template <int BRC>
+__device__ __forceinline__ void left_rows2_dt(const BatchInst& b, int64_t l0, int64_t L, int C,
+                                              int R, const float* bsm) {
+  if (b.xbf16) left_rows2<BRC, true>(b, l0, L, C, R, bsm);
+  else left_rows2<BRC, false>(b, l0, L, C, R, bsm);
 }
 
 template <int TL>
@@ -181,11 +233,10 @@ batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__
       __syncthreads();
       cur = bi;
     }
-    const int64_t l = (int64_t)items[it].y * TL + threadIdx.x;
-    const bool live = l < L;
-    if (cls == 8) left_row<8>(b, l, live, L, C, R, bsm);
-    else if (cls == 16) left_row<16>(b, l, live, L, C, R, bsm);
-    else left_row<32>(b, l, live, L, C, R, bsm);
+    const int64_t l0 = ((int64_t)items[it].y * TL + threadIdx.x) * 2;
+    if (cls == 8) left_rows2_dt<8>(b, l0, L, C, R, bsm);
+    else if (cls == 16) left_rows2_dt<16>(b, l0, L, C, R, bsm);
+    else left_rows2_dt<32>(b, l0, L, C, R, bsm);
   }
 }
 
@@ -362,7 +413,7 @@ cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// tl: rows per item (64, 128 or 256); smem_floats: max C x 32 over the batch;
+// tl: threads per item (64, 128 or 256; two rows each); smem_floats: max C x 32 over the batch;
 // sched: rank-class schedule (see rank_class)
 cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
                                  int grid, size_t smem_floats, int sched, cudaStream_t st) {

@@ -39,8 +39,10 @@ constexpr int kNT[3] = {64, 128, 256};
 struct TuneKey {
   int count;
   long long elems, rank_sum;
+  int bf16_count;  // storage dtype mix (BF16 instances): tuned separately
   bool operator<(const TuneKey& o) const {
-    return std::tie(count, elems, rank_sum) < std::tie(o.count, o.elems, o.rank_sum);
+    return std::tie(count, elems, rank_sum, bf16_count) <
+           std::tie(o.count, o.elems, o.rank_sum, o.bf16_count);
   }
 };
 // the schedule of the two partial MTTKRPs: tile candidate indices and rank
@@ -154,7 +156,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   for (int t = 0; t < 3; ++t)
     for (int b : by_rank) {
       const int64_t L = inst[b].dims[0] * inst[b].dims[1];
-      for (int64_t y = 0; y * kTL[t] < L; ++y) left_items[t].push_back(make_int2(b, (int)y));
+      for (int64_t y = 0; y * 2 * kTL[t] < L; ++y) left_items[t].push_back(make_int2(b, (int)y));
     }
   const size_t off_tab = bytes; bytes += align256(sizeof(BatchInst) * count);
   const size_t off_sq = bytes; bytes += align256(sizeof(int2) * sq_items.size());
@@ -230,10 +232,11 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   // ---- schedule: every (tile, rank blocking) candidate of each partial
   // MTTKRP timed on this batch (second of two runs), cached per batch
   // signature
-  TuneKey key{count, 0, 0};
+  TuneKey key{count, 0, 0, 0};
   for (int b = 0; b < count; ++b) {
     key.elems += inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
     key.rank_sum += inst[b].R;
+    key.bf16_count += inst[b].x_dtype == PLANC_BF16 ? 1 : 0;
   }
   TuneChoice ch;
   bool tuned = false;
@@ -366,7 +369,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
 extern "C" planc_status_t planc_batch_schedule(int* out) {
   if (!out) return PLANC_E_INVALID;
   const planc::TuneChoice& c = planc::t_last_choice;
-  out[0] = planc::kTL[c.tl];
+  out[0] = 2 * planc::kTL[c.tl];  // two rows per thread
   out[1] = planc::kNT[c.nt];
   out[2] = c.sched_left;
   out[3] = c.sched_right;

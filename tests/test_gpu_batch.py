@@ -146,5 +146,5 @@ def test_batch_schedule_is_reported():
     Xd, _, H0 = _instances(4, 8, 10, 40, 2, 30)
     _, rep = p.batch_solve(Xd, _dev(H0), "hals", 2)
     sch = rep["schedule"]
-    assert sch["left_rows"] in (64, 128, 256) and sch["right_threads"] in (64, 128, 256)
+    assert sch["left_rows"] in (128, 256, 512) and sch["right_threads"] in (64, 128, 256)
     assert sch["left_rank_blocking"] in (0, 1, 2) and sch["right_rank_blocking"] in (0, 1, 2)
