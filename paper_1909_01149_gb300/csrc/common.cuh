@@ -15,6 +15,15 @@
 
 namespace planc {
 
+// ---- programmatic dependent launch: a kernel launched with the PDL
+// attribute starts while its predecessor in the stream finishes; it runs its
+// prologue (shared memory, barriers, TMEM), then waits here before touching
+// global data (no-op for a kernel launched without the attribute), and lets
+// its own successor launch early.  Every PDL kernel waits in every thread, so
+// completion stays ordered along the stream.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // ---- element loads: every stored tensor type is widened to its accumulator
 // type on load (F32/BF16/F16 -> float, F64 -> double).
 __device__ __forceinline__ float to_acc(float v) { return v; }

@@ -22,6 +22,24 @@ struct KrpHost {
 // Count of kernels this library has launched (all contexts); the solve
 // reports how many of its kernels ran.
 void note_launches(int n);
+// launches of the solve's hot kernels use programmatic dependent launch
+// unless PLANC_PDL=0 (read once)
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
 long long launch_count();
 
 inline size_t dtype_size(planc_dtype_t d) {

@@ -251,6 +251,8 @@ __device__ __forceinline__ void mode_update_body(
   const bool bulk = nel > 0 && (cbytes & 15u) == 0 &&
                     ((reinterpret_cast<uintptr_t>(Mrow) | reinterpret_cast<uintptr_t>(Hrow)) & 15u) == 0;
 
+  pdl_wait();  // the MTTKRP and the previous mode's Grams are complete
+  pdl_trigger();
   // every CTA of the cluster must be running before any remote store
   cluster_arrive_relaxed();
   constexpr int EPT = RP * RP / MC_NT;      // entries of S per thread
@@ -717,13 +719,15 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   cfg.blockDim = dim3(MC_NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = MC_CS;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
   e = cudaLaunchKernelEx(&cfg, kern, rows, R, N, n, G, Gf, (const TA*)M, (TA*)H, lam, (int)alg,
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
                          inner, alpha, fit_out, err, nes_scr,

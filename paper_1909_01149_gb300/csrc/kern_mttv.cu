@@ -115,6 +115,8 @@ constexpr int CR4_P = CR4_THREADS * 4;
 __global__ void __launch_bounds__(CR4_THREADS)
 contract_rest_v4_kernel(const float* __restrict__ T, int64_t P1, int64_t Q, int R, Krp<float> K,
                         int64_t qchunk, float* __restrict__ out, int to_part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float Ks[CR_QCH];
   const int r = blockIdx.y;
   const int z = blockIdx.z;
@@ -174,6 +176,8 @@ constexpr int CF4_QW = 4;  // outputs per warp
 __global__ void __launch_bounds__(CF4_THREADS)
 contract_first_v4_kernel(const float* __restrict__ T, int64_t P1, int64_t Q, int R,
                          const float* __restrict__ h, float* __restrict__ out, int rowmajor) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float4 sh4[];  // P1 / 4
   const int r = blockIdx.y;
   for (int64_t e = threadIdx.x; e < P1 / 4; e += CF4_THREADS) {
@@ -231,11 +235,11 @@ cudaError_t launch_contract_first(bool f64, const void* T, int64_t P1, int64_t Q
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(contract_first_v4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    contract_first_v4_kernel<<<grid, CF4_THREADS, smem, st>>>((const float*)T, P1, Q, R,
-                                                              (const float*)h, (float*)out,
-                                                              out_rowmajor ? 1 : 0);
+    const cudaError_t e =
+        launch_pdl(contract_first_v4_kernel, dim3(grid), dim3(CF4_THREADS), smem, st,
+                   (const float*)T, P1, Q, R, (const float*)h, (float*)out, out_rowmajor ? 1 : 0);
     note_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   int gw = 1;
   while (gw < 32 && gw < P1) gw <<= 1;
@@ -283,11 +287,11 @@ cudaError_t launch_contract_rest(bool f64, const void* T, int64_t P1, int64_t Q,
     const int64_t qchunk = (Q + qsplit - 1) / qsplit;
     dim3 grid((unsigned)((P1 + CR4_P - 1) / CR4_P), (unsigned)R, (unsigned)qsplit);
     void* dst = qsplit > 1 ? part : out;
-    contract_rest_v4_kernel<<<grid, CR4_THREADS, 0, st>>>((const float*)T, P1, Q, R,
-                                                          make_krp<float>(krp, R), qchunk,
-                                                          (float*)dst, qsplit > 1);
+    cudaError_t e = launch_pdl(contract_rest_v4_kernel, grid, dim3(CR4_THREADS), 0, st,
+                               (const float*)T, P1, Q, R, make_krp<float>(krp, R), qchunk,
+                               (float*)dst, (int)(qsplit > 1));
     note_launches(1);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess || qsplit == 1) return e;
     return launch_split_reduce(false, part, qsplit, P1, R, out, true, st);
   }

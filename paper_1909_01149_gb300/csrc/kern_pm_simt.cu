@@ -107,6 +107,8 @@ pm_simt_kernel(const TX* __restrict__ X, int64_t L, Krp<typename AccOf<TX>::type
 template <typename TA>
 __global__ void split_reduce_kernel(const TA* __restrict__ part, int nsplit, int64_t Mdim,
                                     int R, TA* __restrict__ out, int rowmajor) {
+  pdl_wait();
+  pdl_trigger();
   int64_t n = Mdim * R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -198,14 +200,15 @@ cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t 
   int64_t n = Mdim * R;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
+  cudaError_t e;
   if (f64)
-    split_reduce_kernel<double><<<blocks, 256, 0, st>>>((const double*)part, nsplit, Mdim, R,
-                                                        (double*)out, out_rowmajor ? 1 : 0);
+    e = launch_pdl(split_reduce_kernel<double>, dim3(blocks), dim3(256), 0, st,
+                   (const double*)part, nsplit, Mdim, R, (double*)out, out_rowmajor ? 1 : 0);
   else
-    split_reduce_kernel<float><<<blocks, 256, 0, st>>>((const float*)part, nsplit, Mdim, R,
-                                                       (float*)out, out_rowmajor ? 1 : 0);
-    note_launches(1);
-  return cudaGetLastError();
+    e = launch_pdl(split_reduce_kernel<float>, dim3(blocks), dim3(256), 0, st,
+                   (const float*)part, nsplit, Mdim, R, (float*)out, out_rowmajor ? 1 : 0);
+  note_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace planc

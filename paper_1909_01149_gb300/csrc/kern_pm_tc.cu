@@ -913,6 +913,8 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     *abort = 0;
     fence_mbar_init();
   }
+  pdl_wait();  // the factors of the previous mode update are complete
+  pdl_trigger();
   // H_in (d_in x R, row-major FP32) arrives by one bulk copy into the X stage
   // area (idle until the pipeline starts) when aligned and small enough; the
   // image below is then built from shared memory
@@ -1623,7 +1625,8 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(pl.items, sms);
-  k<<<grid, threads, pl.smem, st>>>(tmap, p);
+  err = launch_pdl(k, dim3(grid), dim3(threads), pl.smem, st, tmap, p);
+  if (err != cudaSuccess) return err;
   note_launches(1);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;

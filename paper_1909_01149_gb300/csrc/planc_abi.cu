@@ -18,6 +18,13 @@ namespace planc {
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("PLANC_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 }  // namespace planc
 
 namespace {
@@ -607,6 +614,7 @@ namespace {
 __global__ void record_kernel(const double* __restrict__ fit3, double* __restrict__ hist,
                               const int32_t* __restrict__ inner_now, int32_t* __restrict__ inner_hist,
                               int N, int* __restrict__ counter, int cap_iters) {
+  pdl_wait();
   int it = *counter;
   if (it < cap_iters) {
     hist[3 * it + 0] = fit3[0];
@@ -741,10 +749,10 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   if (o.alg == PLANC_NES && o.nes_accel &&
       (st = accelerate(ctx, H, counter)) != PLANC_OK)
     return st;
-  record_kernel<<<1, 1, 0, ctx->stream>>>(ctx->scal + 8, ctx->hist, inner_now, ctx->inner, N,
-                                          counter, ctx->hist_cap / 3);
+  CK(launch_pdl(record_kernel, dim3(1), dim3(1), 0, ctx->stream, (const double*)(ctx->scal + 8),
+                ctx->hist, (const int32_t*)inner_now, ctx->inner, N, counter, ctx->hist_cap / 3),
+     "record launch");
   note_launches(1);
-  CK(cudaGetLastError(), "record launch");
   return PLANC_OK;
 }
 
