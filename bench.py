@@ -166,33 +166,18 @@ def profiled_traffic(workload, sha):
 
 
 def dist_setup():
-    import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    return ws, rank, local
+    from paper_1909_01149_gb300 import replicas
+    return replicas.setup("nccl")
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1909_01149_gb300 import replicas
+    replicas.barrier(ws)
 
 
 def allreduce_max(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1909_01149_gb300 import replicas
+    return replicas.allreduce_max(x, ws, "cuda")
 
 
 # ----------------------------------------------------------------------------- arms
@@ -241,7 +226,8 @@ def run_planc(args, cfg):
     barrier(ws)
     clk = clocks.stop()
     ms = allreduce_max(e0.elapsed_time(e1), ws)
-    value = ws * args.steps * iters / (ms / 1e3)
+    from paper_1909_01149_gb300 import replicas
+    value = replicas.job_throughput(args.steps * iters, ws, ms)
     rel_err = res["rel_err"][-1]
 
     # --- partial-MTTKRP launch durations (events around each launch, same stream)
@@ -289,7 +275,7 @@ def run_planc(args, cfg):
     torch.cuda.synchronize()
     barrier(ws)
     e2e_ms = allreduce_max(f0.elapsed_time(f1), ws)
-    e2e = ws * args.steps * iters / (e2e_ms / 1e3)
+    e2e = replicas.job_throughput(args.steps * iters, ws, e2e_ms)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "iter/s", "n_gpus": ws,
@@ -706,8 +692,8 @@ def main():
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "planc":
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        from paper_1909_01149_gb300 import replicas
+        replicas.teardown(int(os.environ["WORLD_SIZE"]))
 
 
 if __name__ == "__main__":
