@@ -205,15 +205,19 @@ struct McLayout {
 // G: the N Grams (FP64, R x R each), Gf: the same in FP32.  Mode n's entries
 // of both are overwritten with G^(n) of the updated factor.  err: set to 10
 // if the wait for the bulk copies of M and H gives up.
-template <typename TA, int RP>
+// ALG >= 0 fixes the update at compile time (the kernel then carries only
+// that update's code: the launch is short and runs its code cold, so code
+// size shows up as instruction-fetch stalls); ALG < 0 dispatches on alg.
+template <typename TA, int RP, int ALG = -1>
 __device__ __forceinline__ void mode_update_body(
     int rows, int R, int N, int n, double* __restrict__ G, float* __restrict__ Gf,
-    const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg,
+    const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg_rt,
     double mu_eps, int pgd_steps, double tiny, int32_t* __restrict__ inner,
     const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err,
     const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
+  const int alg = ALG >= 0 ? ALG : alg_rt;
   extern __shared__ __align__(16) unsigned char mc_smem[];
   TA* Ss = reinterpret_cast<TA*>(mc_smem + L::oSs);                 // S^(n), RP x RP
   TA* Hs = reinterpret_cast<TA*>(mc_smem + L::oHs);                 // this CTA's rows
@@ -680,7 +684,7 @@ __device__ __forceinline__ void mode_update_body(
   }
 }
 
-template <typename TA, int RP>
+template <typename TA, int RP, int ALG>
 __global__ void __launch_bounds__(MC_NT, 1)
 mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     float* __restrict__ Gf, const TA* __restrict__ M, TA* __restrict__ H,
@@ -688,7 +692,7 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     int32_t* __restrict__ inner, const double* __restrict__ alpha,
                     double* __restrict__ fit_out, int* __restrict__ err,
                     const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
-  mode_update_body<TA, RP>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
+  mode_update_body<TA, RP, ALG>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
                            alpha, fit_out, err, nes_scr, nes_kmax, nes_tol);
 }
 
@@ -710,7 +714,10 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
                    const double* alpha, double* fit_out, int* err, const double* nes_scr,
                    cudaStream_t st) {
   const size_t smem = McLayout<TA, RP>::bytes;
-  auto kern = mode_cluster_kernel<TA, RP>;
+  auto kern = alg == PLANC_MU     ? mode_cluster_kernel<TA, RP, PLANC_MU>
+              : alg == PLANC_HALS ? mode_cluster_kernel<TA, RP, PLANC_HALS>
+              : alg == PLANC_PGD  ? mode_cluster_kernel<TA, RP, PLANC_PGD>
+                                  : mode_cluster_kernel<TA, RP, PLANC_NES>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
