@@ -186,11 +186,21 @@ cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, pl
                               const planc_nls_opts& o, int* err, cudaStream_t st);
 int mode_batch_max_rows();
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64);
+// the per-iteration history record (error triple and inner counts at index
+// *counter, then ++*counter), done by the last mode's fused update when given
+struct RecArgs {
+  double* hist = nullptr;
+  const int32_t* inner_now = nullptr;
+  int32_t* inner_hist = nullptr;
+  int* counter = nullptr;
+  int N = 0, cap = 0;
+};
 // nes_scr: the Nesterov parameters (launch_nes_prep) when alg is NES
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, int* err, const double* nes_scr, cudaStream_t st);
+                              double* fit_out, int* err, const double* nes_scr,
+                              const RecArgs& rec, cudaStream_t st);
 
 // ---- PM-right / mTTV split reductions -------------------------------------------
 cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,

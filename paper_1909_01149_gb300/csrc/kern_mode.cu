@@ -214,7 +214,8 @@ __device__ __forceinline__ void mode_update_body(
     const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg_rt,
     double mu_eps, int pgd_steps, double tiny, int32_t* __restrict__ inner,
     const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err,
-    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
+    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol,
+    const RecArgs& rec = RecArgs()) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
   const int alg = ALG >= 0 ? ALG : alg_rt;
@@ -681,6 +682,16 @@ __device__ __forceinline__ void mode_update_body(
     fit_out[0] = eps;
     fit_out[1] = beta;
     fit_out[2] = gamma;
+    if (rec.hist) {  // this iteration's history record (replaces a separate launch)
+      const int it = *rec.counter;
+      if (it < rec.cap) {
+        rec.hist[3 * it + 0] = eps;
+        rec.hist[3 * it + 1] = beta;
+        rec.hist[3 * it + 2] = gamma;
+        for (int q = 0; q < rec.N; ++q) rec.inner_hist[it * rec.N + q] = rec.inner_now[q];
+      }
+      *rec.counter = it + 1;
+    }
   }
 }
 
@@ -691,9 +702,10 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     double* __restrict__ lam, int alg, double mu_eps, int pgd_steps, double tiny,
                     int32_t* __restrict__ inner, const double* __restrict__ alpha,
                     double* __restrict__ fit_out, int* __restrict__ err,
-                    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol) {
+                    const double* __restrict__ nes_scr, int nes_kmax, double nes_tol,
+                    const __grid_constant__ RecArgs rec) {
   mode_update_body<TA, RP, ALG>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
-                           alpha, fit_out, err, nes_scr, nes_kmax, nes_tol);
+                           alpha, fit_out, err, nes_scr, nes_kmax, nes_tol, rec);
 }
 
 // Batched form: cluster b (blocks MC_CS b .. MC_CS b + MC_CS - 1) updates mode n
@@ -712,7 +724,7 @@ template <typename TA, int RP>
 cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const void* M, void* H,
                    double* lam, planc_nls_t alg, const planc_nls_opts& o, int32_t* inner,
                    const double* alpha, double* fit_out, int* err, const double* nes_scr,
-                   cudaStream_t st) {
+                   const RecArgs& rec, cudaStream_t st) {
   const size_t smem = McLayout<TA, RP>::bytes;
   auto kern = alg == PLANC_MU     ? mode_cluster_kernel<TA, RP, PLANC_MU>
               : alg == PLANC_HALS ? mode_cluster_kernel<TA, RP, PLANC_HALS>
@@ -738,7 +750,8 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   e = cudaLaunchKernelEx(&cfg, kern, rows, R, N, n, G, Gf, (const TA*)M, (TA*)H, lam, (int)alg,
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
                          inner, alpha, fit_out, err, nes_scr,
-                         std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)), o.nes_tol);
+                         std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)), o.nes_tol,
+                         rec);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -781,21 +794,22 @@ bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
-                              double* fit_out, int* err, const double* nes_scr, cudaStream_t st) {
+                              double* fit_out, int* err, const double* nes_scr,
+                              const RecArgs& rec, cudaStream_t st) {
   const int r = (int)rows;
   double* Gw = const_cast<double*>(G);
   if (f64) {
     if (R <= 16)
       return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                                nes_scr, st);
+                                nes_scr, rec, st);
     return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                              nes_scr, st);
+                              nes_scr, rec, st);
   }
   if (R <= 16)
     return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                             nes_scr, st);
+                             nes_scr, rec, st);
   return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                           nes_scr, st);
+                           nes_scr, rec, st);
 }
 
 }  // namespace planc

@@ -107,10 +107,13 @@ contract_rest_kernel(const TA* __restrict__ T, int64_t P1, int64_t Q, int R, Krp
 
 // ---- vectorised variants (FP32, P1 % 4 == 0, 16-byte aligned T) ---------------------
 // contract_rest: each thread owns four consecutive p and streams float4 loads
-// of T over its q-range, eight in flight; the Khatri-Rao values of the range
+// of T over its q-range, sixteen in flight; the Khatri-Rao values of the range
 // are staged in shared memory.
 constexpr int CR4_THREADS = 128;
 constexpr int CR4_P = CR4_THREADS * 4;
+// float4 loads a thread keeps in flight: the grid is small (P1 / 512 x R x
+// qsplit CTAs), so each thread must cover more of the HBM latency
+constexpr int CR4_INFLIGHT = 16;
 
 __global__ void __launch_bounds__(CR4_THREADS)
 contract_rest_v4_kernel(const float* __restrict__ T, int64_t P1, int64_t Q, int R, Krp<float> K,
@@ -135,12 +138,12 @@ contract_rest_v4_kernel(const float* __restrict__ T, int64_t P1, int64_t Q, int 
       const float4* base = reinterpret_cast<const float4*>(Tr + p + P1 * qc);
       const int64_t step = P1 / 4;
       int e = 0;
-      for (; e + 8 <= nq; e += 8) {
-        float4 v[8];
+      for (; e + CR4_INFLIGHT <= nq; e += CR4_INFLIGHT) {
+        float4 v[CR4_INFLIGHT];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(base + step * (e + u));
+        for (int u = 0; u < CR4_INFLIGHT; ++u) v[u] = __ldg(base + step * (e + u));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < CR4_INFLIGHT; ++u) {
           const float k = Ks[e + u];
           acc.x = fmaf(v[u].x, k, acc.x);
           acc.y = fmaf(v[u].y, k, acc.y);

@@ -680,6 +680,8 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   int* counter = ctx->flags + 4;
   int32_t* inner_now = ctx->inner + ctx->inner_cap - PLANC_MAX_N;
   planc_status_t st;
+  const bool accel = o.alg == PLANC_NES && o.nes_accel;
+  bool recorded = false;
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
     const bool fused = ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R, is_f64(ctx));
@@ -704,10 +706,22 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
           CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, ctx->stream), "NES prep launch");
         }
       }
-      // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after mode N)
+      // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after
+      // mode N, and then the history record unless an acceleration follows)
+      RecArgs rec;
+      if (last && !accel) {
+        rec.hist = ctx->hist;
+        rec.inner_now = inner_now;
+        rec.inner_hist = ctx->inner;
+        rec.counter = counter;
+        rec.N = N;
+        rec.cap = ctx->hist_cap / 3;
+        recorded = true;
+      }
       CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n],
                            ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
-                           last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->nls_scr, ctx->stream),
+                           last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->nls_scr, rec,
+                           ctx->stream),
          "fused mode update launch");
       continue;
     }
@@ -746,13 +760,13 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
       CK(launch_fit(R, ctx->G, N, ctx->lam, dotp, nb, ctx->scal, ctx->scal + 8, ctx->stream),
          "fit launch");
   }
-  if (o.alg == PLANC_NES && o.nes_accel &&
-      (st = accelerate(ctx, H, counter)) != PLANC_OK)
-    return st;
-  CK(launch_pdl(record_kernel, dim3(1), dim3(1), 0, ctx->stream, (const double*)(ctx->scal + 8),
-                ctx->hist, (const int32_t*)inner_now, ctx->inner, N, counter, ctx->hist_cap / 3),
-     "record launch");
-  note_launches(1);
+  if (accel && (st = accelerate(ctx, H, counter)) != PLANC_OK) return st;
+  if (!recorded) {
+    CK(launch_pdl(record_kernel, dim3(1), dim3(1), 0, ctx->stream, (const double*)(ctx->scal + 8),
+                  ctx->hist, (const int32_t*)inner_now, ctx->inner, N, counter, ctx->hist_cap / 3),
+       "record launch");
+    note_launches(1);
+  }
   return PLANC_OK;
 }
 
