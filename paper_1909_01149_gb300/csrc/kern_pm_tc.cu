@@ -873,8 +873,11 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   // accumulator (a tcgen05.mma costs its issuing thread a fixed ~80 cycles
   // for N <= 128, so two issuers double the MMA rate)
   constexpr int W_MMA2 = 10;
-  // two MMA warps when the accumulators fit next to four TMEM A slots (R <= 32)
-  constexpr bool DUAL = F32 && RBX == 32;
+  // two MMA warps for FP32 X: R <= 32 with four TMEM A slots; R <= 64 in the
+  // left branch with two (the accumulators of 3 RB columns fill the rest; the
+  // right branch's epilogue, already its limit there, would read a third
+  // accumulator: slower in A/B)
+  constexpr bool DUAL = F32 && (RBX == 32 || LEFT);
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -1563,9 +1566,10 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   p.tpi = pl.tpc / pl.nsplit;
   p.jdim = pl.jdim;
   p.Mdim = left ? L : C;
-  // TMEM: 4 A slots of 64 columns + 2 accumulator buffers of 3 RB (RB <= 32,
-  // two MMA warps) or 2 RB (RB <= 64, one) columns <= 512
-  p.aslots = 4;
+  // TMEM: A slots of 64 columns + 2 accumulator buffers <= 512 columns:
+  // FP32 with two MMA warps (buffers of 3 RB): 4 slots for RB <= 32, 2 for
+  // RB <= 64 (left branch); one MMA warp (2 RB): 4 slots; BF16: buffers of 256
+  p.aslots = (f32 && pl.RB > 32 && left) ? 2 : 4;
   p.err = err_flag;
   p.Hin = (const float*)kh.H[0];
   p.W.nm = kh.nm - 1;
