@@ -1509,8 +1509,6 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
   return pl;
 }
 
-KrpHost dims_only(const KrpHost& kh) { return kh; }
-
 }  // namespace
 
 bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
