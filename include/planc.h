@@ -157,9 +157,17 @@ planc_status_t planc_plan_split(int N, const int64_t* dims, int* split);
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  *   split        root split S, 1-based; -1 chooses planc_plan_split's S
  * The partial MTTKRPs run on the tcgen05 tensor cores when the shape allows
- * (BF16 X, R <= 64, prod_{k<S} I_k a multiple of 8, X 16-byte aligned) and
- * on the CUDA-core kernels otherwise; the environment variable
- * PLANC_PM_PATH=simt, read here, forces the CUDA-core kernels.
+ * (BF16 or FP32 X, R <= 64, TMA-compatible strides, X 16-byte aligned; the
+ * resident-operand kernel when its factor image fits in shared memory, the
+ * streamed-operand kernel otherwise) and on the CUDA-core kernels
+ * otherwise (planc_pm_tensor_cores reports which).
+ * Environment switches: PLANC_PM_PATH=simt (read here) forces the CUDA-core
+ * partial MTTKRPs; PLANC_FUSED_MODES=0 (read here) keeps the per-mode update
+ * on the multi-launch path; PLANC_TC_STREAMED_KRP (set; read at each launch)
+ * forces the streamed-operand tensor-core kernel; PLANC_PDL=0 (read once per
+ * process) launches without programmatic dependent launch.  They select
+ * among equivalent paths for tests and measurements; results agree within
+ * the stated tolerances.
  * Allocates the workspace (dimension-tree temporaries, split-K partials,
  * reduction scratch).  Errors: PLANC_E_SHAPE, PLANC_E_DTYPE, PLANC_E_INVALID,
  * PLANC_E_NOMEM, PLANC_E_CUDA (no device / not sm_103). */
