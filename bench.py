@@ -305,7 +305,14 @@ def run_planc(args, cfg):
     if rank == 0 and ws == 1 and not args.no_mixed and args.config == "c2":
         out["mixed"] = run_mixed(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(cfg, X, H0, alg)
+        cb = cpu_baseline(cfg, X, H0, alg)
+        # the GPU result against the FP64 oracle on the same inputs: relative
+        # error after the first outer iteration (the oracle's bounded sample)
+        o1 = cb.pop("rel_err_iter1")
+        out["cpu_baseline"] = cb
+        out["oracle_check"] = {"iter": 1, "gpu_rel_err": res["rel_err"][0], "oracle_rel_err": o1,
+                               "abs_diff": abs(res["rel_err"][0] - o1),
+                               "tolerance": 1e-5 if cfg["dtype"] != "f64" else 1e-10}
     return out, rank
 
 
@@ -592,12 +599,13 @@ def cpu_baseline(cfg, X, H0, alg):
     Xs = np.asarray(X, dtype=np.float64)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     t = time.time()
-    o.nncp(Xs, Hs, alg, iters=1)
+    ref = o.nncp(Xs, Hs, alg, iters=1)
     dt = time.time() - t
     return {"value": round(1.0 / dt, 5), "unit": "iter/s", "cores": os.cpu_count(),
             "kind": "oracle",
             "sample": f"1 outer iteration (alpha, {len(cfg['dims'])} mode updates, error) "
-                      f"of the full {cfg['workload']} workload, NumPy FP64, default BLAS threads"}
+                      f"of the full {cfg['workload']} workload, NumPy FP64, default BLAS threads",
+            "rel_err_iter1": ref["rel_err"][0]}
 
 
 def run_reference(args, cfg):
