@@ -328,7 +328,8 @@ admm_step_kernel(int64_t rows, int R, const TA* __restrict__ M, TA* __restrict__
 }
 
 // ---- BPP (Eq. snls; Kim-Park block principal pivoting) ---------------------------------
-// One warp per row, R <= 64 (lane j holds indices j and j + 32), FP64.
+// One warp per row, R <= 64 (lane j holds indices j and j + 32), FP64; the
+// passive-set Cholesky in shared memory with a padded leading dimension.
 constexpr int BPP_WARPS = 4;
 
 __device__ __forceinline__ uint64_t ballot64(bool lo, bool hi) {
@@ -343,12 +344,19 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
                TA* __restrict__ H, const double* __restrict__ lam, int max_iter,
                int32_t* __restrict__ inner, int* __restrict__ flags) {
   extern __shared__ double bsm[];
-  double* Ss = bsm;                                   // R x R
+  // matrices with leading dimension LD = R + 1: a column read by the 32
+  // lanes then spreads over the banks (stride R put every lane on one bank)
+  const int LD = R + 1;
+  double* Ss = bsm;                                   // R x R (stride LD)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* A = bsm + R * R + (size_t)warp * (R * R + 2 * 64);  // f x f (stride R)
-  double* xs = A + R * R;                              // 64: passive solution / rhs
+  double* A = bsm + R * LD + (size_t)warp * (R * LD + 3 * 64);  // f x f (stride LD)
+  double* xs = A + R * LD;                             // 64: passive solution / rhs
   double* zs = xs + 64;                                // 64: full x
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ss[e] = S[e];
+  double* dinv = zs + 64;                              // 64: 1 / pivot
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int a = e / R, b = e - a * R;
+    Ss[a * LD + b] = S[e];
+  }
   __syncthreads();
   const int64_t row = (int64_t)blockIdx.x * BPP_WARPS + warp;
   if (row >= rows) return;
@@ -371,48 +379,51 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     uint64_t below1 = F & ((1ull << j1) - 1ull);
     int p0 = __popcll(below0), p1 = __popcll(below1);
     bool in0 = v0 && ((F >> j0) & 1ull), in1 = v1 && ((F >> j1) & 1ull);
-    // build A = S_FF (row-major, stride R) and rhs = m_F
-    // each lane owns the rows/cols of its indices: A[p_a][p_b] = S[a][b]
+    // build A = S_FF and rhs = m_F: each lane owns the columns of its
+    // indices, A[p_a][p_b] = S[a][b]
     for (int a = 0; a < R; ++a) {
       if (!((F >> a) & 1ull)) continue;
       int pa = __popcll(a == 0 ? 0ull : (F & ((1ull << a) - 1ull)));
-      if (in0) A[pa * R + p0] = Ss[a * R + j0];
-      if (in1) A[pa * R + p1] = Ss[a * R + j1];
+      if (in0) A[pa * LD + p0] = Ss[a * LD + j0];
+      if (in1) A[pa * LD + p1] = Ss[a * LD + j1];
     }
     if (in0) xs[p0] = m0;
     if (in1) xs[p1] = m1;
     __syncwarp();
-    // Cholesky (lower) of A, f x f
+    // Cholesky (lower) of A, f x f, right-looking; the pivot's reciprocal is
+    // formed once and multiplied (FP64 division is a long sequence here)
     for (int c = 0; c < f; ++c) {
       if (lane == 0) {
-        double d = A[c * R + c];
+        double d = A[c * LD + c];
         if (!(d > 0.0)) { bad = 1; d = 1e-300; }
-        A[c * R + c] = sqrt(d);
+        const double r = sqrt(d);
+        A[c * LD + c] = r;
+        dinv[c] = 1.0 / r;
       }
       __syncwarp();
-      double dc = A[c * R + c];
-      for (int i = c + 1 + lane; i < f; i += 32) A[i * R + c] /= dc;
+      const double ic = dinv[c];
+      for (int i = c + 1 + lane; i < f; i += 32) A[i * LD + c] *= ic;
       __syncwarp();
-      int mm = f - c - 1;
-      for (int e = lane; e < mm * mm; e += 32) {
-        int i = c + 1 + e / mm, j = c + 1 + e % mm;
-        if (j <= i) A[i * R + j] -= A[i * R + c] * A[j * R + c];
+      // trailing update: lane owns rows i (row i, columns c+1..i)
+      for (int i = c + 1 + lane; i < f; i += 32) {
+        const double aic = A[i * LD + c];
+        for (int j = c + 1; j <= i; ++j) A[i * LD + j] = fma(-aic, A[j * LD + c], A[i * LD + j]);
       }
       __syncwarp();
     }
     // forward: L z = m_F (column-oriented)
     for (int c = 0; c < f; ++c) {
-      double zc = xs[c] / A[c * R + c];
+      double zc = xs[c] * dinv[c];
       __syncwarp();
-      for (int i = c + 1 + lane; i < f; i += 32) xs[i] -= A[i * R + c] * zc;
+      for (int i = c + 1 + lane; i < f; i += 32) xs[i] = fma(-A[i * LD + c], zc, xs[i]);
       if (lane == 0) xs[c] = zc;
       __syncwarp();
     }
     // backward: L^T x = z
     for (int c = f - 1; c >= 0; --c) {
-      double xc = xs[c] / A[c * R + c];
+      double xc = xs[c] * dinv[c];
       __syncwarp();
-      for (int i = lane; i < c; i += 32) xs[i] -= A[c * R + i] * xc;
+      for (int i = lane; i < c; i += 32) xs[i] = fma(-A[c * LD + i], xc, xs[i]);
       if (lane == 0) xs[c] = xc;
       __syncwarp();
     }
@@ -424,8 +435,8 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     double s0 = 0.0, s1 = 0.0;
     for (int k = 0; k < R; ++k) {
       double xk = zs[k];
-      if (v0) s0 += Ss[j0 * R + k] * xk;
-      if (v1) s1 += Ss[j1 * R + k] * xk;
+      if (v0) s0 = fma(Ss[j0 * LD + k], xk, s0);
+      if (v1) s1 = fma(Ss[j1 * LD + k], xk, s1);
     }
     y0 = (v0 && !in0) ? s0 - m0 : 0.0;
     y1 = (v1 && !in1) ? s1 - m1 : 0.0;
@@ -873,7 +884,8 @@ template <typename TA>
 cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
   if (a.alg == PLANC_BPP) {
     const int blocks = (int)((a.rows + BPP_WARPS - 1) / BPP_WARPS);
-    size_t smem = ((size_t)a.R * a.R + BPP_WARPS * ((size_t)a.R * a.R + 128)) * sizeof(double);
+    const size_t rl = (size_t)a.R * (a.R + 1);  // R x R with leading dimension R + 1
+    size_t smem = (rl + BPP_WARPS * (rl + 3 * 64)) * sizeof(double);
     cudaFuncSetAttribute(nls_bpp_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     if (a.inner) {
