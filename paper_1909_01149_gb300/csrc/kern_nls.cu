@@ -6,8 +6,9 @@
 // MU, HALS, ADMM steps and PGD keep one row per thread with the row in
 // registers (R padded to RP in {16, 32, 64}) and S (or the ADMM inverse) in
 // shared memory, read as warp-wide broadcasts.  BPP gives each row a warp
-// and does its passive-set Cholesky solves in FP64.  ADMM factors S + rho I
-// once per call in FP64 and keeps the explicit inverse for the row solves.
+// and does its passive-set Cholesky solves in FP64.  ADMM (and UCP) invert
+// S + rho I once per call in FP64 and keep the explicit inverse for the row
+// solves.
 #include <algorithm>
 
 #include "internal.h"
@@ -160,67 +161,69 @@ nls_pgd_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
 // (R x R, FP64), then W as TA, then per-step per-block norm partials.
 constexpr int ADMM_W = 8;
 
-// ucp != 0: no shift (rho = 0), W = S^{-1} for the unconstrained update
+// ucp != 0: no shift (rho = 0), W = S^{-1} for the unconstrained update.
+// W = (S + rho I)^{-1} by the symmetric sweep operator (Gauss-Jordan
+// elimination in place, which needs no pivoting for a symmetric positive
+// definite matrix): R steps, each a rank-1 update of the whole matrix spread
+// over the CTA, instead of a Cholesky factorisation followed by a serial
+// inverse per column.  Its pivots are those of the Cholesky factorisation, so
+// a non-positive pivot flags the same matrices.
 __global__ void __launch_bounds__(256)
 admm_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, int wtf_f64,
                  int ucp) {
   extern __shared__ double sm[];
-  double* A = sm;             // R x R: S + rho I, then its Cholesky factor (lower)
-  double* Li = sm + R * R;    // R x R: L^{-1} (lower)
-  __shared__ double s_rho;
+  const int LD = R + 1;        // padded leading dimension (no bank conflicts)
+  double* A = sm;              // R x R (stride LD): S + rho I, swept in place
+  double* col = sm + R * LD;   // R: column k before the step
+  __shared__ double s_rho, s_inv;
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
+  if (tid < 32) {
     double tr = 0.0;
-    for (int r = 0; r < R; ++r) tr += S[r * R + r];
-    // reading: rho = trace(S) / R; an all-zero S (no information) uses rho = 1
-    s_rho = ucp ? 0.0 : (tr > 0.0 ? tr / R : 1.0);
-    s_bad = 0;
+    for (int r = tid; r < R; r += 32) tr += S[r * R + r];
+    tr = warp_sum(tr);
+    if (tid == 0) {
+      // reading: rho = trace(S) / R; an all-zero S (no information) uses rho = 1
+      s_rho = ucp ? 0.0 : (tr > 0.0 ? tr / R : 1.0);
+      s_bad = 0;
+    }
   }
   __syncthreads();
   for (int e = tid; e < R * R; e += nt) {
-    int i = e / R, j = e - i * R;
-    A[e] = S[e] + (i == j ? s_rho : 0.0);
-    Li[e] = 0.0;
+    const int i = e / R, j = e - i * R;
+    A[i * LD + j] = S[e] + (i == j ? s_rho : 0.0);
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle
-  for (int c = 0; c < R; ++c) {
+  for (int k = 0; k < R; ++k) {
     if (tid == 0) {
-      double d = A[c * R + c];
+      double d = A[k * LD + k];
       if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
-      A[c * R + c] = sqrt(d);
+      s_inv = 1.0 / d;
+    }
+    for (int i = tid; i < R; i += nt) col[i] = A[i * LD + k];
+    __syncthreads();
+    const double inv = s_inv;
+    // A_ij -= A_ik A_kj / d for i, j != k (A symmetric: A_kj = A_jk = col[j])
+    for (int e = tid; e < R * R; e += nt) {
+      const int i = e / R, j = e - i * R;
+      if (i != k && j != k) A[i * LD + j] = fma(-col[i] * inv, col[j], A[i * LD + j]);
     }
     __syncthreads();
-    double dc = A[c * R + c];
-    for (int i = c + 1 + tid; i < R; i += nt) A[i * R + c] /= dc;
-    __syncthreads();
-    int m = R - c - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      int i = c + 1 + e / m, j = c + 1 + e % m;
-      if (j <= i) A[i * R + j] -= A[i * R + c] * A[j * R + c];
+    for (int i = tid; i < R; i += nt) {
+      const double v = i == k ? -inv : col[i] * inv;
+      A[i * LD + k] = v;
+      A[k * LD + i] = v;
     }
     __syncthreads();
   }
-  // L^{-1}: column j by forward substitution (one thread per column)
-  for (int j = tid; j < R; j += nt) {
-    for (int i = j; i < R; ++i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) s -= A[i * R + k] * Li[k * R + j];
-      Li[i * R + j] = s / A[i * R + i];
-    }
-  }
-  __syncthreads();
-  // W = L^{-T} L^{-1}
+  // after all R steps A = -(S + rho I)^{-1}
   double* W = scr + ADMM_W;
   for (int e = tid; e < R * R; e += nt) {
-    int i = e / R, j = e - i * R;
-    int k0 = i > j ? i : j;
-    double s = 0.0;
-    for (int k = k0; k < R; ++k) s += Li[k * R + i] * Li[k * R + j];
-    W[e] = s;
-    if (wtf_f64) ((double*)(W + R * R))[e] = s;
-    else ((float*)(W + R * R))[e] = (float)s;
+    const int i = e / R, j = e - i * R;
+    const double w = -A[i * LD + j];
+    W[e] = w;
+    if (wtf_f64) ((double*)(W + R * R))[e] = w;
+    else ((float*)(W + R * R))[e] = (float)w;
   }
   if (tid == 0) { scr[0] = s_rho; scr[1] = s_bad; }
 }
@@ -824,7 +827,7 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
       note_launches(1);
       break;
     case PLANC_ADMM: {
-      size_t smem = 2 * (size_t)a.R * a.R * sizeof(double);
+      size_t smem = ((size_t)a.R * (a.R + 1) + a.R) * sizeof(double);
       cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, 0);
@@ -865,7 +868,7 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
       return cudaSuccess;
     }
     case PLANC_UCP: {
-      size_t smem = 2 * (size_t)a.R * a.R * sizeof(double);
+      size_t smem = ((size_t)a.R * (a.R + 1) + a.R) * sizeof(double);
       cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       admm_prep_kernel<<<1, 256, smem, st>>>(a.S, a.R, a.scratch, sizeof(TA) == 8, 1);
