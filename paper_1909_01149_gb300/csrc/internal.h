@@ -155,6 +155,11 @@ struct NlsArgs {
   bool f64;
 };
 size_t nls_scratch_doubles(int64_t rows, int R);
+// (S + rho I)^{-1} into scr (rho = trace(S)/R, or 0 with ucp): [0] rho,
+// [1] 1 if a pivot was not positive; the inverse (FP64) at scr + 8 and in the
+// factor precision at scr + 8 + R^2
+cudaError_t launch_inv_prep(bool f64, const double* S, int R, double* scr, int ucp,
+                            cudaStream_t st);
 // Nesterov-type update parameters from S into scr: [0] lam_p, [1] L,
 // [2] beta, [3] 1/L, [4] lam_p/L, [5] 1 if S = 0; P in the factor precision
 // at scr + 8 + R^2
@@ -195,12 +200,13 @@ struct RecArgs {
   int* counter = nullptr;
   int N = 0, cap = 0;
 };
-// nes_scr: the Nesterov parameters (launch_nes_prep) when alg is NES
+// nes_scr: the prepared parameters when alg is NES (launch_nes_prep) or UCP
+// (launch_inv_prep: the inverse of S); flags[1] counts singular S (UCP)
 cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const double* G,
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
                               double* fit_out, int* err, const double* nes_scr,
-                              const RecArgs& rec, cudaStream_t st);
+                              const RecArgs& rec, int* flags, cudaStream_t st);
 
 // ---- PM-right / mTTV split reductions -------------------------------------------
 cudaError_t launch_split_reduce(bool f64, const void* part, int nsplit, int64_t Mdim, int R,

@@ -4,7 +4,7 @@
 //   Hhat  = NNLS-Update(S^(n), M^(n)) with warm start H^(n) diag(lambda)
 //           (MU, Eq. muupd; HALS, Eq. halsupd; projected gradient; the
 //           Nesterov-type steps of Eq. nesinnerupd, with the per-step stop
-//           test reduced over the cluster),
+//           test reduced over the cluster; UCP, H = M S^{-1}),
 //   lambda_r = ||Hhat(:, r)||, H^(n) = Hhat diag(lambda)^{-1}, G^(n) = H^T H,
 //   and after the last mode the error identity of Sec. A.2,
 // in a single launch of one thread-block cluster.
@@ -215,7 +215,7 @@ __device__ __forceinline__ void mode_update_body(
     double mu_eps, int pgd_steps, double tiny, int32_t* __restrict__ inner,
     const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err,
     const double* __restrict__ nes_scr, int nes_kmax, double nes_tol,
-    const RecArgs& rec = RecArgs()) {
+    const RecArgs& rec = RecArgs(), int* __restrict__ nflags = nullptr) {
   using L = McLayout<TA, RP>;
   using S = Swz<TA, RP>;
   const int alg = ALG >= 0 ? ALG : alg_rt;
@@ -450,6 +450,26 @@ __device__ __forceinline__ void mode_update_body(
 #pragma unroll
         for (int r = 0; r < RP; ++r) h[r] = nh[r];
       }
+    }
+  }
+  if (ALG == PLANC_UCP || (ALG < 0 && alg == PLANC_UCP)) {
+    // H = M W with W = S^{-1} (prepared in FP64, stored in the factor
+    // precision after scr + 8 + R^2); W replaces S in shared memory
+    __syncthreads();
+    const TA* Wt = reinterpret_cast<const TA*>(nes_scr + 8 + RR);
+    for (int e = t; e < RP * RP; e += MC_NT) {
+      const int i = e / RP, k = e - i * RP;
+      Ss[e] = (i < R && k < R) ? Wt[i * R + k] : TA(0);
+    }
+    if (c == 0 && t == 0 && nflags && nes_scr[1] != 0.0) atomicAdd(nflags + 1, 1);
+    __syncthreads();
+    if (live) {
+      TA nh[RP];
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+        nh[r] = r < R ? srow_dot<RP>(m, s_base + (uint32_t)(r * RP * sizeof(TA))) : TA(0);
+#pragma unroll
+      for (int r = 0; r < RP; ++r) h[r] = nh[r];  // W symmetric: row r is column r
     }
   }
   int nes_steps = 0;
@@ -703,9 +723,9 @@ mode_cluster_kernel(int rows, int R, int N, int n, double* __restrict__ G,
                     int32_t* __restrict__ inner, const double* __restrict__ alpha,
                     double* __restrict__ fit_out, int* __restrict__ err,
                     const double* __restrict__ nes_scr, int nes_kmax, double nes_tol,
-                    const __grid_constant__ RecArgs rec) {
+                    const __grid_constant__ RecArgs rec, int* __restrict__ nflags) {
   mode_update_body<TA, RP, ALG>(rows, R, N, n, G, Gf, M, H, lam, alg, mu_eps, pgd_steps, tiny, inner,
-                           alpha, fit_out, err, nes_scr, nes_kmax, nes_tol, rec);
+                           alpha, fit_out, err, nes_scr, nes_kmax, nes_tol, rec, nflags);
 }
 
 // Batched form: cluster b (blocks MC_CS b .. MC_CS b + MC_CS - 1) updates mode n
@@ -724,11 +744,12 @@ template <typename TA, int RP>
 cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const void* M, void* H,
                    double* lam, planc_nls_t alg, const planc_nls_opts& o, int32_t* inner,
                    const double* alpha, double* fit_out, int* err, const double* nes_scr,
-                   const RecArgs& rec, cudaStream_t st) {
+                   const RecArgs& rec, int* flags, cudaStream_t st) {
   const size_t smem = McLayout<TA, RP>::bytes;
   auto kern = alg == PLANC_MU     ? mode_cluster_kernel<TA, RP, PLANC_MU>
               : alg == PLANC_HALS ? mode_cluster_kernel<TA, RP, PLANC_HALS>
               : alg == PLANC_PGD  ? mode_cluster_kernel<TA, RP, PLANC_PGD>
+              : alg == PLANC_UCP  ? mode_cluster_kernel<TA, RP, PLANC_UCP>
                                   : mode_cluster_kernel<TA, RP, PLANC_NES>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -751,7 +772,7 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
                          inner, alpha, fit_out, err, nes_scr,
                          std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)), o.nes_tol,
-                         rec);
+                         rec, flags);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -787,7 +808,8 @@ int mode_batch_max_rows() { return MC_CS * MC_RPC; }
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
   // the Nesterov steps hold four row vectors in registers: FP64 up to R = 16
   const bool nes_ok = alg == PLANC_NES && (!f64 || R <= 16);
-  return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD || nes_ok) && rows >= 1 &&
+  return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD || alg == PLANC_UCP ||
+          nes_ok) && rows >= 1 &&
          rows <= (int64_t)MC_CS * MC_RPC && R <= 32;
 }
 
@@ -795,21 +817,21 @@ cudaError_t launch_mode_fused(bool f64, int64_t rows, int R, int N, int n, const
                               float* Gf, const void* M, void* H, double* lam, planc_nls_t alg,
                               const planc_nls_opts& o, int32_t* inner, const double* alpha,
                               double* fit_out, int* err, const double* nes_scr,
-                              const RecArgs& rec, cudaStream_t st) {
+                              const RecArgs& rec, int* flags, cudaStream_t st) {
   const int r = (int)rows;
   double* Gw = const_cast<double*>(G);
   if (f64) {
     if (R <= 16)
       return run_mc<double, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                                nes_scr, rec, st);
+                                nes_scr, rec, flags, st);
     return run_mc<double, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                              nes_scr, rec, st);
+                              nes_scr, rec, flags, st);
   }
   if (R <= 16)
     return run_mc<float, 16>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                             nes_scr, rec, st);
+                             nes_scr, rec, flags, st);
   return run_mc<float, 32>(r, R, N, n, Gw, Gf, M, H, lam, alg, o, inner, alpha, fit_out, err,
-                           nes_scr, rec, st);
+                           nes_scr, rec, flags, st);
 }
 
 }  // namespace planc

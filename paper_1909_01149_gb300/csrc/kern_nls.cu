@@ -913,6 +913,15 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
 
 }  // namespace
 
+cudaError_t launch_inv_prep(bool f64, const double* S, int R, double* scr, int ucp,
+                            cudaStream_t st) {
+  const size_t smem = ((size_t)R * (R + 1) + R) * sizeof(double);
+  cudaFuncSetAttribute(admm_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  admm_prep_kernel<<<1, 256, smem, st>>>(S, R, scr, f64 ? 1 : 0, ucp);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nes_prep(bool f64, const double* S, int R, double* scr, cudaStream_t st) {
   if (f64) {
     const size_t psm = ((size_t)R * R + 4 * 64) * sizeof(double);

@@ -685,25 +685,33 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
     const bool fused = ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R, is_f64(ctx));
-    const bool fork = fused && o.alg == PLANC_NES && ctx->side;
+    const bool prepared = o.alg == PLANC_NES || o.alg == PLANC_UCP;
+    const bool fork = fused && prepared && ctx->side;
+    auto prep = [&](cudaStream_t sp) -> planc_status_t {
+      CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, sp), "gram_hadamard launch");
+      if (o.alg == PLANC_NES)
+        CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, sp), "NES prep launch");
+      else
+        CK(launch_inv_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, 1, sp), "inverse prep launch");
+      return PLANC_OK;
+    };
     if (fork) {
-      // S^(n) and the Nesterov parameters (eigenvalues of S^(n)) need only the
-      // Grams: they run on the side stream while the MTTKRP of mode n runs
+      // S^(n) and what the update prepares from it (the Nesterov parameters,
+      // or S^{-1} for UCP) need only the Grams: they run on the side stream
+      // while the MTTKRP of mode n runs
       CK(cudaEventRecord(ctx->ev_fork, ctx->stream), "fork record");
       CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
-      CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->side), "gram_hadamard launch");
-      CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, ctx->side), "NES prep launch");
+      if ((st = prep(ctx->side)) != PLANC_OK) return st;
       CK(cudaEventRecord(ctx->ev_join, ctx->side), "join record");
     }
     if ((st = dt_mode(ctx, H, n, ctx->Mbuf, &cur[s], &cf[s])) != PLANC_OK) return st;
     const bool last = n == N - 1;
     if (fused) {
-      if (o.alg == PLANC_NES) {
+      if (prepared) {
         if (fork) {
           CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait");
-        } else {
-          CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->stream), "gram_hadamard launch");
-          CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, ctx->stream), "NES prep launch");
+        } else if ((st = prep(ctx->stream)) != PLANC_OK) {
+          return st;
         }
       }
       // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after
@@ -721,7 +729,7 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
       CK(launch_mode_fused(is_f64(ctx), ctx->dims[n], R, N, n, ctx->G, ctx->Gf, ctx->Mbuf, H[n],
                            ctx->lam, o.alg, o.nls, inner_now + n, ctx->scal,
                            last ? ctx->scal + 8 : nullptr, ctx->tc_err, ctx->nls_scr, rec,
-                           ctx->stream),
+                           ctx->flags, ctx->stream),
          "fused mode update launch");
       continue;
     }
@@ -802,7 +810,8 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   CK(cudaMemsetAsync(ctx->hist, 0, (size_t)ctx->hist_cap * 8, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->accel_hist, 0, (size_t)(ctx->hist_cap / 3) * 4, ctx->stream), "memset");
 
-  if (o.alg == PLANC_NES && ctx->side == nullptr && ctx->stream != nullptr) {
+  if ((o.alg == PLANC_NES || o.alg == PLANC_UCP) && ctx->side == nullptr &&
+      ctx->stream != nullptr) {
     CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "side stream");
     CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event create");
     CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event create");
