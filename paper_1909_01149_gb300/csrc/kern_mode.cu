@@ -4,7 +4,8 @@
 //   Hhat  = NNLS-Update(S^(n), M^(n)) with warm start H^(n) diag(lambda)
 //           (MU, Eq. muupd; HALS, Eq. halsupd; projected gradient; the
 //           Nesterov-type steps of Eq. nesinnerupd, with the per-step stop
-//           test reduced over the cluster; UCP, H = M S^{-1}),
+//           test reduced over the cluster; ADMM, Eq. admmupd, likewise;
+//           UCP, H = M S^{-1}),
 //   lambda_r = ||Hhat(:, r)||, H^(n) = Hhat diag(lambda)^{-1}, G^(n) = H^T H,
 //   and after the last mode the error identity of Sec. A.2,
 // in a single launch of one thread-block cluster.
@@ -185,7 +186,7 @@ struct McLayout {
   static constexpr int RCN = MC_NT / NBLK;              // row chunks of the Gram
   static constexpr int NP = RP * (RP + 1) / 2;          // packed pairs r <= s
   static constexpr int NPO = (NP + MC_CS - 1) / MC_CS;  // pairs owned per CTA
-  static constexpr int RED = 8;                         // beta / gamma warp sums
+  static constexpr int RED = 16;                        // warp sums (beta / gamma; ADMM 4 x 4)
   // byte offsets
   static constexpr size_t oSs = 0;
   static constexpr size_t oHs = oSs + sizeof(TA) * RP * RP;
@@ -197,8 +198,8 @@ struct McLayout {
   static constexpr size_t oBeta = oGs + sizeof(double) * MC_CS * NPO;
   static constexpr size_t oGam = oBeta + sizeof(double) * MC_CS;
   static constexpr size_t oRed = oGam + sizeof(double) * MC_CS;
-  static constexpr size_t oNes = oRed + sizeof(double) * RED;  // [parity][src CTA][2]
-  static constexpr size_t bytes = oNes + sizeof(double) * 2 * MC_CS * 2;
+  static constexpr size_t oNes = oRed + sizeof(double) * RED;  // [parity][src CTA][<= 4]
+  static constexpr size_t bytes = oNes + sizeof(double) * 2 * MC_CS * 4;
   static_assert(MC_NT % RP == 0 && MC_NT == MC_RPC && NPO <= MC_NT, "one row / pair per thread");
 };
 
@@ -472,6 +473,73 @@ __device__ __forceinline__ void mode_update_body(
       for (int r = 0; r < RP; ++r) h[r] = nh[r];  // W symmetric: row r is column r
     }
   }
+  int admm_steps = 0;
+  // ADMM (Eq. admmupd): W = (S + rho I)^{-1} prepared in FP64 (stored in the
+  // factor precision after scr + 8 + R^2), U = 0; each step
+  //   Htil = (M + rho (H + U)) W,  H = [Htil - U]_+,  U = U + H - Htil,
+  // then the four stop norms are summed over the cluster (compiled where the
+  // fused path takes ADMM: FP32, or FP64 with R <= 16)
+  constexpr bool kAdmm = (ALG == PLANC_ADMM || ALG < 0) && (sizeof(TA) == 4 || RP <= 16);
+  if (kAdmm && alg == PLANC_ADMM) {
+    __syncthreads();
+    const TA* Wt = reinterpret_cast<const TA*>(nes_scr + 8 + RR);
+    for (int e = t; e < RP * RP; e += MC_NT) {
+      const int i = e / RP, k = e - i * RP;
+      Ss[e] = (i < R && k < R) ? Wt[i * R + k] : TA(0);
+    }
+    const TA rho = (TA)nes_scr[0];
+    if (c == 0 && t == 0 && nflags && nes_scr[1] != 0.0) atomicAdd(nflags + 1, 1);
+    __syncthreads();
+    TA u[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) u[r] = TA(0);
+    cluster_wait();  // pairs with the arrive at kernel start: every CTA is running
+    for (int k = 0; k < nes_kmax; ++k) {
+      TA rhs[RP];
+#pragma unroll
+      for (int r = 0; r < RP; ++r) rhs[r] = fma(rho, h[r] + u[r], m[r]);
+      TA npr = TA(0), nh = TA(0), ndu = TA(0), nu = TA(0);
+      if (live) {
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          const TA ht = srow_dot<RP>(rhs, s_base + (uint32_t)(r * RP * sizeof(TA)));  // W symmetric
+          TA hn = ht - u[r];
+          hn = hn > TA(0) ? hn : TA(0);
+          const TA un = u[r] + hn - ht;
+          npr = fma(hn - ht, hn - ht, npr);
+          nh = fma(hn, hn, nh);
+          ndu = fma(hn - h[r], hn - h[r], ndu);
+          nu = fma(un, un, nu);
+          h[r] = hn;
+          u[r] = un;
+        }
+      }
+      double q4[4] = {(double)npr, (double)nh, (double)ndu, (double)nu};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) q4[q] = warp_sum(q4[q]);
+      if ((t & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[(t >> 5) + 4 * q] = q4[q];
+      __syncthreads();
+      double* sl = nes_slot + (k & 1) * MC_CS * 4;
+      if (t < MC_CS) {  // thread d pushes this CTA's four sums to CTA d
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          double v = 0.0;
+          for (int w = 0; w < MC_NT / 32; ++w) v += red[w + 4 * q];
+          st_cluster(sl + c * 4 + q, (uint32_t)t, v);
+        }
+      }
+      cluster_arrive();
+      cluster_wait();
+      double a4[4];  // the same slots in the same order in every CTA
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a4[q] = slot_sum(sl + q, 4);
+      ++admm_steps;
+      if (a4[0] < nes_tol * a4[1] && a4[2] < nes_tol * a4[3]) break;
+    }
+    cluster_arrive_relaxed();  // re-pairs with the wait before the Gram exchange
+  }
   int nes_steps = 0;
   // (compiled only where the fused path takes NES: FP32, or FP64 with R <= 16)
   constexpr bool kNes = sizeof(TA) == 4 || RP <= 16;
@@ -678,7 +746,8 @@ __device__ __forceinline__ void mode_update_body(
   }
   if (c == 0 && t == 0 && inner)
     *inner = alg == PLANC_PGD ? pgd_steps
-             : alg == PLANC_NES ? (nes_scr[5] != 0.0 ? 0 : nes_steps) : 1;
+             : alg == PLANC_NES ? (nes_scr[5] != 0.0 ? 0 : nes_steps)
+             : alg == PLANC_ADMM ? admm_steps : 1;
   if (!fit_out) return;  // uniform over the cluster: no remote access follows
   gam = warp_sum(gam);
   if ((t & 31) == 0) red[4 + (t >> 5)] = gam;
@@ -750,6 +819,7 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
               : alg == PLANC_HALS ? mode_cluster_kernel<TA, RP, PLANC_HALS>
               : alg == PLANC_PGD  ? mode_cluster_kernel<TA, RP, PLANC_PGD>
               : alg == PLANC_UCP  ? mode_cluster_kernel<TA, RP, PLANC_UCP>
+              : alg == PLANC_ADMM ? mode_cluster_kernel<TA, RP, PLANC_ADMM>
                                   : mode_cluster_kernel<TA, RP, PLANC_NES>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -771,8 +841,10 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   e = cudaLaunchKernelEx(&cfg, kern, rows, R, N, n, G, Gf, (const TA*)M, (TA*)H, lam, (int)alg,
                          o.mu_eps, std::max(1, o.pgd_steps), sizeof(TA) == 8 ? 1e-300 : 1e-30,
                          inner, alpha, fit_out, err, nes_scr,
-                         std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)), o.nes_tol,
-                         rec, flags);
+                         alg == PLANC_ADMM
+                             ? std::min(PLANC_MAX_ADMM_STEPS, std::max(1, o.admm_max_inner))
+                             : std::min(PLANC_MAX_NES_STEPS, std::max(1, o.nes_max_inner)),
+                         alg == PLANC_ADMM ? o.admm_tol : o.nes_tol, rec, flags);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -806,10 +878,11 @@ cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, pl
 int mode_batch_max_rows() { return MC_CS * MC_RPC; }
 
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
-  // the Nesterov steps hold four row vectors in registers: FP64 up to R = 16
-  const bool nes_ok = alg == PLANC_NES && (!f64 || R <= 16);
+  // the Nesterov and ADMM steps hold four row vectors in registers: FP64 up
+  // to R = 16
+  const bool steps_ok = (alg == PLANC_NES || alg == PLANC_ADMM) && (!f64 || R <= 16);
   return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD || alg == PLANC_UCP ||
-          nes_ok) && rows >= 1 &&
+          steps_ok) && rows >= 1 &&
          rows <= (int64_t)MC_CS * MC_RPC && R <= 32;
 }
 

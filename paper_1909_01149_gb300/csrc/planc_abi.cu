@@ -685,14 +685,15 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
     const bool fused = ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R, is_f64(ctx));
-    const bool prepared = o.alg == PLANC_NES || o.alg == PLANC_UCP;
+    const bool prepared = o.alg == PLANC_NES || o.alg == PLANC_UCP || o.alg == PLANC_ADMM;
     const bool fork = fused && prepared && ctx->side;
     auto prep = [&](cudaStream_t sp) -> planc_status_t {
       CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, sp), "gram_hadamard launch");
       if (o.alg == PLANC_NES)
         CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, sp), "NES prep launch");
-      else
-        CK(launch_inv_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, 1, sp), "inverse prep launch");
+      else  // UCP: S^{-1}; ADMM: (S + rho I)^{-1}
+        CK(launch_inv_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, o.alg == PLANC_UCP ? 1 : 0, sp),
+           "inverse prep launch");
       return PLANC_OK;
     };
     if (fork) {
@@ -810,8 +811,8 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   CK(cudaMemsetAsync(ctx->hist, 0, (size_t)ctx->hist_cap * 8, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->accel_hist, 0, (size_t)(ctx->hist_cap / 3) * 4, ctx->stream), "memset");
 
-  if ((o.alg == PLANC_NES || o.alg == PLANC_UCP) && ctx->side == nullptr &&
-      ctx->stream != nullptr) {
+  if ((o.alg == PLANC_NES || o.alg == PLANC_UCP || o.alg == PLANC_ADMM) &&
+      ctx->side == nullptr && ctx->stream != nullptr) {
     CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "side stream");
     CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event create");
     CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event create");
