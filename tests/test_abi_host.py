@@ -101,3 +101,13 @@ def test_option_defaults_cross_the_abi():
     assert (s.alg, s.iters, s.tol, s.use_graph, s.profile, s.nes_accel) == (1, 10, 0.0, 1, 0, 1)
     assert s.nls.nes_max_inner == 20 and s.nls.nes_tol == 1e-3
     assert planc.ALGS["nes"] == 6 and planc.ALGS["ucp"] == 5
+
+
+def test_dimension_tree_of_nmf_is_two_leaves():
+    """N = 2 (NMF): the root split is S = 1 and both partial MTTKRPs are the
+    leaves themselves (M^(1) = X H^(2), M^(2) = X^T H^(1)); no multi-TTV."""
+    planc = _planc()
+    for dims in [(300, 200), (7, 1000), (1000, 7)]:
+        text = planc.describe(dims)
+        assert "split S=1" in text
+        assert sorted(_edges(text)) == ["PM {1,2} -> {1}", "PM {1,2} -> {2}"]
