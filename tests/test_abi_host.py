@@ -111,3 +111,30 @@ def test_dimension_tree_of_nmf_is_two_leaves():
         text = planc.describe(dims)
         assert "split S=1" in text
         assert sorted(_edges(text)) == ["PM {1,2} -> {1}", "PM {1,2} -> {2}"]
+
+
+def _paper_facts():
+    kv = {}
+    for line in open(os.path.join(HERE, "golden", "paper_facts.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            kv[k] = int(v)
+    return kv
+
+
+def test_defaults_follow_the_numbers_the_paper_states():
+    """ADMM at most 5 inner steps (Sec. 4.3.4), NES at most 20 (Sec. 4.3.5),
+    two partial MTTKRPs per outer iteration for any N (Sec. 4.2): in the
+    library's defaults, in the oracle, and in the planned dimension tree."""
+    import inspect
+    planc = _planc()
+    facts = _paper_facts()
+    d = planc.lib.planc_nls_opts_default()
+    assert d.admm_max_inner == facts["admm_max_inner"]
+    assert d.nes_max_inner == facts["nes_max_inner"]
+    assert o.NES_MAX_INNER == facts["nes_max_inner"]
+    assert inspect.signature(o.nls_admm).parameters["max_inner"].default == facts["admm_max_inner"]
+    for dims in [(8, 9), (5, 6, 7), (3, 4, 5, 6), (2, 3, 4, 5, 6)]:
+        pms = [e for e in _edges(planc.describe(dims)) if e.startswith("PM")]
+        assert len(pms) == facts["pm_per_outer_iteration"], dims
