@@ -8,7 +8,8 @@ NNLS update, normalisation, Gram) per mode and the error identity (all rows
 of the hot path).  value = outer iterations per second over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl planc|reference]
-                  [--config c2|c3|c1|c4] [--alg hals|mu|admm|bpp|pgd]
+                  [--config dense512-f32|mouse4d-bf16|dense64-f64|dense96x4-f32-r64]
+                  [--alg hals|mu|admm|bpp|pgd|ucp|nes]
                   [--mode solve|pm|grad|batch|ablation]
                   [--no-mixed] [--no-cpu-baseline]
 
@@ -36,18 +37,22 @@ sys.path.insert(0, ROOT)
 
 CONFIGS = {
     # 512^3 FP32, R = 32, planted + 5% noise, 50 outer iterations
-    "c2": dict(workload="nncp-dense-3way-512x512x512-fp32-R32", dims=(512, 512, 512), R=32,
-               dtype="f32", alg="hals", iters=50, noise=0.05, kind="planted"),
+    "dense512-f32": dict(
+        workload="nncp-dense-3way-512x512x512-fp32-R32", dims=(512, 512, 512), R=32,
+        dtype="f32", alg="hals", iters=50, noise=0.05, kind="planted"),
     # 128x128x200x100 BF16 storage, R = 16, mouse-like, BPP, 30 iterations
-    "c3": dict(workload="nncp-dense-4way-128x128x200x100-bf16-R16", dims=(128, 128, 200, 100),
-               R=16, dtype="bf16", alg="bpp", iters=30, noise=None, kind="mouse"),
+    "mouse4d-bf16": dict(
+        workload="nncp-dense-4way-128x128x200x100-bf16-R16", dims=(128, 128, 200, 100), R=16,
+        dtype="bf16", alg="bpp", iters=30, noise=None, kind="mouse"),
     # 64^3 FP64, R = 8, HALS, 20 iterations
-    "c1": dict(workload="nncp-dense-3way-64x64x64-fp64-R8", dims=(64, 64, 64), R=8,
-               dtype="f64", alg="hals", iters=20, noise=0.01, kind="planted"),
+    "dense64-f64": dict(
+        workload="nncp-dense-3way-64x64x64-fp64-R8", dims=(64, 64, 64), R=8,
+        dtype="f64", alg="hals", iters=20, noise=0.01, kind="planted"),
     # 96^4 FP32, R = 64: CP-loss gradient (--mode grad) and 100 projected-gradient
     # outer iterations (the solve with the PGD update)
-    "c4": dict(workload="nncp-dense-4way-96x96x96x96-fp32-R64", dims=(96, 96, 96, 96), R=64,
-               dtype="f32", alg="pgd", iters=100, noise=0.01, kind="planted"),
+    "dense96x4-f32-r64": dict(
+        workload="nncp-dense-4way-96x96x96x96-fp32-R64", dims=(96, 96, 96, 96), R=64,
+        dtype="f32", alg="pgd", iters=100, noise=0.01, kind="planted"),
 }
 METRIC = "NNCP outer iterations/s (+ partial-MTTKRP HBM GB/s)"
 
@@ -302,7 +307,7 @@ def run_planc(args, cfg):
     ctx.close()
     del Xd
     torch.cuda.empty_cache()
-    if rank == 0 and ws == 1 and not args.no_mixed and args.config == "c2":
+    if rank == 0 and ws == 1 and not args.no_mixed and args.config == "dense512-f32":
         out["mixed"] = run_mixed(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(cfg, X, H0, alg)
@@ -391,7 +396,7 @@ def run_ablation(args):
     from paper_1909_01149_gb300 import planc, synth
     torch.cuda.set_device(0)
     out = {"mode": "ablation", "what": "all-mode MTTKRP at fixed factors"}
-    for key in ("c2", "c4"):
+    for key in ("dense512-f32", "dense96x4-f32-r64"):
         cfg = CONFIGS[key]
         X, H0 = make_inputs(cfg)
         Xd = torch.from_numpy(synth.flat(X)).float().cuda()
@@ -548,7 +553,7 @@ def run_mixed(args):
     measured against the unrounded tensor."""
     import torch
     from paper_1909_01149_gb300 import planc, synth
-    cfg = CONFIGS["c3"]
+    cfg = CONFIGS["mouse4d-bf16"]
     X, H0 = make_inputs(cfg)
     flat = synth.flat(X)
     Xb = torch.from_numpy(flat).to(torch.bfloat16).cuda()
@@ -648,14 +653,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="planc", choices=["planc", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="dense512-f32", choices=sorted(CONFIGS))
     ap.add_argument("--alg", default=None)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "pm", "grad", "batch", "ablation", "algs"],
                     help="pm: time only the two partial MTTKRPs (profiling aid); "
-                         "grad: time the CP-loss gradient (config c4); "
+                         "grad: time the CP-loss gradient (config dense96x4-f32-r64); "
                          "batch: 256 uneven instances, batched vs per-instance loop; "
                          "ablation: dimension tree vs per-mode MTTKRP; "
                          "algs: every update algorithm on one workload")
@@ -690,8 +695,8 @@ def main():
     elif args.mode == "algs":
         out, rank = run_algs(args, cfg)
     elif args.mode == "grad":
-        if args.config == "c2" and not (args.dims or args.rank or args.dtype):
-            cfg = dict(CONFIGS["c4"])
+        if args.config == "dense512-f32" and not (args.dims or args.rank or args.dtype):
+            cfg = dict(CONFIGS["dense96x4-f32-r64"])
         out, rank = run_grad(args, cfg)
     elif args.impl == "reference":
         out, rank = run_reference(args, cfg)
