@@ -249,9 +249,16 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     }
   }
   if (!tuned) {
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    struct Events {  // released on every return path
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~Events() {
+        for (cudaEvent_t x : e)
+          if (x) cudaEventDestroy(x);
+      }
+    } ev;
+    if (cudaEventCreate(&ev.e[0]) != cudaSuccess || cudaEventCreate(&ev.e[1]) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "event creation failed");
+    const cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     float best_l = 1e30f, best_r = 1e30f;
     auto time_it = [&](auto&& launch, float& ms) -> bool {
       for (int rep = 0; rep < 2; ++rep) {
@@ -276,8 +283,6 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
           return bfail(PLANC_E_CUDA, "tuning launch failed");
         if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
       }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = ch;
   }
