@@ -143,9 +143,34 @@ def _ptrs(ts):
 
 
 def _check_mat(t, rows, cols, dtype, what):
-    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype and tuple(t.shape) == (rows, cols)):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and
+            t.dtype == dtype and tuple(t.shape) == (rows, cols)):
+        got = (tuple(t.shape), t.dtype, t.device) if isinstance(t, torch.Tensor) else type(t)
         raise ValueError(f"{what} must be a contiguous CUDA {dtype} tensor of shape "
-                         f"({rows}, {cols}), got {tuple(t.shape)} {t.dtype}")
+                         f"({rows}, {cols}), got {got}")
+
+
+def _check_buf(t, numel, dtype, what):
+    """The library reads and writes through raw pointers: a buffer must be a
+    contiguous CUDA tensor of the expected dtype with room for `numel` entries.
+    Raises ValueError naming the first property that fails."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what} must be a torch tensor, got {type(t)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{what} must have dtype {dtype}, got {t.dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{what} needs at least {numel} entries, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor, got {t.device}")
+
+
+def _rows_of(H, R, dtype, what):
+    if not (isinstance(H, torch.Tensor) and H.dim() == 2):
+        raise ValueError(f"{what} must be a 2-D (rows, {R}) tensor")
+    _check_mat(H, H.shape[0], R, dtype, what)
+    return H.shape[0]
 
 
 class Context:
@@ -231,6 +256,8 @@ class Context:
         if 0 <= n < self.N:
             self._check_H(H, skip=n)
         M = self._empty(self.dims[n] if 0 <= n < self.N else 1) if M is None else M
+        if 0 <= n < self.N:
+            _check_buf(M, self.dims[n] * self.R, self.fdtype, "M")
         self._check(lib.planc_mttkrp(self.h, _ptrs(H), int(n), _ptr(M)))
         return M
 
@@ -250,34 +277,52 @@ class Context:
         self._check_H(H)
         if T is None:
             T = torch.empty(self.R * rows, dtype=self.fdtype, device=self.device)
+        _check_buf(T, self.R * rows, self.fdtype, "T")
         self._check(lib.planc_partial_mttkrp(self.h, _ptrs(H), int(side), _ptr(T)))
         return T
 
     def gram_hadamard(self, G: torch.Tensor, n: int, S: torch.Tensor | None = None):
         S = torch.empty((self.R, self.R), dtype=torch.float64, device=self.device) if S is None else S
+        _check_buf(G, self.N * self.R * self.R, torch.float64, "G")
+        _check_buf(S, self.R * self.R, torch.float64, "S")
         self._check(lib.planc_gram_hadamard(self.h, _ptr(G), int(n), _ptr(S)))
         return S
 
     def gram(self, H: torch.Tensor, G: torch.Tensor | None = None) -> torch.Tensor:
+        rows = _rows_of(H, self.R, self.fdtype, "H")
         G = torch.empty((self.R, self.R), dtype=torch.float64, device=self.device) if G is None else G
-        self._check(lib.planc_gram(self.h, H.shape[0], _ptr(H), _ptr(G)))
+        _check_buf(G, self.R * self.R, torch.float64, "G")
+        self._check(lib.planc_gram(self.h, rows, _ptr(H), _ptr(G)))
         return G
 
     def nls_update(self, alg: str, S, M, H, aux=None, opts: NlsOpts | None = None,
                    inner: torch.Tensor | None = None):
         o = lib.planc_nls_opts_default() if opts is None else opts
+        rows = _rows_of(H, self.R, self.fdtype, "H")
+        _check_buf(S, self.R * self.R, torch.float64, "S")
+        _check_buf(M, rows * self.R, self.fdtype, "M")
+        if aux is not None:
+            _check_buf(aux, rows * self.R, self.fdtype, "aux")
+        if inner is not None:
+            _check_buf(inner, 1, torch.int32, "inner")
         self._check(lib.planc_nls_update(
-            self.h, ALGS[alg], C.byref(o), H.shape[0], _ptr(S), _ptr(M), _ptr(H),
+            self.h, ALGS[alg], C.byref(o), rows, _ptr(S), _ptr(M), _ptr(H),
             None if aux is None else _ptr(aux), None if inner is None else _ptr(inner)))
         return H
 
     def normalize(self, H, lam: torch.Tensor | None = None, G: torch.Tensor | None = None):
+        rows = _rows_of(H, self.R, self.fdtype, "H")
         lam = torch.empty(self.R, dtype=torch.float64, device=self.device) if lam is None else lam
-        self._check(lib.planc_normalize(self.h, H.shape[0], _ptr(H), _ptr(lam),
+        _check_buf(lam, self.R, torch.float64, "lam")
+        if G is not None:
+            _check_buf(G, self.R * self.R, torch.float64, "G")
+        self._check(lib.planc_normalize(self.h, rows, _ptr(H), _ptr(lam),
                                         None if G is None else _ptr(G)))
         return H, lam
 
     def fit(self, H, lam: torch.Tensor):
+        self._check_H(H)
+        _check_buf(lam, self.R, torch.float64, "lam")
         e = C.c_double()
         f = C.c_double()
         self._check(lib.planc_fit(self.h, _ptrs(H), _ptr(lam), C.byref(e), C.byref(f)))

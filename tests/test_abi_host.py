@@ -138,3 +138,41 @@ def test_defaults_follow_the_numbers_the_paper_states():
     for dims in [(8, 9), (5, 6, 7), (3, 4, 5, 6), (2, 3, 4, 5, 6)]:
         pms = [e for e in _edges(planc.describe(dims)) if e.startswith("PM")]
         assert len(pms) == facts["pm_per_outer_iteration"], dims
+
+
+def test_binding_rejects_bad_buffers_before_the_library():
+    """The binding checks every buffer it passes as a raw pointer (device,
+    dtype, contiguity, size) and raises ValueError before any library call,
+    so a wrong tensor never reaches a kernel.  Runs on the host: a Context
+    shell with no library handle, CPU tensors standing for device ones."""
+    import torch
+    planc = _planc()
+    ctx = object.__new__(planc.Context)
+    ctx.h = None
+    ctx.dims, ctx.N, ctx.R = (6, 7, 8), 3, 4
+    ctx.fdtype, ctx.device = torch.float32, torch.device("cpu")
+    H = [torch.zeros(d, 4) for d in ctx.dims]
+    cases = [
+        lambda: ctx.mttkrp(H, 0),                                    # host factors
+        lambda: ctx.gram(torch.zeros(6, 4)),
+        lambda: ctx.gram(torch.zeros(24)),                           # not 2-D
+        lambda: ctx.normalize(torch.zeros(6, 4)),
+        lambda: ctx.nls_update("hals", torch.zeros(4, 4, dtype=torch.float64),
+                               torch.zeros(6, 4), torch.zeros(6, 4)),
+        lambda: ctx.gram_hadamard(torch.zeros(3, 4, 4, dtype=torch.float64), 0),
+        lambda: ctx.fit(H, torch.ones(4, dtype=torch.float64)),
+        lambda: ctx.partial_mttkrp(H, 0, torch.zeros(4)),
+        lambda: ctx.cp_grad(H),
+    ]
+    for call in cases:
+        with pytest.raises(ValueError):
+            call()
+    # the buffer check itself: each property rejects on its own
+    ok = torch.zeros(16, dtype=torch.float64)
+    for bad, why in [([0.0] * 16, "torch tensor"),
+                     (torch.zeros(16), "dtype"),
+                     (torch.zeros(15, dtype=torch.float64), "at least 16"),
+                     (torch.zeros(4, 4, dtype=torch.float64).t(), "contiguous"),
+                     (ok, "CUDA")]:
+        with pytest.raises(ValueError, match=why):
+            planc._check_buf(bad, 16, torch.float64, "x")
