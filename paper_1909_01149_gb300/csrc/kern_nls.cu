@@ -588,26 +588,29 @@ template <typename CT>
 __global__ void __launch_bounds__(64)
 nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, double kappa) {
   extern __shared__ __align__(16) unsigned char nes_prep_smem[];
-  CT* A = reinterpret_cast<CT*>(nes_prep_smem);  // R x R working copy of S
-  CT* v = A + R * R;        // Householder vector
+  // R x R working copy of S with leading dimension R + 1: the lanes' row
+  // and column reads fall in distinct banks
+  const int LD = R + 1;
+  CT* A = reinterpret_cast<CT*>(nes_prep_smem);
+  CT* v = A + R * LD;       // Householder vector
   CT* w = v + 64;           // w = p - K v
   CT* d = w + 64;           // diagonal
   CT* e2 = d + 64;          // squared off-diagonal
   __shared__ double s_ev[2];
   __shared__ CT s_g;
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int e = tid; e < R * R; e += 64) A[e] = (CT)S[e];
+  for (int e = tid; e < R * R; e += 64) A[(e / R) * LD + e % R] = (CT)S[e];
   __syncthreads();
   if (tid < 32) {
     for (int k = 0; k + 2 < R; ++k) {
       const int m = R - k - 1;  // x = A[k+1.., k]
       CT ss = CT(0);
       for (int i = lane + 1; i < m; i += 32) {
-        const CT x = A[(k + 1 + i) * R + k];
+        const CT x = A[(k + 1 + i) * LD + k];
         ss = fma(x, x, ss);
       }
       ss = warp_sum(ss);
-      const CT x0 = A[(k + 1) * R + k];
+      const CT x0 = A[(k + 1) * LD + k];
       if (ss == CT(0)) {  // already reduced
         if (lane == 0) e2[k] = x0 * x0;
         __syncwarp();
@@ -617,13 +620,13 @@ nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, d
       const CT sig = x0 >= CT(0) ? -alpha : alpha;
       const CT v0 = x0 - sig;
       const CT tau = CT(2) / fma(v0, v0, ss);
-      for (int i = lane; i < m; i += 32) v[i] = i == 0 ? v0 : A[(k + 1 + i) * R + k];
+      for (int i = lane; i < m; i += 32) v[i] = i == 0 ? v0 : A[(k + 1 + i) * LD + k];
       __syncwarp();
       // p = tau A_sub v: lane owns rows lane, lane + 32
       CT p0 = CT(0), p1 = CT(0);
       const int i0 = lane, i1 = lane + 32;
-      const CT* r0 = A + (k + 1 + i0) * R + k + 1;
-      const CT* r1 = A + (k + 1 + i1) * R + k + 1;
+      const CT* r0 = A + (k + 1 + i0) * LD + k + 1;
+      const CT* r1 = A + (k + 1 + i1) * LD + k + 1;
       for (int j = 0; j < m; ++j) {
         const CT vj = v[j];
         if (i0 < m) p0 = fma(r0[j], vj, p0);
@@ -642,16 +645,16 @@ nes_prep_kernel(const double* __restrict__ S, int R, double* __restrict__ scr, d
       const CT vc1 = i1 < m ? v[i1] : CT(0), wc1 = i1 < m ? w[i1] : CT(0);
       for (int i = 0; i < m; ++i) {
         const CT vi = v[i], wi = w[i];
-        CT* row = A + (k + 1 + i) * R + k + 1;
+        CT* row = A + (k + 1 + i) * LD + k + 1;
         if (i0 < m) row[i0] = fma(-vi, wc0, fma(-wi, vc0, row[i0]));
         if (i1 < m) row[i1] = fma(-vi, wc1, fma(-wi, vc1, row[i1]));
       }
       if (lane == 0) e2[k] = sig * sig;
       __syncwarp();
     }
-    for (int i = lane; i < R; i += 32) d[i] = A[i * R + i];
+    for (int i = lane; i < R; i += 32) d[i] = A[i * LD + i];
     if (lane == 0 && R >= 2) {
-      const CT x = A[(R - 1) * R + R - 2];
+      const CT x = A[(R - 1) * LD + R - 2];
       e2[R - 2] = x * x;
     }
     __syncwarp();
@@ -924,12 +927,12 @@ cudaError_t launch_inv_prep(bool f64, const double* S, int R, double* scr, int u
 
 cudaError_t launch_nes_prep(bool f64, const double* S, int R, double* scr, cudaStream_t st) {
   if (f64) {
-    const size_t psm = ((size_t)R * R + 4 * 64) * sizeof(double);
+    const size_t psm = ((size_t)R * (R + 1) + 4 * 64) * sizeof(double);
     cudaFuncSetAttribute(nes_prep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)psm);
     nes_prep_kernel<double><<<1, 64, psm, st>>>(S, R, scr, kNesKappa);
   } else {
-    const size_t psm = ((size_t)R * R + 4 * 64) * sizeof(float);
+    const size_t psm = ((size_t)R * (R + 1) + 4 * 64) * sizeof(float);
     cudaFuncSetAttribute(nes_prep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)psm);
     nes_prep_kernel<float><<<1, 64, psm, st>>>(S, R, scr, kNesKappa);
