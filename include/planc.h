@@ -49,7 +49,7 @@ typedef enum {
   PLANC_E_DTYPE = 3,          /* unsupported dtype combination */
   PLANC_E_NOMEM = 4,          /* workspace allocation failed */
   PLANC_E_CUDA = 5,           /* a CUDA runtime/driver call failed */
-  PLANC_E_NUMERIC = 6,        /* non-finite value or failed Cholesky */
+  PLANC_E_NUMERIC = 6,        /* non-finite value or a non-positive pivot */
   PLANC_E_NOT_CONVERGED = 7,  /* reserved: NNLS caps are reported, not errors */
   PLANC_E_TIMEOUT = 8,        /* a bounded device-side wait gave up */
   PLANC_E_UNSUPPORTED = 9     /* valid request this build does not implement */
@@ -60,8 +60,8 @@ typedef enum { PLANC_F64 = 0, PLANC_F32 = 1, PLANC_BF16 = 2, PLANC_F16 = 3 } pla
 /* NNLS-Update choices of Sec. 4.3 (MU, HALS, BPP, ADMM, NES) plus projected
  * gradient (PGD), the project's gradient-driven option, and UCP, the
  * unconstrained update of Sec. 6 (CP-ALS: H S = M solved exactly, no
- * non-negativity; a non-positive Cholesky pivot of S reports
- * PLANC_E_NUMERIC at the end of a solve).
+ * non-negativity; a non-positive pivot while inverting S, i.e. S not
+ * positive definite, reports PLANC_E_NUMERIC at the end of a solve).
  * NES is the Nesterov-type update of Sec. 4.3.5 (Eq. nesnls, Eq.
  * nesinnerupd): accelerated projected gradient on the proximal problem
  * 1/2 tr(H S H^T) - tr(M^T H) + lam_p/2 ||H - H*||^2 (H* the warm start),
@@ -239,8 +239,9 @@ planc_status_t planc_gram(planc_t ctx, int64_t rows, const void* H, double* G);
  * exit the updated (unnormalised) factor.
  *   alg  MU (Eq. muupd, one step), HALS (Eq. halsupd, one sweep in column
  *        order), BPP (Eq. snls, exact NNLS per row, FP64 passive-set
- *        Cholesky), ADMM (Eq. admmupd, FP64 Cholesky of S + rho I, U reset
- *        to zero), NES (see planc_nls_t; eigenvalues of S in FP64), PGD
+ *        Cholesky), ADMM (Eq. admmupd, FP64 inverse of S + rho I by the
+ *        symmetric sweep operator, U reset to zero), NES (see planc_nls_t;
+ *        eigenvalues of S in the factor precision), PGD
  *        (projected gradient), UCP (H = M S^{-1}).
  *   opts may be NULL (defaults).
  *   aux  ADMM dual U (device rows x R) to use and return, or NULL for the

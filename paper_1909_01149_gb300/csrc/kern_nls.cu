@@ -157,7 +157,7 @@ nls_pgd_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
 }
 
 // ---- ADMM (Eq. admmupd) --------------------------------------------------------------
-// Scratch layout (doubles): [0] rho, [1] Cholesky status, [8 ..) W = (S + rho I)^{-1}
+// Scratch layout (doubles): [0] rho, [1] 1 if a pivot was not positive, [8 ..) W = (S + rho I)^{-1}
 // (R x R, FP64), then W as TA, then per-step per-block norm partials.
 constexpr int ADMM_W = 8;
 
