@@ -112,8 +112,9 @@ typedef struct {
   double fit;           /* 1 - eps */
   double* rel_err_hist; /* optional host array, length >= opts.iters */
   int32_t* inner_hist;  /* optional host array, length >= opts.iters * N:
-                           inner steps per NNLS call (ADMM steps, max BPP
-                           exchanges over rows, 1 for MU/HALS/PGD) */
+                           inner steps per NNLS call (ADMM or NES steps, max
+                           BPP exchanges over rows, pgd_steps for PGD, 1 for
+                           MU/HALS/UCP) */
   int bpp_unconverged;  /* rows whose BPP hit the exchange cap (summed) */
   float pm_ms;          /* profile: summed time of the partial MTTKRPs */
   int pm_launches;      /* profile: number of partial-MTTKRP launches timed */
@@ -149,7 +150,7 @@ planc_status_t planc_plan_split(int N, const int64_t* dims, int* split);
 /* ---- context ------------------------------------------------------------ */
 
 /* Create a context for the tensor X (Alg. 1 "Require").
- *   N, dims      order and mode sizes (N >= 2, dims[n] >= 1, prod < 2^40)
+ *   N, dims      order and mode sizes (2 <= N <= 16, dims[n] >= 1, prod < 2^40)
  *   R            CP rank (1 <= R <= 256)
  *   x_dtype, X   storage type and device pointer of X (borrowed, see above);
  *                F32/BF16/F16 data are accumulated in FP32, F64 in FP64
@@ -251,7 +252,7 @@ planc_status_t planc_gram(planc_t ctx, int64_t rows, const void* H, double* G);
  *        NES when S = 0, which leaves H unchanged).
  * Asynchronous.  A BPP row that hits the exchange cap returns its current
  * clipped iterate (no error).  Errors: PLANC_E_INVALID, PLANC_E_SHAPE
- * (rows > the largest mode of the context). */
+ * (rows > the largest mode of the context), PLANC_E_UNSUPPORTED (R > 64). */
 planc_status_t planc_nls_update(planc_t ctx, planc_nls_t alg,
                                 const planc_nls_opts* opts, int64_t rows,
                                 const double* S, const void* M, void* H,
@@ -260,7 +261,9 @@ planc_status_t planc_nls_update(planc_t ctx, planc_nls_t alg,
 /* Column normalisation of Alg. 4: lambda_r = ||Hhat(:, r)||_2 (FP64
  * accumulation), H = Hhat diag(lambda)^{-1} in place (a zero column keeps
  * lambda_r = 0 and stays zero), and, if G is not NULL, G = H^T H of the
- * normalised H.  lambda: device R doubles.  Asynchronous. */
+ * normalised H.  lambda: device R doubles.  Asynchronous.  Errors:
+ * PLANC_E_INVALID, PLANC_E_SHAPE (rows > the largest mode), PLANC_E_UNSUPPORTED
+ * (R > 64; planc_gram likewise). */
 planc_status_t planc_normalize(planc_t ctx, int64_t rows, void* H,
                                double* lambda, double* G);
 
@@ -279,13 +282,18 @@ planc_status_t planc_fit(planc_t ctx, void* const* H, const double* lambda,
  * normalisation, G^(n)) for n = 1..N and the error identity after mode N.
  * H: host array of N device pointers, initial factors in, normalised
  * factors out.  lambda: HOST double[R] out.  report: optional host record.
- * Synchronises the stream. */
+ * Synchronises the stream.  Requirements: R <= 64, 0 <= opts->iters <=
+ * 1024 - ceil(16 / N) (the per-iteration history is kept on the device).
+ * Errors: PLANC_E_INVALID (NULL H, iters out of range, unknown alg),
+ * PLANC_E_UNSUPPORTED (R > 64), PLANC_E_NUMERIC (UCP or ADMM: S not positive
+ * definite), PLANC_E_TIMEOUT (a bounded wait in a kernel gave up),
+ * PLANC_E_CUDA. */
 planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts,
                                 void* const* H, double* lambda,
                                 planc_report* report);
 
 /* Default solve options: HALS, 10 iterations, tol 0, default NNLS options,
- * graph replay on, profiling off. */
+ * graph replay on, profiling off, NES outer acceleration on. */
 planc_solve_opts planc_solve_opts_default(void);
 
 /* CP reconstruction loss f = ||X - [[H^(1..N)]]||^2 (Eq. nncp objective,
