@@ -55,6 +55,7 @@ CONFIGS = {
         dtype="f32", alg="pgd", iters=100, noise=0.01, kind="planted"),
 }
 METRIC = "NNCP outer iterations/s (+ partial-MTTKRP HBM GB/s)"
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e datasheet figure (context for frac)
 
 
 def log(*a):
@@ -296,6 +297,7 @@ def run_planc(args, cfg):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_kind": peak_kind,
+                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "kernel": "partial MTTKRP (both root branches)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                      "launches_timed": pm_n},
