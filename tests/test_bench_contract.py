@@ -2,7 +2,9 @@
 (`bench.py --impl reference`, no GPU): one JSON line with the contract's
 keys, the warm-up floor of 3, and under torchrun with two ranks a line from
 rank 0 only while every rank exits 0.  The 64^3 FP64 workload keeps each
-run to seconds."""
+run to seconds.  Also the roofline's inputs: the peak from the measured-peaks
+record and the DRAM traffic from the committed ncu summary, used only while
+its kernel source hash matches."""
 
 import json
 import os
@@ -61,3 +63,37 @@ def test_reference_arm_under_torchrun_prints_on_rank_0_only():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_is_reported_only_for_the_profiled_kernel_source():
+    """`roofline.traffic` comes from the committed ncu summary, and only while
+    the kernel source hash recorded there matches."""
+    b = _bench_module()
+    path = os.path.join(ROOT, "profiles", "pm_tcr_traffic_512x512x512_fp32_r32.txt")
+    kv = dict(l.split(":", 1) for l in open(path) if ":" in l and not l.startswith("#"))
+    kv = {k.strip(): v.strip() for k, v in kv.items()}
+    wl = b.CONFIGS["dense512-f32"]["workload"]
+    assert kv["workload"] == wl
+    got = b.profiled_traffic(wl, kv["kernel_source_sha"])
+    assert got == float(kv["dram_bytes_per_launch"])
+    assert b.profiled_traffic(wl, "0" * 16) is None
+    assert b.profiled_traffic("another-workload", kv["kernel_source_sha"]) is None
+    assert len(b.pm_source_sha(True)) == 16
+
+
+def test_roofline_peak_is_the_measured_copy_bandwidth():
+    b = _bench_module()
+    peak, kind = b.measured_peak()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
+    else:
+        assert kind == "fallback" and peak == 6800.0
