@@ -652,7 +652,9 @@ def run_reference(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 60 for the solve, 10 for the other modes "
+                         "and for the oracle arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="planc", choices=["planc", "reference"])
     ap.add_argument("--config", default="dense512-f32", choices=sorted(CONFIGS))
@@ -671,6 +673,13 @@ def main():
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
     ap.add_argument("--iters", type=int, default=None, help="override outer iterations per step")
     args = ap.parse_args()
+    if args.steps is None:
+        # 60 solves of the default workload take ~0.9 s, long enough for the
+        # 100 ms clock sampler to record several samples inside the timed
+        # region; the oracle arm keeps 10 bounded samples (~45 s)
+        args.steps = 60 if args.mode == "solve" and args.impl == "planc" else 10
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3

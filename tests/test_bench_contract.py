@@ -97,3 +97,12 @@ def test_roofline_peak_is_the_measured_copy_bandwidth():
         assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
     else:
         assert kind == "fallback" and peak == 6800.0
+
+
+def test_default_step_counts():
+    """Without --steps the oracle arm takes 10 bounded samples (the solve arm
+    takes 60, which needs a GPU and is not run here)."""
+    r = _run(["bench.py", "--impl", "reference", "--config", "dense64-f64"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = _json_lines(r.stdout)[0]
+    assert d["steps"] == 10 and d["warmup"] == 3
