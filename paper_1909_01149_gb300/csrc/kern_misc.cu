@@ -510,7 +510,7 @@ cudaError_t launch_accel_extrapolate(bool f64, const AccelModes& t, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_accel_finish(bool f64, const AccelModes& t, const double* nu, double* lam_c,
+cudaError_t launch_accel_finish(bool /*f64: lambda is FP64 either way*/, const AccelModes& t, const double* nu, double* lam_c,
                                 cudaStream_t st) {
   accel_lam_kernel<<<(t.R + 63) / 64, 64, 0, st>>>(nu, t.N, t.R, lam_c);
   note_launches(1);
