@@ -176,3 +176,31 @@ def test_binding_rejects_bad_buffers_before_the_library():
                      (ok, "CUDA")]:
         with pytest.raises(ValueError, match=why):
             planc._check_buf(bad, 16, torch.float64, "x")
+
+
+def test_every_computational_entry_point_cites_the_paper():
+    """Each call that computes a step of the method cites the section,
+    algorithm or equation it implements in its header comment; the helpers
+    (status, defaults, getters) and the library's own extensions are the only
+    uncited declarations, and the extensions say they have no counterpart."""
+    txt = open(os.path.join(ROOT, "include", "planc.h")).read()
+    decl = re.compile(r"/\*((?:(?!\*/).)*)\*/\s*(?:const\s+)?[\w\*]+\s+\**(planc_\w+)\s*\(", re.S)
+    cited, uncited = set(), {}
+    for comment, name in decl.findall(txt):
+        if re.search(r"\b(Sec|Alg|Eq|Fig|Tab)\.", comment):
+            cited.add(name)
+        else:
+            uncited[name] = comment
+    helpers = {"planc_status_str", "planc_last_error", "planc_nls_opts_default",
+               "planc_solve_opts_default", "planc_destroy", "planc_get_split",
+               "planc_pm_tensor_cores", "planc_batch_schedule"}
+    extensions = {"planc_sqnorm_noalloc"}
+    assert set(uncited) <= helpers | extensions, sorted(set(uncited) - helpers - extensions)
+    for name in extensions:
+        assert "no counterpart" in " ".join(re.sub(r"\n\s*\*", " ", uncited[name]).split())
+    for name in ("planc_init", "planc_mttkrp", "planc_mttkrp_all", "planc_partial_mttkrp",
+                 "planc_gram_hadamard", "planc_gram", "planc_nls_update", "planc_normalize",
+                 "planc_fit", "planc_nncp_solve", "planc_sqnorm", "planc_cp_grad",
+                 "planc_batch_solve", "planc_plan_split", "planc_describe"):
+        assert name in cited, name
+    assert cited | set(uncited) == set(_planc().header_functions())
