@@ -220,7 +220,9 @@ planc_status_t planc_mttkrp_all(planc_t ctx, void* const* H, void* const* M);
  *   side 0: T^{1:S} = X_(1:S) K^{S+1:N}  ((prod_{k<S} I_k) x R)
  *   side 1: T^{S+1:N} = X_(1:S)^T K^{1:S}  ((prod_{k>=S} I_k) x R)
  * written column-major (R slowest) to the device buffer T.  The benchmark
- * and the tests use this to time and check the HBM-bound kernel alone. */
+ * and the tests use this to time and check the HBM-bound kernel alone.
+ * Asynchronous.  Errors: PLANC_E_INVALID (side not 0 or 1, T NULL, or a NULL
+ * factor among the modes of the other branch, which form K). */
 planc_status_t planc_partial_mttkrp(planc_t ctx, void* const* H, int side,
                                     void* T);
 

@@ -503,6 +503,9 @@ planc_status_t planc_mttkrp_all(planc_t ctx, void* const* H, void* const* M) {
 planc_status_t planc_partial_mttkrp(planc_t ctx, void* const* H, int side, void* T) {
   if (!ctx) return PLANC_E_INVALID;
   if (!H || !T || (side != 0 && side != 1)) return fail(ctx, PLANC_E_INVALID, "bad arguments");
+  // the Khatri-Rao operand of a branch is built from the other branch's modes
+  for (int k = side_a(ctx, 1 - side); k <= side_b(ctx, 1 - side); ++k)
+    if (!H[k]) return fail(ctx, PLANC_E_INVALID, "H[%d] is NULL", k);
   return run_pm(ctx, H, side, T, false);
 }
 
