@@ -585,6 +585,8 @@ planc_status_t planc_fit(planc_t ctx, void* const* H, const double* lambda, doub
                          double* fit) {
   if (!ctx) return PLANC_E_INVALID;
   if (!H || !lambda) return fail(ctx, PLANC_E_INVALID, "bad arguments");
+  for (int k = 0; k < ctx->N; ++k)
+    if (!H[k]) return fail(ctx, PLANC_E_INVALID, "H[%d] is NULL", k);
   if (ctx->R > PLANC_MAX_NLS_R) return fail(ctx, PLANC_E_UNSUPPORTED, "fit needs R <= %d", PLANC_MAX_NLS_R);
   const int N = ctx->N, R = ctx->R;
   planc_status_t st;
