@@ -466,7 +466,8 @@ planc_status_t planc_describe(int N, const int64_t* dims, int split, char* buf, 
 }
 
 planc_status_t planc_sqnorm(planc_t ctx, double* alpha) {
-  if (!ctx || !alpha) return PLANC_E_INVALID;
+  if (!ctx) return PLANC_E_INVALID;
+  if (!alpha) return fail(ctx, PLANC_E_INVALID, "alpha is NULL");
   int nb = sqnorm_blocks(ctx->I, ctx->sm_count);
   CK(launch_sqnorm(ctx->xd, ctx->X, ctx->I, ctx->red, nb, alpha, ctx->stream), "sqnorm launch");
   return PLANC_OK;
