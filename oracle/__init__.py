@@ -14,6 +14,8 @@ that a reader can check it against the definitions of the paper by eye.
 Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   unfold, khatri_rao, mttkrp ........ pinned (brute-force sums, CP closed form,
                                       N=2 plain GEMM, two-stage 3-way equations)
+  mttkrp_rows ....................... pinned (row-restricted brute-force sums,
+                                      unsorted rows, every mode, N = 3..5)
   gram_hadamard ..................... pinned (explicit K^T K)
   nls_bpp ........................... pinned (scipy Lawson-Hanson NNLS,
                                       brute-force passive-set enumeration, KKT)
@@ -21,7 +23,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                       column step is the exact 1-D minimiser;
                                       HALS fixed point satisfies KKT)
   nls_admm .......................... pinned (uncapped ADMM reaches the BPP
-                                      solution; capped form is deterministic)
+                                      solution; hand-worked stop steps that
+                                      separate the two ratios and their
+                                      denominators; rho = 1 for S = 0)
   nls_pgd ........................... pinned (objective non-increasing; fixed
                                       point satisfies KKT)
   nls_ucp ........................... pinned (least squares on the explicit
@@ -36,7 +40,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   nes_extrapolate, model_error ...... pinned (explicit reconstruction of the
                                       extrapolated, projected model)
   normalize_columns ................. pinned (norms, reconstruction unchanged)
-  fit_identity ...................... pinned (explicit reconstruction residual)
+  fit_identity ...................... pinned (explicit reconstruction residual;
+                                      alpha = 0 reports eps = 0)
   nncp .............................. pinned (noiseless planted tensor -> zero
                                       residual; monotone error for BPP/HALS)
   cp_loss_grad ...................... pinned (central finite differences)

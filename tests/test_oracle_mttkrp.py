@@ -139,3 +139,52 @@ def test_choose_split(dims, S):
     """Root split: products of the two contiguous mode groups nearly equal,
     ties to the larger S (agrees with the literal rule on 3-way cubes)."""
     assert o.choose_split(dims) == S
+
+
+def _rows_bruteforce(X, H, n, rows):
+    """Element sums of Sec. 4.2.1 restricted to the listed rows of mode n,
+    with Python loops (independent of the matricization path)."""
+    R = H[0].shape[1]
+    out = np.zeros((len(rows), R))
+    for q, i in enumerate(rows):
+        for idx in itertools.product(*[range(s) for s in X.shape]):
+            if idx[n] != i:
+                continue
+            for r in range(R):
+                p = X[idx]
+                for k in range(X.ndim):
+                    if k != n:
+                        p *= H[k][idx[k], r]
+                out[q, r] += p
+    return out
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 5), (3, 4, 2, 3), (2, 3, 2, 3, 2)])
+def test_mttkrp_rows_is_the_row_restricted_definition(shape):
+    """mttkrp_rows (the sampled checker of the full-size GPU tests) returns
+    exactly the requested rows of M^(n), in the requested order: unsorted,
+    duplicate-free row lists in every mode, checked against element sums."""
+    R = 3
+    X = _rand(shape, 50 + len(shape))
+    H = [_rand((d, R), 60 + k) for k, d in enumerate(shape)]
+    rng = np.random.default_rng(len(shape))
+    for n, d in enumerate(shape):
+        rows = rng.permutation(d)[: max(1, d - 1)]
+        if len(rows) > 1 and np.all(np.diff(rows) > 0):
+            rows = rows[::-1].copy()  # keep the list unsorted
+        got = o.mttkrp_rows(X, H, n, rows)
+        np.testing.assert_allclose(got, _rows_bruteforce(X, H, n, rows), rtol=1e-13, atol=0)
+        np.testing.assert_allclose(got, o.mttkrp(X, H, n)[rows], rtol=1e-13, atol=0)
+
+
+def test_mttkrp_rows_single_row_and_float32_input():
+    """One row of a float32 tensor is summed in float64 (the full-size tests
+    pass the stored float32 tensor)."""
+    shape, R = (5, 4, 3), 2
+    X = _rand(shape, 71).astype(np.float32)
+    H = [_rand((d, R), 80 + k) for k, d in enumerate(shape)]
+    Xd = X.astype(np.float64)
+    for n, d in enumerate(shape):
+        got = o.mttkrp_rows(X, H, n, [d - 1])
+        assert got.dtype == np.float64 and got.shape == (1, R)
+        np.testing.assert_allclose(got, _rows_bruteforce(Xd, H, n, [d - 1]), rtol=1e-13)

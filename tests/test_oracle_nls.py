@@ -198,3 +198,58 @@ def test_ucp_als_objective_non_increasing_and_exact_recovery():
     obj = res["objective"]
     assert all(b <= a * (1 + 1e-10) + 1e-14 for a, b in zip(obj, obj[1:]))
     assert res["rel_err"][-1] < 1e-6
+
+
+# ADMM stop rule (reading of Sec. 4.3.4; the paper defers it to its
+# reference).  Hand-worked family: S = I (R = 2), so rho = trace(S)/R = 1 and
+# the two columns decouple; one row M = [b, -a] with a, b > 0, H = U = 0.
+# Each step is Htil = (M + H + U)/2, H = [Htil - U]_+, U = U + H - Htil.
+#   column 1 (b > 0): U stays 0, H_k = Htil_k = b (1 - 2^-k);
+#   column 2 (-a < 0): H stays 0, Htil_k = -a 2^-k, U_k = a (1 - 2^-k).
+# After step k:
+#   ||H - Htil||^2 = a^2 4^-k,      ||H||^2 = b^2 (1 - 2^-k)^2,
+#   ||H - H_prev||^2 = b^2 4^-k,    ||U||^2 = a^2 (1 - 2^-k)^2.
+# With rho = a / b and tol = t^2 the primal test holds iff
+# 2^-k < t / (rho + t) and the dual test iff 2^-k < t / (1/rho + t).
+# tol = 1e-2 (t = 0.1):
+#   a = 4, b = 1: primal from k = 6 (2^-6 < 0.1/4.1 = 0.0244 < 2^-5), dual
+#                 from k = 2 (2^-2 < 0.1/0.35 = 0.286 < 2^-1): stop at 6;
+#   a = 1, b = 4: the mirror image: stop at 6;
+#   a = b:        both from k = 4 (2^-4 < 0.1/1.1 = 0.0909 < 2^-3): stop at 4.
+# tol = 4e-2 (t = 0.2), a = 4, b = 1: primal from k = 5 (0.2/4.2 = 0.0476),
+#   dual from k = 2: stop at 5.
+# A rule with "or" would stop at 2, 2, 4, 2; one that swaps the two
+# denominators (||U|| for the primal, ||H|| for the dual) at 4, 4, 4, 4.
+@pytest.mark.parametrize("a,b,tol,stop", [(4.0, 1.0, 1e-2, 6), (1.0, 4.0, 1e-2, 6),
+                                          (2.0, 2.0, 1e-2, 4), (4.0, 1.0, 4e-2, 5)])
+def test_admm_stop_rule_by_hand(a, b, tol, stop):
+    S = np.eye(2)
+    M = np.array([[b, -a]])
+    H, U, k = o.nls_admm(S, M, np.zeros((1, 2)), max_inner=20, tol=tol,
+                         return_state=True)
+    assert k == stop
+    np.testing.assert_allclose(H, [[b * (1 - 2.0 ** -stop), 0.0]], rtol=1e-14, atol=0)
+    np.testing.assert_allclose(U, [[0.0, a * (1 - 2.0 ** -stop)]], rtol=1e-14, atol=1e-15)
+    # the default cap of 5 steps ends the 6-step cases early
+    _, _, k5 = o.nls_admm(S, M, np.zeros((1, 2)), tol=tol, return_state=True)
+    assert k5 == min(stop, 5)
+
+
+def test_admm_zero_gram_uses_rho_one():
+    """S = 0 (every other factor has a zero column): trace(S) = 0, the reading
+    takes rho = 1, so one step from H = [0.5, 0.5], U = 0 with M = [1, -1] is
+    Htil = M + H = [1.5, -0.5], H = [1.5, 0], U = [0, 0.5] (rho = 2 would give
+    Htil = [1, 0])."""
+    S = np.zeros((2, 2))
+    M = np.array([[1.0, -1.0]])
+    H, U, k = o.nls_admm(S, M, np.array([[0.5, 0.5]]), max_inner=1, return_state=True)
+    assert k == 1
+    np.testing.assert_array_equal(H, [[1.5, 0.0]])
+    np.testing.assert_array_equal(U, [[0.0, 0.5]])
+
+
+def test_fit_identity_zero_tensor():
+    """alpha = 0 (an all-zero tensor) reports eps = 0 and fit = 1 (reading)."""
+    z = np.zeros((3, 2))
+    eps, fit = o.fit_identity(0.0, z, z, np.ones((2, 2)), np.eye(2), np.zeros(2))
+    assert eps == 0.0 and fit == 1.0
