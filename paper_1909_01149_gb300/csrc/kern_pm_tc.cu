@@ -80,9 +80,12 @@ __device__ __forceinline__ Item decode_item(const TcParams& p, int64_t it) {
 // unrolled to this bound so the per-mode indices stay in registers).
 constexpr int TC_MAXM = 6;
 // Stages accumulated into one TMEM accumulator before the epilogue drains it
-// into FP32 registers: the tensor core's FP32 accumulation is not
-// round-to-nearest, and long chains of accumulations drift low (about 2^-25
-// relative per accumulation); draining every 8 stages bounds the drift.
+// into FP32 registers.  The tensor core's FP32 accumulation truncates each
+// product to the running sum's exponent range, so a chain of positive
+// accumulations drifts low in proportion to its length (measured on the
+// 512^3 workload: 1.4e-6 relative at 8 stages of 4 MMAs, 5.9e-7 at 4, 2.4e-7
+// at 2); 8 stages bound it below the 1e-5 entry tolerance, and the right
+// branch removes it by centring its rows (pm_tcr_kernel).
 constexpr int SEG_STAGES = 8;
 
 // Row k of the Khatri-Rao operand as per-mode row indices (mode 0 fastest).
@@ -747,6 +750,31 @@ pm_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constan
   }
 }
 
+// Row r of a 128 x 32 FP32 X stage stored [rows][32 k] with the 128-byte swizzle.
+__device__ __forceinline__ void lds_row_sw128(uint32_t x, int row, float* v) {
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const uint32_t a = x + row * 128 + (((jj ^ (row & 7)) & 7) << 4);
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[4 * jj + 0]), "=f"(v[4 * jj + 1]), "=f"(v[4 * jj + 2]),
+                   "=f"(v[4 * jj + 3])
+                 : "r"(a)
+                 : "memory");
+  }
+}
+
+// The mean of a row's 32 values in one stage (pairwise sum over 32).
+__device__ __forceinline__ float stage_mean(const float* v) {
+  float t[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) t[c] = v[2 * c] + v[2 * c + 1];
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int c = 0; c < w; ++c) t[c] += t[c + w];
+  return t[0] * (1.f / 32.f);
+}
+
 // ---- resident Khatri-Rao operand ------------------------------------------------------
 //
 // The Khatri-Rao operand factors row-wise as K[k, r] = H_in[k_in, r] * W[k_out, r]:
@@ -787,6 +815,8 @@ struct TcrParams {
                         // items are runs of tpi tiles; each 32-row block (one c)
                         // writes its weighted row sum to out[block * R + r]
   int64_t nblocks;      // blockmode: rows / 32
+  int seg;              // stages accumulated into one TMEM accumulator per drain
+  int center;           // FP32 X, right branch, RB <= 32: rows centred per stage (see kernel)
   float* out;
   int* err;
   const float* Hin;     // resident factor, d_in x R row-major
@@ -861,8 +891,9 @@ __device__ __forceinline__ float warp_reduce_scatter32(float* v, int lane) {
   return v[0];
 }
 
-// RBX: 32 or 64, the register arrays of the epilogue hold RBX columns (RB <= RBX)
-template <bool LEFT, bool F32, int RBX>
+// RBX: 32 or 64, the register arrays of the epilogue hold RBX columns (RB <= RBX);
+// CEN: the right branch with FP32 X and RB <= 32 centres its rows (see below)
+template <bool LEFT, bool F32, int RBX, bool CEN = false>
 __global__ void __launch_bounds__(F32 ? 352 : 192, 1)
 pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcrParams p) {
   constexpr int BKX = F32 ? F_BK : BK;             // reduction elements per stage
@@ -878,6 +909,26 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   // right branch's epilogue, already its limit there, would read a third
   // accumulator: slower in A/B)
   constexpr bool DUAL = F32 && (RBX == 32 || LEFT);
+  // Row centring (FP32 X, right branch, RB <= 32).  The tensor core's FP32
+  // accumulation truncates every product to the running sum's exponent
+  // range, so a chain of all-positive accumulations loses a little on every
+  // MMA and comes out low (about 1.4e-6 relative after the 32 MMAs of an
+  // 8-stage segment, nearly the same in every entry).  The right branch
+  // yields the last mode's MTTKRP, whose inner product with the updated
+  // factor is the error identity's beta, so there the converters feed the
+  // MMA x' = x - c_g for every stage of a drain segment g, with c_g the
+  // mean of the row's 32 values in the segment's first stage: the partial
+  // sums stay small and change sign, and the truncation errors cancel.  The
+  // converters hand c_g to the epilogue through a ring of four slots of 128
+  // floats (c_full / c_empty); the epilogue adds back c_g colsum_g(H_in)[r]
+  // when it drains segment g (any c_g is exact here, as long as both sides
+  // use the same value).  A per-segment c keeps the converters' added work
+  // to one subtraction per element (the converters set the pace of this
+  // kernel).  (A uniform bias in the left branch only rescales lambda, which
+  // the normalisation after each update absorbs.)
+  static_assert(!CEN || (F32 && RBX == 32 && !LEFT), "centring: FP32 right branch, RB <= 32");
+  constexpr bool CENTER = CEN;
+  constexpr bool cen = CEN;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -897,6 +948,29 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* red = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(drain) + 16);  // 4 x 64
+  // H_in (d_in x R, row-major FP32) arrives by one bulk copy into the X stage
+  // area (idle until the pipeline starts) when aligned and small enough; the
+  // image below is then built from shared memory
+  uint64_t* hbar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(red) + 1024);
+  // centring: c_full[4] (converters -> epilogue), c_empty[4] (back), the
+  // ring cring[slot * BM + row], and the column sums of H_in over each drain
+  // segment, ksg[g * RB + r] = sum_{k in segment g} H_in[k, r]
+  const int nsegs = (p.nst + p.seg - 1) / p.seg;
+  uint64_t* c_full = hbar + 1;
+  uint64_t* c_empty = c_full + 4;
+  float* cring = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(c_empty + 4) + 15) & ~static_cast<uintptr_t>(15));
+  float* ksg = cring + (cen ? 4 * BM : 0);
+  {
+    // the layout must fit the dynamic shared memory the launch provides
+    uint32_t dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const uintptr_t end = reinterpret_cast<uintptr_t>(ksg + (cen ? nsegs * RB : 0));
+    if (end - reinterpret_cast<uintptr_t>(smem_raw) > (uintptr_t)dyn) {
+      if (threadIdx.x == 0) atomicExch(p.err, 31);
+      return;  // uniform: no barrier, TMEM or memory access has happened yet
+    }
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -913,15 +987,17 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
       mbar_init(&acc_empty[b], 4);
     }
     mbar_init(drain, DUAL ? 2 : 1);
+    if (cen) {
+      for (int b = 0; b < 4; ++b) {
+        mbar_init(&c_full[b], 4);   // the converter warps
+        mbar_init(&c_empty[b], 4);  // the epilogue warps
+      }
+    }
     *abort = 0;
     fence_mbar_init();
   }
   pdl_wait();  // the factors of the previous mode update are complete
   pdl_trigger();
-  // H_in (d_in x R, row-major FP32) arrives by one bulk copy into the X stage
-  // area (idle until the pipeline starts) when aligned and small enough; the
-  // image below is then built from shared memory
-  uint64_t* hbar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(red) + 1024);
   const uint32_t hbytes = (uint32_t)((int64_t)p.d_in * p.R * 4);
   const bool hbulk = (hbytes & 15u) == 0 && (reinterpret_cast<uintptr_t>(p.Hin) & 15u) == 0 &&
                      (size_t)hbytes <= (size_t)stages * XST;
@@ -974,6 +1050,35 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
           *reinterpret_cast<__nv_bfloat16*>(bb + sw128_off(2 * RB + r, kk)) =
               __float2bfloat16_rn(r1 - __bfloat162float(mid));
         }
+      }
+    }
+    if (cen) {
+      // one warp per column sum: the lanes split the segment's rows and the
+      // partial sums are combined with their rounding errors (Knuth's
+      // TwoSum), so the sum is exact to about one FP32 rounding
+      const int kseg = p.seg * BKX;
+      const int nw = (int)blockDim.x >> 5;
+      for (int e = warp; e < nsegs * RB; e += nw) {
+        const int g = e / RB, r = e - (e / RB) * RB;
+        float sm = 0.f, cm = 0.f;
+        if (r < p.R) {
+          const int k1 = min(p.d_in, (g + 1) * kseg);
+          for (int k = g * kseg + lane; k < k1; k += 32) {
+            const float x = hsrc[k * p.R + r];
+            const float t = sm + x, z = t - sm;
+            cm += (sm - (t - z)) + (x - z);
+            sm = t;
+          }
+        }
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {
+          const float so = __shfl_xor_sync(0xffffffffu, sm, w);
+          const float co = __shfl_xor_sync(0xffffffffu, cm, w);
+          const float t = sm + so, z = t - sm;
+          cm += co + ((sm - (t - z)) + (so - z));
+          sm = t;
+        }
+        if (lane == 0) ksg[e] = sm + cm;
       }
     }
     fence_proxy_async_smem();
@@ -1056,7 +1161,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
       for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
         for (int u = 0; u < nsub && ok; ++u) {
           for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
-            for (int g0 = 0; g0 < p.nst && ok; g0 += SEG_STAGES) {
+            for (int g0 = 0; g0 < p.nst && ok; g0 += p.seg) {
               if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 22)) {
                 ok = false;
                 break;
@@ -1066,7 +1171,7 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
               const uint32_t d =
                   tmem + d_col0 + (uint32_t)buf * d_stride + (lo_warp ? (uint32_t)(2 * RB) : 0u);
               uint32_t acc = 0;
-              const int g1 = min(p.nst, g0 + SEG_STAGES);
+              const int g1 = min(p.nst, g0 + p.seg);
               for (int j = g0; j < g1; ++j) {
                 // FP32: the converters consume X and hand over TMEM slots;
                 // BF16: the MMA reads the X tile itself
@@ -1134,47 +1239,75 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     int s = 0, as = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
+    // centring: this segment's c, the stage's place in its segment, and the
+    // ring slot with the slot phases
+    float cseg = 0.f;
+    int jseg = 0, cb = 0;
+    uint32_t cph = 0;
     for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
       for (int u = 0; u < nsub && ok; ++u) {
         for (int64_t o = item_o0(it); o < item_o1(it) && ok; ++o) {
           for (int j = 0; j < p.nst; ++j) {
-            if (!mbar_wait(&full_x[s], ph, abort, p.err, 25)) { ok = false; break; }
-            if (!mbar_wait(&a_empty[as], aph ^ 1, abort, p.err, 26)) { ok = false; break; }
-            const uint32_t x = smem_u32(Xs + (size_t)s * XST);
-            float v[F_BK];
-            if (LEFT) {
+            {
+              if (!mbar_wait(&full_x[s], ph, abort, p.err, 25)) { ok = false; break; }
+              if (!mbar_wait(&a_empty[as], aph ^ 1, abort, p.err, 26)) { ok = false; break; }
+              const uint32_t x = smem_u32(Xs + (size_t)s * XST);
+              float v[F_BK];
+              if (LEFT) {
 #pragma unroll
-              for (int c = 0; c < F_BK; ++c) v[c] = lds_f32(x + c * 512 + row * 4);
-            } else {
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {
-                const uint32_t a = x + row * 128 + (((jj ^ (row & 7)) & 7) << 4);
-                asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                             : "=f"(v[4 * jj + 0]), "=f"(v[4 * jj + 1]), "=f"(v[4 * jj + 2]),
-                               "=f"(v[4 * jj + 3])
-                             : "r"(a)
-                             : "memory");
+                for (int c = 0; c < F_BK; ++c) v[c] = lds_f32(x + c * 512 + row * 4);
+              } else {
+                lds_row_sw128(x, row, v);
               }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&x_empty[s]);
-            tc_fence_after();
-            uint32_t hi[F_BK], lo[F_BK];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&x_empty[s]);
+              tc_fence_after();
+              if constexpr (CENTER) {
+                if (cen) {
+                  if (j == 0) jseg = 0;
+                  if (jseg == 0) {
+                    // first stage of a segment: its c goes to a ring slot once
+                    // the drain that last read the slot (four segments back)
+                    // has taken it
+                    if (!mbar_wait(&c_empty[cb], ((cph >> cb) & 1u) ^ 1u, abort, p.err, 29)) {
+                      ok = false;
+                      break;
+                    }
+                    cph ^= 1u << cb;
+                    cseg = stage_mean(v);
+                    cring[cb * BM + row] = cseg;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&c_full[cb]);
+                    cb = (cb + 1) & 3;
+                  }
 #pragma unroll
-            for (int c = 0; c < F_BK; ++c) {
-              const float h = tf32_rn(v[c]);
-              hi[c] = __float_as_uint(h);
-              lo[c] = __float_as_uint(tf32_rn(v[c] - h));
+                  for (int c = 0; c < F_BK; ++c) v[c] -= cseg;
+                  if (++jseg == p.seg) jseg = 0;
+                }
+              }
+              // 3xTF32 split: hi = x with the 13 low mantissa bits cleared
+              // (exact in TF32), lo = x - hi (exact in FP32).  The MMA reads
+              // lo by dropping its own low bits, a truncation toward zero:
+              // centred rows have both signs and the errors cancel; otherwise
+              // lo is rounded to TF32 first so that the split stays unbiased.
+              uint32_t hi[F_BK], lo[F_BK];
+#pragma unroll
+              for (int c = 0; c < F_BK; ++c) {
+                const uint32_t hb = __float_as_uint(v[c]) & 0xffffe000u;
+                hi[c] = hb;
+                const float l = v[c] - __uint_as_float(hb);
+                lo[c] = cen ? __float_as_uint(l) : __float_as_uint(tf32_rn(l));
+              }
+              const uint32_t a = tmem + lane_base + (uint32_t)as * 64u;
+              tmem_st16(a, hi);
+              tmem_st16(a + 16, hi + 16);
+              tmem_st16(a + 32, lo);
+              tmem_st16(a + 48, lo + 16);
+              tmem_st_wait();
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&a_full[as]);
             }
-            const uint32_t a = tmem + lane_base + (uint32_t)as * 64u;
-            tmem_st16(a, hi);
-            tmem_st16(a + 16, hi + 16);
-            tmem_st16(a + 32, lo);
-            tmem_st16(a + 48, lo + 16);
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[as]);
             if (++s == stages) { s = 0; ph ^= 1; }
             if (++as == aslots) { as = 0; aph ^= 1; }
           }
@@ -1187,6 +1320,8 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     const int row = q * 32 + lane;
     uint32_t fph = 0;
     int buf = 0;
+    int eb = 0;         // centring: ring slot of the segment being drained
+    uint32_t ecph = 0;  // and the phases of c_full
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
       float sum[RBX];
@@ -1199,15 +1334,16 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
         }
         // Weights.  Left: W[o] is the same for every row of the tile; one warp
         // stages it in shared memory before the accumulator wait.  Right: row
-        // (j, c) carries W[j]; held in registers for RBX = 32, read per
-        // 16-column chunk for RBX = 64 (register budget).
+        // (j, c) carries W[j]; held in registers for BF16 X with RBX = 32,
+        // read per 16-column chunk otherwise (register budget).
         const float* wrow[TC_MAXM];
-        float wreg[RBX == 32 ? 32 : 1];
+        constexpr bool WREG = !F32 && RBX == 32;
+        float wreg[WREG ? 32 : 1];
         const bool weighted = p.W.nm > 0;
         if (!LEFT && weighted) {
           const int64_t jrow = (tile_m0(it, u) + row) % p.jdim;
           tcr_rows(p, jrow, wrow);
-          if constexpr (RBX == 32) {
+          if constexpr (WREG) {
             tcr_w16(p, wrow, 0, wreg);
             tcr_w16(p, wrow, 1, wreg + 16);
           }
@@ -1221,8 +1357,19 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
             }
             asm volatile("bar.sync 2, 128;" ::: "memory");
           }
-          for (int g0 = 0; g0 < p.nst; g0 += SEG_STAGES) {
+          for (int g0 = 0; g0 < p.nst; g0 += p.seg) {
             if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 27)) { ok = false; break; }
+            // centring: this row's c of the segment (the slot goes back to the
+            // converters once it is in a register)
+            float cseg = 0.f;
+            if (CENTER && cen) {
+              if (!mbar_wait(&c_full[eb], (ecph >> eb) & 1u, abort, p.err, 30)) { ok = false; break; }
+              ecph ^= 1u << eb;
+              cseg = cring[eb * BM + row];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&c_empty[eb]);
+              eb = (eb + 1) & 3;
+            }
             fph ^= 1u << buf;
             tc_fence_after();
             const uint32_t taddr =
@@ -1230,27 +1377,37 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < RBX / 16; ++c) {
               if (c * 16 < RB) {
-                // FP32: x_hi k_hi + (x_hi k_lo + x_lo k_hi); BF16: hi + (mid + lo)
-                float v[16], t1[16];
+                // FP32: x_hi k_hi + (x_hi k_lo + x_lo k_hi) [+ centring
+                // correction]; BF16: hi + (mid + lo)
+                float v[16], t1[16], t2[16];
                 tmem_ld16(taddr + c * 16, v);
                 tmem_ld16(taddr + RB + c * 16, t1);
+                if (!F32 || DUAL) tmem_ld16(taddr + 2 * RB + c * 16, t2);
+                tmem_ld_wait();
                 if (!F32 || DUAL) {
-                  float t2[16];
-                  tmem_ld16(taddr + 2 * RB + c * 16, t2);
-                  tmem_ld_wait();
 #pragma unroll
                   for (int jj = 0; jj < 16; ++jj) t1[jj] += t2[jj];
-                } else {
-                  tmem_ld_wait();
                 }
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] += t1[jj];
+                if (CENTER && cen) {
+                  // + c_g colsum_g(H_in)[16 c + jj]
+                  const float* kg = ksg + (g0 / p.seg) * RB + c * 16;
+#pragma unroll
+                  for (int q4 = 0; q4 < 4; ++q4) {
+                    const float4 k4 = *reinterpret_cast<const float4*>(kg + 4 * q4);
+                    v[4 * q4 + 0] = fmaf(cseg, k4.x, v[4 * q4 + 0]);
+                    v[4 * q4 + 1] = fmaf(cseg, k4.y, v[4 * q4 + 1]);
+                    v[4 * q4 + 2] = fmaf(cseg, k4.z, v[4 * q4 + 2]);
+                    v[4 * q4 + 3] = fmaf(cseg, k4.w, v[4 * q4 + 3]);
+                  }
+                }
                 if (weighted) {
                   float w[16];
                   if (LEFT) {
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) w[jj] = ws[c * 16 + jj];
-                  } else if constexpr (RBX == 32) {
+                  } else if constexpr (WREG) {
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) w[jj] = wreg[c * 16 + jj];
                   } else {
@@ -1498,7 +1655,9 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
   const size_t xst = (size_t)BM * bk * e;
   const size_t budget = 227 * 1024 - 256;
   for (int st = 6; st >= 3; --st) {
-    const size_t total = 1024 + st * xst + bimg + (2 * st + 2 * F_A_SLOTS + 5) * 8 + 16 + 1024 + 16;
+    // ... barriers, TMEM slot, reduction area, H_in barrier, column sums
+    const size_t total = 1024 + st * xst + bimg + (2 * st + 2 * F_A_SLOTS + 5) * 8 + 16 + 1024 +
+                         16 + 64 + 16 + 4 * BM * 4 + (size_t)pl.nst * pl.RB * 4;
     if (total <= budget) {
       pl.stages = st;
       pl.smem = total;
@@ -1541,6 +1700,25 @@ size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C,
 
 namespace {
 
+// FP32 row centring in the tensor-core partial MTTKRP (PLANC_PM_CENTER=0 turns it off)
+bool tcr_center() {
+  static const bool on = [] {
+    const char* v = getenv("PLANC_PM_CENTER");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+// stages per accumulator drain (PLANC_PM_SEG overrides; 1..64)
+int tcr_seg_stages(bool f32) {
+  static const int env = [] {
+    const char* v = getenv("PLANC_PM_SEG");
+    return v ? atoi(v) : 0;
+  }();
+  (void)f32;
+  return (env >= 1 && env <= 64) ? env : SEG_STAGES;
+}
+
 cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
                        const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
                        size_t work_bytes, int* err_flag, const TcrPlan& pl, cudaStream_t st) {
@@ -1578,6 +1756,8 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   }
   p.blockmode = pl.blockmode ? 1 : 0;
   p.nblocks = pl.nblocks;
+  p.seg = tcr_seg_stages(f32);
+  p.center = (f32 && !left && pl.RB <= 32 && tcr_center()) ? 1 : 0;
   if (pl.blockmode) {
     if (work_bytes < (size_t)pl.nblocks * R * sizeof(float)) return cudaErrorInvalidValue;
     p.out_mode = 3;
@@ -1618,7 +1798,9 @@ cudaError_t launch_tcr(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, b
   cudaError_t err;
   auto k = pl.RB <= 32
                ? (left ? (f32 ? pm_tcr_kernel<true, true, 32> : pm_tcr_kernel<true, false, 32>)
-                       : (f32 ? pm_tcr_kernel<false, true, 32> : pm_tcr_kernel<false, false, 32>))
+                       : (f32 ? (p.center ? pm_tcr_kernel<false, true, 32, true>
+                                          : pm_tcr_kernel<false, true, 32>)
+                              : pm_tcr_kernel<false, false, 32>))
                : (left ? (f32 ? pm_tcr_kernel<true, true, 64> : pm_tcr_kernel<true, false, 64>)
                        : (f32 ? pm_tcr_kernel<false, true, 64> : pm_tcr_kernel<false, false, 64>));
   err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
