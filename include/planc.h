@@ -380,8 +380,9 @@ planc_status_t planc_batch_schedule(int* out);
  * equals planc_sqnorm's.
  *
  * The first call on each device looks up that array's device address with
- * cudaGetSymbolAddress while the device is current; make that first call
- * outside any stream capture.  All calls share the one array, so calls whose
+ * cudaGetSymbolAddress while the device is current (and looks it up again
+ * when the device's CUDA context has been destroyed and created anew since);
+ * make that first call outside any stream capture.  All calls share the one array, so calls whose
  * work overlaps on the GPU (different streams, no ordering between them) race
  * on it; calls ordered on one stream are safe.  Every call overwrites the
  * partials it reads, so nothing needs clearing between calls.

@@ -21,23 +21,55 @@ static __device__ __align__(256) double g_sqnorm_partials[kMaxPartials];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_partials_addr[kMaxDevices] = {};
+// the array's device address per device, with the CUDA context it was looked
+// up in: a context that is torn down and created again (cudaDeviceReset, a
+// primary-context reset) loads the library's module anew, and the array may
+// then sit elsewhere, so an address is reused only inside its own context
+struct Cached {
+  void* ctx;
+  double* addr;
+};
+Cached g_cache[kMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per
-// device with that device current.
+// cuCtxGetCurrent through the runtime's driver entry point (no link-time
+// dependency on the driver library)
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(f);
+  });
+  return fn;
+}
+
+// Device address of the array in the current device's current context,
+// looked up with that device current the first time it is needed there.
 cudaError_t partials_on_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  CtxGetCurrentFn get = ctx_get_current();
+  void* ctx = nullptr;
+  if (get == nullptr || get(&ctx) != 0) return cudaErrorInitializationError;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_partials_addr[dev] == nullptr) {
+  if (ctx == nullptr || g_cache[dev].addr == nullptr || g_cache[dev].ctx != ctx) {
     void* p = nullptr;
+    // (with no context current on this thread yet, the lookup makes the
+    // device's primary context current, and the handle is read after it)
     e = cudaGetSymbolAddress(&p, g_sqnorm_partials);
     if (e != cudaSuccess) return e;
-    g_partials_addr[dev] = static_cast<double*>(p);
+    if (ctx == nullptr && (get(&ctx) != 0 || ctx == nullptr)) return cudaErrorInitializationError;
+    g_cache[dev].ctx = ctx;
+    g_cache[dev].addr = static_cast<double*>(p);
   }
-  *out = g_partials_addr[dev];
+  *out = g_cache[dev].addr;
   return cudaSuccess;
 }
 
