@@ -18,6 +18,10 @@ Recipes (one per workload):
                             trial gains, Poisson-like noise at 10 dB SNR
   batch(count)              many small uneven 3-way planted problems
   init_factors(dims, R)     U[0,1) initial factors, drawn in mode order
+  perturbed_factors(A)      planted factors times 1 + 10% U[-1,1) (start
+                            near the solution)
+  decaying(dims, R)         planted tensor whose mode-1 factor columns decay
+                            exponentially (fibres spanning orders of magnitude)
 """
 
 from __future__ import annotations
@@ -128,6 +132,31 @@ def batch(count=256, data_seed=1, noise=0.02, lo=32, hi=160, rlo=8, rhi=32,
         X, A = planted(dims, R, data_seed * 1000 + i, noise, dtype)
         out.append((X, A, R))
     return out
+
+
+def perturbed_factors(A, level=0.1, seed=3, dtype=np.float64):
+    """Start factors near planted ones: A_n * (1 + level * U[-1, 1)) entry
+    by entry, drawn in mode order from `seed` (a start close to the
+    solution, for runs that should reach the noise floor)."""
+    rng = np.random.default_rng(seed)
+    return [(a * (1.0 + level * (2.0 * rng.random(a.shape) - 1.0))).astype(dtype) for a in A]
+
+
+def decaying(dims, R, data_seed=1, noise=0.01, tau=(5.0, 40.0), dtype=np.float32):
+    """Planted tensor whose mode-1 factor columns decay, A_1[i, r] =
+    exp(-i / tau_r) with tau_r ~ U[tau): along mode 1 every fibre falls by
+    orders of magnitude (rows whose scale drifts inside a reduction); the
+    other factors U[0, 1); noise as in planted().  Returns (X, A)."""
+    rng = np.random.default_rng(data_seed)
+    taus = rng.uniform(tau[0], tau[1], R)
+    A = [np.exp(-np.arange(dims[0])[:, None] / taus[None, :])]
+    A += [rng.random((d, R)) for d in dims[1:]]
+    M = _cp_dense(A, dtype=np.float64)
+    if noise > 0:
+        level = noise * float(M.mean())
+        flat_m = M.reshape(-1, order="F")
+        flat_m += level * rng.random(flat_m.size)
+    return M.astype(dtype, order="F"), A
 
 
 # ----------------------------------------------------------------------------
