@@ -216,24 +216,26 @@ def run_planc(args, cfg):
     torch.cuda.synchronize()
 
     # --- timed region: K steps, device-timed with events on the launch stream
+    # (one event between consecutive steps: the step times, their median)
     clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
     launches = 0
-    for _ in range(args.steps):
+    for k in range(args.steps):
         res = step()
         launches += res["launches"]
-    e1.record(stream)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
-    ms = allreduce_max(e0.elapsed_time(e1), ws)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = allreduce_max(ev[0].elapsed_time(ev[-1]), ws)
+    med_ms = allreduce_max(statistics.median(step_ms), ws)
     from paper_1909_01149_gb300 import replicas
-    value = replicas.job_throughput(args.steps * iters, ws, ms)
+    value = replicas.job_throughput(iters, ws, med_ms)
     rel_err = res["rel_err"][-1]
 
     # --- partial-MTTKRP launch durations (events around each launch, same stream)
@@ -285,7 +287,10 @@ def run_planc(args, cfg):
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "iter/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(med_ms, 4),
+        "step_stats": {"median_ms": round(med_ms, 4), "mean_ms": round(ms / args.steps, 4),
+                       "min_ms": round(min(step_ms), 4), "max_ms": round(max(step_ms), 4),
+                       "value_from": "median step time (iterations per step / median)"},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if cfg["dtype"] == "f64" else "f32" if cfg["dtype"] == "f32" else "bf16-storage/f32-accumulate",
         "data": "synthetic (seeded planted CP tensor; no dataset)",
@@ -311,15 +316,24 @@ def run_planc(args, cfg):
     torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_mixed and args.config == "dense512-f32":
         out["mixed"] = run_mixed(args)
+    tol = 1e-5 if cfg["dtype"] != "f64" else 1e-10
+    hist = golden_history(args.config, cfg, alg)
+    if rank == 0 and hist is not None:
+        # the GPU's error history against the FP64 oracle's on the same inputs
+        # (oracle.nncp, stored by tests/golden/make_fullsize_golden.py)
+        d = [abs(a - b) for a, b in zip(res["rel_err"], hist)]
+        out["oracle_check"] = {"source": "tests/golden/fullsize_oracle.json (oracle.nncp)",
+                               "iters": len(d), "max_abs_diff": max(d),
+                               "final_gpu": res["rel_err"][-1], "final_oracle": hist[-1],
+                               "tolerance": tol}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(cfg, X, H0, alg)
-        # the GPU result against the FP64 oracle on the same inputs: relative
-        # error after the first outer iteration (the oracle's bounded sample)
+        cb = cpu_baseline(cfg, X, H0, alg, args.config)
+        # live: the oracle's first outer iteration against the GPU's
         o1 = cb.pop("rel_err_iter1")
         out["cpu_baseline"] = cb
-        out["oracle_check"] = {"iter": 1, "gpu_rel_err": res["rel_err"][0], "oracle_rel_err": o1,
-                               "abs_diff": abs(res["rel_err"][0] - o1),
-                               "tolerance": 1e-5 if cfg["dtype"] != "f64" else 1e-10}
+        out.setdefault("oracle_check", {})["live_iter1"] = {
+            "gpu_rel_err": res["rel_err"][0], "oracle_rel_err": o1,
+            "abs_diff": abs(res["rel_err"][0] - o1), "tolerance": tol}
     return out, rank
 
 
@@ -546,73 +560,186 @@ def run_batch(args):
     return out, 0
 
 
+def pm_alg_bytes(dims, split, R, xb, fb=4):
+    """Algorithmic bytes of one partial-MTTKRP launch, averaged over the two
+    root branches: X once, the partial result once, the factor rows of the
+    Khatri-Rao operand."""
+    L = int(np.prod(dims[:split]))
+    Cc = int(np.prod(dims[split:]))
+    I = L * Cc
+    left_b = I * xb + L * R * fb + sum(dims[split:]) * R * fb
+    right_b = I * xb + Cc * R * fb + sum(dims[:split]) * R * fb
+    return (left_b + right_b) / 2.0
+
+
 def run_mixed(args):
-    """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP), equal
-    iterations from the same initial factors.  'fp32_same_values' stores the
-    BF16-rounded tensor in FP32, so it solves the identical problem with FP32
-    streaming: the comparison at equal fit.  'fp32' solves the unrounded
-    tensor; 'bf16_err_vs_unrounded' is the BF16 solution's relative error
-    measured against the unrounded tensor."""
+    """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP, 30 outer
+    iterations from the same initial factors).  Arms: 'bf16'; 'fp32_same_values'
+    (the BF16-rounded tensor stored in FP32: the identical problem with FP32
+    streaming); 'fp32' (the unrounded tensor).  Each arm: outer iterations/s
+    (median of timed solves) and the event-timed partial-MTTKRP roofline, with
+    the clocks sampled during the timed solves.  'seeds': BF16 vs FP32 on the
+    unrounded tensor for data seeds 1-3, both final errors, and the speed at
+    matched error (outer iterations each needs to reach the FP32 run's final
+    error, over its iterations/s)."""
     import torch
     from paper_1909_01149_gb300 import planc, synth
     cfg = CONFIGS["mouse4d-bf16"]
+    dims, R, iters = cfg["dims"], cfg["R"], cfg["iters"]
+    peak, peak_kind = measured_peak()
     X, H0 = make_inputs(cfg)
     flat = synth.flat(X)
     Xb = torch.from_numpy(flat).to(torch.bfloat16).cuda()
-    arms = (("bf16", Xb), ("fp32_same_values", Xb.float()),
-            ("fp32", torch.from_numpy(flat).cuda()))
-    out = {"workload": cfg["workload"], "alg": cfg["alg"], "iters": cfg["iters"]}
+    arms = (("bf16", Xb, 2), ("fp32_same_values", Xb.float(), 4),
+            ("fp32", torch.from_numpy(flat).cuda(), 4))
+    out = {"workload": cfg["workload"], "alg": cfg["alg"], "iters": iters}
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     Hbf = None
-    for name, Xd in arms:
+    for name, Xd, xb in arms:
         H0d = [torch.from_numpy(h).cuda() for h in H0]
         H = [h.clone() for h in H0d]
-        with planc.Context(Xd, cfg["dims"], cfg["R"]) as ctx:
-            def step():
+        with planc.Context(Xd, dims, R) as ctx:
+            def step(profile=False):
                 for h, h0 in zip(H, H0d):
                     h.copy_(h0)
-                return ctx.solve(H, alg=cfg["alg"], iters=cfg["iters"])
-            for _ in range(2):
+                return ctx.solve(H, alg=cfg["alg"], iters=iters, use_graph=not profile,
+                                 profile=profile)
+            for _ in range(3):
                 step()
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            n = max(2, args.steps // 2)
-            for _ in range(n):
+            n = max(5, args.steps // 2)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+            ev[0].record()
+            for k in range(n):
                 r = step()
-            e1.record()
+                ev[k + 1].record()
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            out[name] = {"iter_s": round(n * cfg["iters"] / (ms / 1e3), 2),
-                         "rel_err": r["rel_err"][-1], "tc_mask": ctx.tc_mask}
+            med = statistics.median(ev[k].elapsed_time(ev[k + 1]) for k in range(n))
+            prof = step(profile=True)
+            torch.cuda.synchronize()
+            avg_ms = prof["pm_ms"] / max(prof["pm_launches"], 1)
+            ab = pm_alg_bytes(dims, ctx.split, R, xb)
+            gbs = ab / (avg_ms / 1e3) / 1e9
+            out[name] = {"iter_s": round(iters / (med / 1e3), 2), "rel_err": r["rel_err"][-1],
+                         "tc_mask": ctx.tc_mask,
+                         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                                      "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                      "peak_kind": peak_kind,
+                                      "algorithmic_bytes_per_launch": ab,
+                                      "avg_launch_ms": round(avg_ms, 5),
+                                      "launches_timed": prof["pm_launches"]}}
             if name == "bf16":
                 Hbf = ([h.clone() for h in H], torch.tensor(r["lam"], dtype=torch.float64,
                                                               device="cuda"))
             if name == "fp32" and Hbf is not None:
                 out["bf16_err_vs_unrounded"] = ctx.fit(Hbf[0], Hbf[1])[0]
+    out["clocks"] = clocks.stop()
     out["rel_err_diff_same_values"] = abs(out["bf16"]["rel_err"] -
                                           out["fp32_same_values"]["rel_err"])
     out["speedup_bf16_over_fp32"] = round(out["bf16"]["iter_s"] /
                                           out["fp32_same_values"]["iter_s"], 3)
     del Xb, arms
     torch.cuda.empty_cache()
+    # seeds: BF16 storage vs FP32 on the unrounded tensor, matched error
+    seeds = []
+    for seed in (1, 2, 3):
+        Xs, _ = synth.mouse_like(dims, R, data_seed=seed, dtype=np.float32)
+        Hs0 = synth.init_factors(dims, R, seed + 1, dtype=np.float32)
+        fl = synth.flat(Xs)
+        hist = {}
+        for name, Xd in (("bf16", torch.from_numpy(fl).to(torch.bfloat16).cuda()),
+                         ("fp32", torch.from_numpy(fl).cuda())):
+            H = [torch.from_numpy(h).cuda() for h in Hs0]
+            with planc.Context(Xd, dims, R) as ctx:
+                hist[name] = ctx.solve(H, alg=cfg["alg"], iters=2 * iters)["rel_err"]
+            del Xd
+        target = hist["fp32"][iters - 1]
+        need = {k: next((i + 1 for i, e in enumerate(v) if e <= target), None)
+                for k, v in hist.items()}
+        t = {k: (need[k] / out[k]["iter_s"] if need[k] else None) for k in need}
+        seeds.append({"data_seed": seed, "final_bf16": hist["bf16"][iters - 1],
+                      "final_fp32": hist["fp32"][iters - 1],
+                      "diff": abs(hist["bf16"][iters - 1] - hist["fp32"][iters - 1]),
+                      "iters_to_fp32_final": need,
+                      "speedup_at_matched_error": (round(t["fp32"] / t["bf16"], 3)
+                                                   if t["bf16"] else None)})
+    out["seeds"] = seeds
+    torch.cuda.empty_cache()
     return out
 
 
-def cpu_baseline(cfg, X, H0, alg):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_one_iteration(config, alg):
+    """Seconds for one outer iteration of the FP64 oracle on the full
+    workload (inputs regenerated here, not timed)."""
+    import oracle as o
+    X, H0 = make_inputs(CONFIGS[config])
+    Xs = np.asarray(X, dtype=np.float64)
+    Hs = [np.asarray(h, dtype=np.float64) for h in H0]
+    t = time.time()
+    ref = o.nncp(Xs, Hs, alg, iters=1)
+    return time.time() - t, ref["rel_err"][0]
+
+
+def cpu_baseline(cfg, X, H0, alg, config):
     """The FP64 oracle, as it stands, on a bounded sample: one outer iteration
-    of the full workload (every mode's MTTKRP, NNLS, normalisation, error)."""
+    of the full workload (every mode's MTTKRP, NNLS, normalisation, error),
+    with BLAS on all host cores (this process) and on one thread (a fresh
+    interpreter started with the BLAS and OpenMP thread counts set to 1)."""
     import oracle as o
     Xs = np.asarray(X, dtype=np.float64)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     t = time.time()
     ref = o.nncp(Xs, Hs, alg, iters=1)
     dt = time.time() - t
-    return {"value": round(1.0 / dt, 5), "unit": "iter/s", "cores": os.cpu_count(),
-            "kind": "oracle",
+    one = None
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-iteration",
+                            config, alg], env=env, capture_output=True, text=True, timeout=600)
+        one = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError, KeyError):
+        one = None
+    cores = os.cpu_count()
+    return {"value": round(1.0 / dt, 5), "unit": "iter/s", "cores": cores, "kind": "oracle",
             "sample": f"1 outer iteration (alpha, {len(cfg['dims'])} mode updates, error) "
-                      f"of the full {cfg['workload']} workload, NumPy FP64, default BLAS threads",
+                      f"of the full {cfg['workload']} workload, NumPy FP64",
+            "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS", f"default ({cores})"),
+            "cpu_model": cpu_model(),
+            "one_thread": ({"value": round(1.0 / one, 5), "unit": "iter/s", "cores": 1,
+                            "seconds_per_iter": round(one, 3)} if one else None),
+            "seconds_per_iter": round(dt, 3),
             "rel_err_iter1": ref["rel_err"][0]}
+
+
+def golden_history(config, cfg, alg):
+    """The oracle's error history for this workload from the committed golden
+    file (tests/golden/fullsize_oracle.json), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
+    if config != "dense512-f32" or not os.path.exists(path):
+        return None
+    g = json.load(open(path)).get("dense512", {})
+    if tuple(g.get("dims", ())) != tuple(cfg["dims"]) or g.get("iters") != cfg["iters"]:
+        return None
+    return g.get(alg, {}).get("rel_err")
 
 
 def run_reference(args, cfg):
@@ -629,21 +756,27 @@ def run_reference(args, cfg):
     alg = args.alg or cfg["alg"]
     for _ in range(args.warmup):
         o.nncp(Xs, Hs, alg, iters=1)
-    t = time.time()
+    times = []
     for _ in range(args.steps):
+        t = time.time()
         o.nncp(Xs, Hs, alg, iters=1)
-    dt = time.time() - t
-    v = args.steps / dt
+        times.append(time.time() - t)
+    med = statistics.median(times)
+    v = 1.0 / med
+    cores = os.cpu_count()
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "iter/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+           "ms_per_step": round(1e3 * med, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded planted CP tensor; no dataset)",
            "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "R": cfg["R"],
                       "alg": alg, "outer_iters_per_step": 1},
-           "cpu_baseline": {"value": round(v, 5), "unit": "iter/s", "cores": os.cpu_count(),
-                            "kind": "oracle",
-                            "sample": "1 outer iteration of the full workload per step"},
+           "cpu_baseline": {"value": round(v, 5), "unit": "iter/s", "cores": cores,
+                            "kind": "oracle", "cpu_model": cpu_model(),
+                            "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS",
+                                                           f"default ({cores})"),
+                            "sample": "1 outer iteration of the full workload per step "
+                                      "(median of the steps)"},
            "e2e": {"value": round(v, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     return out, rank
@@ -672,7 +805,13 @@ def main():
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])
     ap.add_argument("--iters", type=int, default=None, help="override outer iterations per step")
+    ap.add_argument("--oracle-one-iteration", nargs=2, metavar=("CONFIG", "ALG"),
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_one_iteration:
+        sec, e1 = oracle_one_iteration(*args.oracle_one_iteration)
+        print(json.dumps({"seconds": sec, "rel_err_iter1": e1}), flush=True)
+        return
     if args.steps is None:
         # 60 solves of the default workload take ~0.9 s, long enough for the
         # 100 ms clock sampler to record several samples inside the timed
