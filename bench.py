@@ -621,11 +621,13 @@ def run_mixed(args):
             avg_ms = prof["pm_ms"] / max(prof["pm_launches"], 1)
             ab = pm_alg_bytes(dims, ctx.split, R, xb)
             gbs = ab / (avg_ms / 1e3) / 1e9
+            traffic = (profiled_traffic(cfg["workload"], pm_source_sha(True))
+                       if name == "bf16" else None)
             out[name] = {"iter_s": round(iters / (med / 1e3), 2), "rel_err": r["rel_err"][-1],
                          "tc_mask": ctx.tc_mask,
                          "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
                                       "unit": "GB/s", "frac": round(gbs / peak, 4),
-                                      "peak_kind": peak_kind,
+                                      "traffic": traffic, "peak_kind": peak_kind,
                                       "algorithmic_bytes_per_launch": ab,
                                       "avg_launch_ms": round(avg_ms, 5),
                                       "launches_timed": prof["pm_launches"]}}
