@@ -153,8 +153,11 @@ struct NlsArgs {
   double* scratch;        // FP64 scratch (>= nls_scratch_doubles)
   int* flags;             // int scratch (>= 8 ints)
   bool f64;
+  bool reset_inner = true;  // BPP: zero *inner first (false: the caller did)
 };
 size_t nls_scratch_doubles(int64_t rows, int R);
+// p[0..n) = v (one small launch)
+cudaError_t launch_set_int(int32_t* p, int v, int n, cudaStream_t st);
 // (S + rho I)^{-1} into scr (rho = trace(S)/R, or 0 with ucp): [0] rho,
 // [1] 1 if a pivot was not positive; the inverse (FP64) at scr + 8 and in the
 // factor precision at scr + 8 + R^2

@@ -5,7 +5,8 @@
 //           (MU, Eq. muupd; HALS, Eq. halsupd; projected gradient; the
 //           Nesterov-type steps of Eq. nesinnerupd, with the per-step stop
 //           test reduced over the cluster; ADMM, Eq. admmupd, likewise;
-//           UCP, H = M S^{-1}),
+//           UCP, H = M S^{-1}; BPP: the rows arrive solved by the BPP
+//           kernel, and this launch does the rest),
 //   lambda_r = ||Hhat(:, r)||, H^(n) = Hhat diag(lambda)^{-1}, G^(n) = H^T H,
 //   and after the last mode the error identity of Sec. A.2,
 // in a single launch of one thread-block cluster.
@@ -408,7 +409,8 @@ __device__ __forceinline__ void mode_update_body(
 #pragma unroll
     for (int u = 0; u < S::VPG; ++u) {
       m[g * S::VPG + u] = ms[u];
-      h[g * S::VPG + u] = hs[u] * s_lamt[g * S::VPG + u];  // warm start H diag(lambda)
+      // warm start H diag(lambda); BPP: the solved row Hhat as it is
+      h[g * S::VPG + u] = alg == PLANC_BPP ? hs[u] : hs[u] * s_lamt[g * S::VPG + u];
     }
   }
 
@@ -747,7 +749,7 @@ __device__ __forceinline__ void mode_update_body(
       gam = (r == s ? 1.0 : 2.0) * sv * gh;
     }
   }
-  if (c == 0 && t == 0 && inner)
+  if (c == 0 && t == 0 && inner && alg != PLANC_BPP)  // (BPP: its kernel counts)
     *inner = alg == PLANC_PGD ? pgd_steps
              : alg == PLANC_NES ? (nes_scr[5] != 0.0 ? 0 : nes_steps)
              : alg == PLANC_ADMM ? admm_steps : 1;
@@ -823,6 +825,7 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
               : alg == PLANC_PGD  ? mode_cluster_kernel<TA, RP, PLANC_PGD>
               : alg == PLANC_UCP  ? mode_cluster_kernel<TA, RP, PLANC_UCP>
               : alg == PLANC_ADMM ? mode_cluster_kernel<TA, RP, PLANC_ADMM>
+              : alg == PLANC_BPP  ? mode_cluster_kernel<TA, RP, PLANC_BPP>
                                   : mode_cluster_kernel<TA, RP, PLANC_NES>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -885,7 +888,7 @@ bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
   // to R = 16
   const bool steps_ok = (alg == PLANC_NES || alg == PLANC_ADMM) && (!f64 || R <= 16);
   return (alg == PLANC_MU || alg == PLANC_HALS || alg == PLANC_PGD || alg == PLANC_UCP ||
-          steps_ok) && rows >= 1 &&
+          alg == PLANC_BPP || steps_ok) && rows >= 1 &&
          rows <= (int64_t)MC_CS * MC_RPC && R <= 32;
 }
 

@@ -479,6 +479,16 @@ __global__ void set_int_kernel(int32_t* p, int v, int n) {
   if (i < n) p[i] = v;
 }
 
+}  // namespace
+
+cudaError_t launch_set_int(int32_t* p, int v, int n, cudaStream_t st) {
+  set_int_kernel<<<(n + 255) / 256, 256, 0, st>>>(p, v, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
+
 // ---- UCP (unconstrained, Sec. 6): Hhat = M S^{-1}, one row per thread ----------------
 template <typename TA, int RP>
 __global__ void __launch_bounds__(ROWS_PER_CTA)
@@ -894,7 +904,7 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
     size_t smem = (rl + BPP_WARPS * (rl + 3 * 64)) * sizeof(double);
     cudaFuncSetAttribute(nls_bpp_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    if (a.inner) {
+    if (a.inner && a.reset_inner) {
       set_int_kernel<<<1, 32, 0, st>>>(a.inner, 0, 1);
       note_launches(1);
     }

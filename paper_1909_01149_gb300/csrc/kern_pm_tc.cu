@@ -1323,10 +1323,20 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     int eb = 0;         // centring: ring slot of the segment being drained
     uint32_t ecph = 0;  // and the phases of c_full
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
-      float sum[RBX];
+    // Right branch, BF16 X, R <= 16: two consecutive items of this CTA (two output
+    // rows) accumulate into the two halves of the 32 columns of sum[], and one
+    // warp reduce-scatter and one round of the epilogue barriers write both.
+    // (BF16 X: its right-branch epilogue is this kernel's limit there)
+    constexpr bool PAIRABLE = !F32 && !LEFT && RBX == 32;
+    const bool pair = PAIRABLE && RB <= 16 && !p.blockmode;
+    float sum[RBX];
+    int li = 0;  // items this CTA has started
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x, ++li) {
+      const int half = pair ? (li & 1) : 0;
+      if (half == 0) {
 #pragma unroll
-      for (int r = 0; r < RBX; ++r) sum[r] = 0.f;
+        for (int r = 0; r < RBX; ++r) sum[r] = 0.f;
+      }
       for (int u = 0; u < nsub && ok; ++u) {
         if (!LEFT && p.blockmode) {
 #pragma unroll
@@ -1413,8 +1423,17 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                   } else {
                     tcr_w16(p, wrow, c, w);
                   }
+                  if (RBX == 32 && half) {  // (pair: c == 0, the upper half)
 #pragma unroll
-                  for (int jj = 0; jj < 16; ++jj) sum[c * 16 + jj] = fmaf(v[jj], w[jj], sum[c * 16 + jj]);
+                    for (int jj = 0; jj < 16; ++jj)
+                      sum[(16 + jj) % RBX] = fmaf(v[jj], w[jj], sum[(16 + jj) % RBX]);
+                  } else {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) sum[c * 16 + jj] = fmaf(v[jj], w[jj], sum[c * 16 + jj]);
+                  }
+                } else if (RBX == 32 && half) {
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) sum[(16 + jj) % RBX] += v[jj];
                 } else {
 #pragma unroll
                   for (int jj = 0; jj < 16; ++jj) sum[c * 16 + jj] += v[jj];
@@ -1457,24 +1476,30 @@ pm_tcr_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
           for (int r = 0; r < RBX; ++r)
             if (r < p.R) base[r * stride] = sum[r];
         }
-      } else if (!p.blockmode) {
-        // sum the item's rows (one output row c): reduce-scatter within the
-        // warp (lane r ends with column r), then across the four warps
+      } else if (!p.blockmode && !(pair && half == 0 && it + gridDim.x < p.items)) {
+        // sum the item's rows (one output row c; paired: two items, one per
+        // half of the columns): reduce-scatter within the warp (lane r ends
+        // with column r), then across the four warps
 #pragma unroll
         for (int h = 0; h < RBX / 32; ++h) {
-          if (32 * h < p.R) {
+          if (32 * h < p.R || pair) {
             const float v = warp_reduce_scatter32(sum + 32 * h, lane);
             red[q * 64 + 32 * h + lane] = v;
           }
         }
         asm volatile("bar.sync 2, 128;" ::: "memory");
         const int tid = threadIdx.x - W_EPI * 32;
-        if (tid < p.R) {
+        // paired: columns 16.. belong to this item, 0..15 to the one before
+        const int col = pair ? (tid & 15) : tid;
+        const int64_t iw = (pair && tid < 16 && half) ? it - gridDim.x : it;
+        const bool valid = pair ? (tid < 16 ? col < p.R : (tid < 32 && half && col < p.R))
+                                : tid < p.R;
+        if (valid) {
           const float v = (red[tid] + red[64 + tid]) + (red[128 + tid] + red[192 + tid]);
-          const int64_t c = it / p.nsplit, z = it % p.nsplit;
-          if (p.out_mode == 0) p.out[c + p.Mdim * tid] = v;
-          else if (p.out_mode == 1) p.out[c * p.R + tid] = v;
-          else p.out[z * p.Mdim * p.R + c + p.Mdim * tid] = v;
+          const int64_t c = iw / p.nsplit, z = iw % p.nsplit;
+          if (p.out_mode == 0) p.out[c + p.Mdim * col] = v;
+          else if (p.out_mode == 1) p.out[c * p.R + col] = v;
+          else p.out[z * p.Mdim * p.R + c + p.Mdim * col] = v;
         }
         asm volatile("bar.sync 2, 128;" ::: "memory");
       }

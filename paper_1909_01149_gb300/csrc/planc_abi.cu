@@ -691,12 +691,15 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
   for (int n = 0; n < N; ++n) {
     const int s = side_of(ctx, n);
     const bool fused = ctx->fused_modes && mode_fused_eligible(o.alg, ctx->dims[n], R, is_f64(ctx));
-    const bool prepared = o.alg == PLANC_NES || o.alg == PLANC_UCP || o.alg == PLANC_ADMM;
+    const bool prepared = o.alg == PLANC_NES || o.alg == PLANC_UCP || o.alg == PLANC_ADMM ||
+                          o.alg == PLANC_BPP;
     const bool fork = fused && prepared && ctx->side;
     auto prep = [&](cudaStream_t sp) -> planc_status_t {
       CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, sp), "gram_hadamard launch");
       if (o.alg == PLANC_NES)
         CK(launch_nes_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, sp), "NES prep launch");
+      else if (o.alg == PLANC_BPP)  // the exchange count starts from zero
+        CK(launch_set_int(inner_now + n, 0, 1, sp), "inner reset launch");
       else  // UCP: S^{-1}; ADMM: (S + rho I)^{-1}
         CK(launch_inv_prep(is_f64(ctx), ctx->Sm, R, ctx->nls_scr, o.alg == PLANC_UCP ? 1 : 0, sp),
            "inverse prep launch");
@@ -720,6 +723,25 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
         } else if ((st = prep(ctx->stream)) != PLANC_OK) {
           return st;
         }
+      }
+      if (o.alg == PLANC_BPP) {
+        // BPP solves the rows (one warp each, FP64 passive-set Cholesky); the
+        // cluster launch below then does the rest of the mode
+        NlsArgs a;
+        a.alg = PLANC_BPP;
+        a.opts = o.nls;
+        a.rows = ctx->dims[n];
+        a.R = R;
+        a.S = ctx->Sm;
+        a.M = ctx->Mbuf;
+        a.H = H[n];
+        a.lambda = ctx->lam;  // warm start H^(n) diag(lambda)
+        a.inner = inner_now + n;
+        a.reset_inner = false;
+        a.scratch = ctx->nls_scr;
+        a.flags = ctx->flags;
+        a.f64 = is_f64(ctx);
+        CK(launch_nls(a, ctx->stream), "NNLS launch");
       }
       // one launch: S^(n), NNLS, lambda, normalisation, G^(n) (+ error after
       // mode N, and then the history record unless an acceleration follows)

@@ -32,6 +32,10 @@ TC_CASES = [
     ((40, 96, 50), 16, 2),         # L / I_1 = 96, ragged last row tile
     ((16, 32, 7, 9), 32, 2),       # L / I_1 = 32, 4-way
     ((24, 160, 33), 64, 2),        # L / I_1 = 160, R = 64
+    # right branch with L / I_1 = 128 and R <= 16: BF16 X reduces two output
+    # rows per epilogue round (more items than CTAs, pairs and an odd last item)
+    ((32, 128, 400), 16, 2),
+    ((32, 128, 333), 12, 2),       # R = 12 padded to 16
 ]
 
 
