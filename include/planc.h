@@ -316,7 +316,7 @@ planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,
 /* ---- batched solve --------------------------------------------------------- */
 
 /* One 3-way instance of planc_batch_solve.  X: device, I_1 x I_2 x I_3, mode 1
- * fastest, F32 or BF16, borrowed.  H: three device F32 factors I_n x R
+ * fastest, F32 or BF16, starting on a 16-byte boundary, borrowed.  H: three device F32 factors I_n x R
  * row-major (in: initial factors, out: the solution, columns normalised as in
  * planc_nncp_solve).  lambda: host R doubles or NULL (out).  rel_err_hist:
  * host opts.iters doubles or NULL (out, eps per outer iteration). */
@@ -335,7 +335,9 @@ typedef struct {
  * error identity of Alg. 4) of `count` independent 3-way instances of
  * different sizes, all advanced together: each phase of an outer iteration
  * (left partial MTTKRP, multi-TTVs, right partial MTTKRP, the fused per-mode
- * update) is one launch over a work table of every instance's tiles, and with
+ * update) is one launch over a work table of every instance's tiles (the
+ * partial MTTKRPs as persistent grids, each CTA a contiguous run of tiles
+ * holding an equal share of the elements), and with
  * opts.use_graph the whole solve is one CUDA graph launch.  Tile shapes of the
  * partial-MTTKRP launches are chosen by timing candidates on the first call
  * for a batch of that size (cached per process).  Requirements: each I_n in

@@ -1,7 +1,9 @@
 // Batched kernels for many small 3-way instances solved together: every
-// launch covers all instances through a table of work items (instance, tile),
-// and each CTA walks a contiguous run of items so that per-instance staging
-// (a factor in shared memory) is redone only when the instance changes.
+// launch covers all instances through a table of work items (instance, tile).
+// The two partial MTTKRPs run as persistent grids: each CTA walks a
+// contiguous run of items holding an equal share of the elements (so that
+// per-instance staging, a factor in shared memory, is redone only when the
+// instance changes) and streams X through a ring of shared-memory stages.
 //
 // Per outer iteration (Alg. 1 with the dimension tree of Alg. 3, N = 3, S = 2):
 //   T^{1:2} = X_(1:2) H^(3)                 batch_pm_left   (first X pass)
@@ -20,7 +22,6 @@ namespace planc {
 namespace {
 
 constexpr int BR = 32;  // widest rank class of the batched kernels (R <= 32)
-constexpr int KU = 8;   // X loads a thread keeps in flight in the partial MTTKRPs
 
 // Rank blocking: an instance's partial MTTKRPs run with its rank padded to
 // the smallest class of the schedule that holds it (sched 0: 32; 1: 16, 32;
@@ -33,14 +34,7 @@ __device__ __forceinline__ int rank_class(int R, int sched) {
 
 __device__ __forceinline__ float ldx(const BatchInst& b, int64_t e) {
   if (b.xbf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(b.X)[e]);
-  return __ldg(reinterpret_cast<const float*>(b.X) + e);
-}
-
-// first and one-past-last item of this CTA's contiguous run
-__device__ __forceinline__ void item_run(int nitems, int& i0, int& i1) {
-  const int per = (nitems + gridDim.x - 1) / gridDim.x;
-  i0 = min(nitems, (int)blockIdx.x * per);
-  i1 = min(nitems, i0 + per);
+  return reinterpret_cast<const float*>(b.X)[e];
 }
 
 // rows f..f+nrow of a row-major nrow x R factor into shared memory with
@@ -114,130 +108,211 @@ batch_gram_kernel(const BatchInst* __restrict__ tab, int count) {
   }
 }
 
-// ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of 2 TL rows l) ----------
-// Each thread computes two adjacent rows l0, l0 + 1 (l0 even): both share
-// every read of H3's row k (staged in shared memory with stride BRC, the rank
-// class, read as broadcast 16-byte loads), and when L is even the two X
-// values arrive in one load (float2 / bf16x2).  KU k steps issue their X
-// loads together.
-template <bool BF16>
-__device__ __forceinline__ void ldx2(const void* X, int64_t e, bool pair, bool live0,
-                                     bool live1, float& a, float& b) {
-  if (BF16) {
-    const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(X) + e;
-    if (pair && live1) {
-      const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
-      a = __low2float(v);
-      b = __high2float(v);
+// ---- staged X: asynchronous 16-byte copies into a ring of shared-memory stages -----
+// The two partial MTTKRPs stream X through NSTG stages of SW words each: while
+// one stage is consumed, the copies of the next NSTG - 1 chunks are in flight
+// (the kernels are otherwise bound by the latency of their X loads).  A
+// contiguous byte range [byte0, byte1) of X is copied as the 16-byte-aligned
+// range that starts at or before it (X itself starts on 16 bytes), so any
+// dims and either storage type work: the range's first element sits `shift`
+// elements into the copy, and bytes at or past byte1 are zero-filled without
+// being read.
+constexpr int SW = 4096;  // 32-bit words per stage
+constexpr int NSTG = 2;   // stages (more gained nothing: the kernels are latency-bound in their FMA loop)
+
+__device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc, uint32_t nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sdst), "l"(gsrc), "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// bytes [byte0 & ~15, byte1) of X into shared memory at sdst (16-byte aligned)
+__device__ __forceinline__ void stage_range(uint32_t sdst, const char* xb, int64_t byte0,
+                                            int64_t byte1, int tid, int nt) {
+  const int64_t a0 = byte0 & ~(int64_t)15;
+  const char* src = xb + a0;
+  const int lim = (int)(byte1 - a0);  // at most one stage
+  for (int off = tid * 16; off < lim; off += nt * 16) {
+    const int left = lim - off;
+    cp_async16(sdst + (uint32_t)off, src + off, left >= 16 ? 16u : (uint32_t)left);
+  }
+}
+
+// This CTA's run of items: contiguous, with about 1 / gridDim.x of the total
+// work each (cumw: prefix sums of the items' element counts, nitems + 1 entries).
+__device__ __forceinline__ int64_t lower_bound64(const int64_t* a, int n, int64_t v) {
+  int lo = 0, hi = n;  // first index in [0, n) with a[i] >= v, else n
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ void work_run(const int64_t* cumw, int nitems, int& i0, int& i1) {
+  const int64_t W = cumw[nitems];
+  const int64_t s0 = W * blockIdx.x / gridDim.x, s1 = W * (blockIdx.x + 1) / gridDim.x;
+  i0 = (int)lower_bound64(cumw, nitems, s0);
+  i1 = blockIdx.x + 1 == gridDim.x ? nitems : (int)lower_bound64(cumw, nitems, s1);
+}
+
+// ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of 2 NT rows l) ------------
+// A chunk is KC columns k of the item's row block, each column a run of
+// 2 NT elements of X at stride L, copied into a slot of SB bytes.  Each thread
+// owns two adjacent rows and keeps both rows' R sums in registers across the
+// item's chunks; every read of H3's row k (staged in shared memory with stride
+// BRC, the rank class, as broadcast 16-byte loads) feeds both.
+template <int NT>
+struct LeftGeom {
+  static constexpr int RB = 2 * NT;
+  __device__ __forceinline__ static int sb(int es) { return RB * es + 16; }
+  __device__ __forceinline__ static int kc(int es) { return min(32, 4 * SW / sb(es)); }
+};
+
+template <int NT, int BRC, bool BF16>
+__device__ __forceinline__ void left_chunk(const unsigned char* stage, const float* hs, int64_t l0,
+                                           int64_t L, int k0, int nk, float* a0, float* a1) {
+  constexpr int ES = BF16 ? 2 : 4;
+  constexpr int SB = LeftGeom<NT>::RB * ES + 16;
+  const int t2 = 2 * (int)threadIdx.x;
+#pragma unroll 2
+  for (int kk = 0; kk < nk; ++kk) {
+    // first element of the column within its copy (X starts on 16 bytes)
+    const int sh = (int)((l0 + L * (k0 + kk)) & (16 / ES - 1));
+    float x0, x1;
+    if (BF16) {
+      const __nv_bfloat16* xs = reinterpret_cast<const __nv_bfloat16*>(stage + kk * SB) + sh + t2;
+      if ((sh & 1) == 0) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(xs);
+        x0 = __low2float(v);
+        x1 = __high2float(v);
+      } else {
+        x0 = __bfloat162float(xs[0]);
+        x1 = __bfloat162float(xs[1]);
+      }
     } else {
-      a = live0 ? __bfloat162float(p[0]) : 0.f;
-      b = live1 ? __bfloat162float(p[1]) : 0.f;
+      const float* xs = reinterpret_cast<const float*>(stage + kk * SB) + sh + t2;
+      if ((sh & 1) == 0) {
+        const float2 v = *reinterpret_cast<const float2*>(xs);
+        x0 = v.x;
+        x1 = v.y;
+      } else {
+        x0 = xs[0];
+        x1 = xs[1];
+      }
     }
-  } else {
-    const float* p = reinterpret_cast<const float*>(X) + e;
-    if (pair && live1) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-      a = v.x;
-      b = v.y;
-    } else {
-      a = live0 ? __ldg(p) : 0.f;
-      b = live1 ? __ldg(p + 1) : 0.f;
+    const float4* h = reinterpret_cast<const float4*>(hs + (k0 + kk) * BRC);
+#pragma unroll
+    for (int q = 0; q < BRC / 4; ++q) {
+      const float4 hv = h[q];
+      a0[4 * q + 0] = fmaf(x0, hv.x, a0[4 * q + 0]);
+      a0[4 * q + 1] = fmaf(x0, hv.y, a0[4 * q + 1]);
+      a0[4 * q + 2] = fmaf(x0, hv.z, a0[4 * q + 2]);
+      a0[4 * q + 3] = fmaf(x0, hv.w, a0[4 * q + 3]);
+      a1[4 * q + 0] = fmaf(x1, hv.x, a1[4 * q + 0]);
+      a1[4 * q + 1] = fmaf(x1, hv.y, a1[4 * q + 1]);
+      a1[4 * q + 2] = fmaf(x1, hv.z, a1[4 * q + 2]);
+      a1[4 * q + 3] = fmaf(x1, hv.w, a1[4 * q + 3]);
     }
   }
 }
 
-template <int BRC, bool BF16>
-__device__ __forceinline__ void left_rows2(const BatchInst& b, int64_t l0, int64_t L, int C,
-                                           int R, const float* bsm) {
-  const bool live0 = l0 < L, live1 = l0 + 1 < L;
-  // l0 even: X[l0 + L k] starts an aligned pair for every k when L is even
-  // and X itself is aligned to a pair
-  const bool pair = (L & 1) == 0 &&
-                    (reinterpret_cast<uintptr_t>(b.X) & (BF16 ? 3u : 7u)) == 0;
-  float a0[BRC], a1[BRC];
-#pragma unroll
-  for (int r = 0; r < BRC; ++r) { a0[r] = 0.f; a1[r] = 0.f; }
-  if (live0) {
-    int k = 0;
-    for (; k + KU <= C; k += KU) {
-      float x0[KU], x1[KU];
-#pragma unroll
-      for (int u = 0; u < KU; ++u) ldx2<BF16>(b.X, l0 + L * (k + u), pair, live0, live1, x0[u], x1[u]);
-#pragma unroll
-      for (int u = 0; u < KU; ++u) {
-        const float4* h = reinterpret_cast<const float4*>(bsm + (k + u) * BRC);
-#pragma unroll
-        for (int q = 0; q < BRC / 4; ++q) {
-          const float4 hv = h[q];
-          a0[4 * q + 0] = fmaf(x0[u], hv.x, a0[4 * q + 0]);
-          a0[4 * q + 1] = fmaf(x0[u], hv.y, a0[4 * q + 1]);
-          a0[4 * q + 2] = fmaf(x0[u], hv.z, a0[4 * q + 2]);
-          a0[4 * q + 3] = fmaf(x0[u], hv.w, a0[4 * q + 3]);
-          a1[4 * q + 0] = fmaf(x1[u], hv.x, a1[4 * q + 0]);
-          a1[4 * q + 1] = fmaf(x1[u], hv.y, a1[4 * q + 1]);
-          a1[4 * q + 2] = fmaf(x1[u], hv.z, a1[4 * q + 2]);
-          a1[4 * q + 3] = fmaf(x1[u], hv.w, a1[4 * q + 3]);
-        }
-      }
-    }
-    for (; k < C; ++k) {
-      float x0, x1;
-      ldx2<BF16>(b.X, l0 + L * k, pair, live0, live1, x0, x1);
-      const float4* h = reinterpret_cast<const float4*>(bsm + k * BRC);
-#pragma unroll
-      for (int q = 0; q < BRC / 4; ++q) {
-        const float4 hv = h[q];
-        a0[4 * q + 0] = fmaf(x0, hv.x, a0[4 * q + 0]);
-        a0[4 * q + 1] = fmaf(x0, hv.y, a0[4 * q + 1]);
-        a0[4 * q + 2] = fmaf(x0, hv.z, a0[4 * q + 2]);
-        a0[4 * q + 3] = fmaf(x0, hv.w, a0[4 * q + 3]);
-        a1[4 * q + 0] = fmaf(x1, hv.x, a1[4 * q + 0]);
-        a1[4 * q + 1] = fmaf(x1, hv.y, a1[4 * q + 1]);
-        a1[4 * q + 2] = fmaf(x1, hv.z, a1[4 * q + 2]);
-        a1[4 * q + 3] = fmaf(x1, hv.w, a1[4 * q + 3]);
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < BRC; ++r)
-    if (r < R) {
-      if (live0) b.T[l0 + L * r] = a0[r];
-      if (live1) b.T[l0 + 1 + L * r] = a1[r];
-    }
-}
-
-template <int BRC>
-__device__ __forceinline__ void left_rows2_dt(const BatchInst& b, int64_t l0, int64_t L, int C,
-                                              int R, const float* bsm) {
-  if (b.xbf16) left_rows2<BRC, true>(b, l0, L, C, R, bsm);
-  else left_rows2<BRC, false>(b, l0, L, C, R, bsm);
-}
-
-template <int TL>
-__global__ void __launch_bounds__(TL)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                     int nitems, int sched) {
-  extern __shared__ __align__(16) float bsm[];
+                     const int64_t* __restrict__ cumw, int nitems, int sched) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  using G = LeftGeom<NT>;
+  float* hs = reinterpret_cast<float*>(bsm + (size_t)NSTG * SW * 4);
+  const uint32_t stg = (uint32_t)__cvta_generic_to_shared(bsm);
+  const int tid = threadIdx.x;
   int i0, i1;
-  item_run(nitems, i0, i1);
-  int cur = -1;
-  for (int it = i0; it < i1; ++it) {
+  work_run(cumw, nitems, i0, i1);
+
+  int pit = i0, pk = 0;  // next chunk to copy: item, first column
+  auto issue = [&](int slot) {
+    if (pit < i1) {
+      const BatchInst& b = tab[items[pit].x];
+      const int64_t L = b.I[0] * b.I[1];
+      const int C = (int)b.I[2];
+      const int es = b.xbf16 ? 2 : 4;
+      const int64_t l0 = (int64_t)items[pit].y * G::RB;
+      const int64_t nb = (int64_t)es * min((int64_t)G::RB, L - l0);
+      const int sb = G::sb(es);
+      const int nk = min(G::kc(es), C - pk);
+      const char* xb = reinterpret_cast<const char*>(b.X);
+      for (int kk = 0; kk < nk; ++kk) {
+        const int64_t byte0 = (int64_t)es * (l0 + L * (pk + kk));
+        stage_range(stg + (uint32_t)(slot * SW * 4 + kk * sb), xb, byte0, byte0 + nb, tid, NT);
+      }
+      pk += nk;
+      if (pk >= C) {
+        ++pit;
+        pk = 0;
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < NSTG - 1; ++s) issue(s);
+
+  float a0[BR], a1[BR];
+  int cur = -1, ck = 0, cls = 32;
+  for (int it = i0, k = 0; it < i1; ++k) {
+    cp_async_wait<NSTG - 2>();
+    __syncthreads();  // chunk k visible; chunk k - 1 consumed by every thread
+    issue((k + NSTG - 1) % NSTG);
     const int bi = items[it].x;
     const BatchInst& b = tab[bi];
     const int64_t L = b.I[0] * b.I[1];
     const int C = (int)b.I[2], R = b.R;
-    const int cls = rank_class(R, sched);
-    if (bi != cur) {
-      __syncthreads();
-      stage_factor(bsm, b.H[2], C, R, cls);
-      __syncthreads();
-      cur = bi;
+    const bool bf = b.xbf16 != 0;
+    const int64_t l0 = (int64_t)items[it].y * G::RB;
+    const int nk = min(G::kc(bf ? 2 : 4), C - ck);
+    if (ck == 0) {
+      if (bi != cur) {  // H3 of a new instance (the old one is no longer read)
+        cls = rank_class(R, sched);
+        stage_factor(hs, b.H[2], C, R, cls);
+        __syncthreads();
+        cur = bi;
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        a0[r] = 0.f;
+        a1[r] = 0.f;
+      }
     }
-    const int64_t l0 = ((int64_t)items[it].y * TL + threadIdx.x) * 2;
-    if (cls == 8) left_rows2_dt<8>(b, l0, L, C, R, bsm);
-    else if (cls == 16) left_rows2_dt<16>(b, l0, L, C, R, bsm);
-    else left_rows2_dt<32>(b, l0, L, C, R, bsm);
+    const unsigned char* stage = bsm + (size_t)(k % NSTG) * SW * 4;
+    if (cls == 8) {
+      if (bf) left_chunk<NT, 8, true>(stage, hs, l0, L, ck, nk, a0, a1);
+      else left_chunk<NT, 8, false>(stage, hs, l0, L, ck, nk, a0, a1);
+    } else if (cls == 16) {
+      if (bf) left_chunk<NT, 16, true>(stage, hs, l0, L, ck, nk, a0, a1);
+      else left_chunk<NT, 16, false>(stage, hs, l0, L, ck, nk, a0, a1);
+    } else {
+      if (bf) left_chunk<NT, 32, true>(stage, hs, l0, L, ck, nk, a0, a1);
+      else left_chunk<NT, 32, false>(stage, hs, l0, L, ck, nk, a0, a1);
+    }
+    ck += nk;
+    if (ck >= C) {  // the item's rows are complete
+      const int64_t l = l0 + 2 * tid;
+      const bool live0 = l < L, live1 = l + 1 < L;
+      float* T = b.T;
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+        if (r < R) {
+          if (live0) T[l + L * r] = a0[r];
+          if (live1) T[l + 1 + L * r] = a1[r];
+        }
+      ++it;
+      ck = 0;
+    }
   }
+  cp_async_wait<0>();
 }
 
 // Sum over the warp of v[r] for r < 32, lane r returning the total of v[r].
@@ -256,143 +331,291 @@ __device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
 }
 
 // ---- M^(3)[c, r] = sum_{i1, i2} X[i1, i2, c] H1[i1, r] H2[i2, r]: items (b, c) ----------
-// Threads own (i1, range of i2); for each the inner sum over i2 runs with H2
-// from shared memory (stride BRC, the rank class) and is then weighted by
-// H1[i1, r]; the CTA's per-thread sums are reduced through warp
-// reduce-scatters and shared memory.
-template <int NT, int BRC>
-__device__ __forceinline__ void right_sums(const BatchInst& b, int64_t c, int I1, int I2,
-                                           int64_t L, int R, const float* bsm, float* acc) {
-  // units (i1, g): thread groups g = 0..ng-1 split the i2 range of each i1 so
-  // that short modes (I1 < NT) still occupy every thread; consecutive threads
-  // take consecutive i1 (coalesced X loads)
-  const int ng = max(1, NT / I1);
-  const int js = (I2 + ng - 1) / ng;  // i2 per group
-  for (int u = threadIdx.x; u < I1 * ng; u += NT) {
-    const int i = u % I1, g = u / I1;
-    const int ja = g * js, jb = min(I2, ja + js);
-    float in[BRC];
+// A chunk is KC columns i2 of the slab X[:, :, c] (one contiguous range).
+// Units (pair of rows i1, i1 + 1; group g) cover the slab, the groups
+// splitting each chunk's columns so that short first modes still occupy every
+// thread.  When the units fit the CTA (I1 <= 2 NT) each thread keeps its
+// unit's inner sums over i2 (H2 staged in shared memory, stride BRC) in
+// registers across the item's chunks and weights them by H1[i1, r] once, at
+// the item's end; longer first modes take one row per unit, looped over the
+// CTA in every chunk, and weight per chunk.  The CTA then reduces the
+// weighted sums (warp reduce-scatter, then shared memory).
+__device__ __forceinline__ int right_kc(int I1, int es) {
+  return max(1, (4 * SW - 16) / (es * I1));
+}
+
+template <bool BF16>
+__device__ __forceinline__ float ldstage(const unsigned char* stage, int q) {
+  if (BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(stage)[q]);
+  return reinterpret_cast<const float*>(stage)[q];
+}
+
+// inner sums of the unit (rows i, i + 1 when live1; columns jj = g, g + ng,
+// ... below nj of the chunk whose first column is j0) into in0, in1
+template <int BRC, bool BF16>
+__device__ __forceinline__ void right_sums(const unsigned char* stage, int sh, const float* hs,
+                                           int I1, int i, bool live1, int g, int ng, int j0,
+                                           int nj, float* in0, float* in1) {
+#pragma unroll 2
+  for (int jj = g; jj < nj; jj += ng) {
+    const int q = sh + jj * I1 + i;
+    const float x0 = ldstage<BF16>(stage, q);
+    const float x1 = live1 ? ldstage<BF16>(stage, q + 1) : 0.f;
+    const float4* h = reinterpret_cast<const float4*>(hs + (j0 + jj) * BRC);
 #pragma unroll
-    for (int r = 0; r < BRC; ++r) in[r] = 0.f;
-    const int64_t base = i + L * c;
-    int j = ja;
-    for (; j + KU <= jb; j += KU) {
-      float x[KU];
+    for (int qq = 0; qq < BRC / 4; ++qq) {
+      const float4 hv = h[qq];
+      in0[4 * qq + 0] = fmaf(x0, hv.x, in0[4 * qq + 0]);
+      in0[4 * qq + 1] = fmaf(x0, hv.y, in0[4 * qq + 1]);
+      in0[4 * qq + 2] = fmaf(x0, hv.z, in0[4 * qq + 2]);
+      in0[4 * qq + 3] = fmaf(x0, hv.w, in0[4 * qq + 3]);
+      in1[4 * qq + 0] = fmaf(x1, hv.x, in1[4 * qq + 0]);
+      in1[4 * qq + 1] = fmaf(x1, hv.y, in1[4 * qq + 1]);
+      in1[4 * qq + 2] = fmaf(x1, hv.z, in1[4 * qq + 2]);
+      in1[4 * qq + 3] = fmaf(x1, hv.w, in1[4 * qq + 3]);
+    }
+  }
+}
+
+// one row per unit (first modes longer than 2 NT): every row of the chunk,
+// weighted by H1[i, r] into acc
+template <int NT, int BRC, bool BF16>
+__device__ __forceinline__ void right_rows(const unsigned char* stage, int sh, const float* hs,
+                                           const float* __restrict__ H1, int I1, int R, int j0,
+                                           int nj, float* acc) {
+  for (int i = threadIdx.x; i < I1; i += NT) {
+    float t[BRC];
 #pragma unroll
-      for (int v = 0; v < KU; ++v) x[v] = ldx(b, base + (int64_t)I1 * (j + v));
+    for (int r = 0; r < BRC; ++r) t[r] = 0.f;
+#pragma unroll 2
+    for (int jj = 0; jj < nj; ++jj) {
+      const float x = ldstage<BF16>(stage, sh + jj * I1 + i);
+      const float4* h = reinterpret_cast<const float4*>(hs + (j0 + jj) * BRC);
 #pragma unroll
-      for (int v = 0; v < KU; ++v) {
-        const float4* h = reinterpret_cast<const float4*>(bsm + (j + v) * BRC);
-#pragma unroll
-        for (int q = 0; q < BRC / 4; ++q) {
-          const float4 hv = h[q];
-          in[4 * q + 0] = fmaf(x[v], hv.x, in[4 * q + 0]);
-          in[4 * q + 1] = fmaf(x[v], hv.y, in[4 * q + 1]);
-          in[4 * q + 2] = fmaf(x[v], hv.z, in[4 * q + 2]);
-          in[4 * q + 3] = fmaf(x[v], hv.w, in[4 * q + 3]);
-        }
+      for (int qq = 0; qq < BRC / 4; ++qq) {
+        const float4 hv = h[qq];
+        t[4 * qq + 0] = fmaf(x, hv.x, t[4 * qq + 0]);
+        t[4 * qq + 1] = fmaf(x, hv.y, t[4 * qq + 1]);
+        t[4 * qq + 2] = fmaf(x, hv.z, t[4 * qq + 2]);
+        t[4 * qq + 3] = fmaf(x, hv.w, t[4 * qq + 3]);
       }
     }
-    for (; j < jb; ++j) {
-      const float x = ldx(b, base + (int64_t)I1 * j);
-      const float4* h = reinterpret_cast<const float4*>(bsm + j * BRC);
-#pragma unroll
-      for (int q = 0; q < BRC / 4; ++q) {
-        const float4 hv = h[q];
-        in[4 * q + 0] = fmaf(x, hv.x, in[4 * q + 0]);
-        in[4 * q + 1] = fmaf(x, hv.y, in[4 * q + 1]);
-        in[4 * q + 2] = fmaf(x, hv.z, in[4 * q + 2]);
-        in[4 * q + 3] = fmaf(x, hv.w, in[4 * q + 3]);
-      }
-    }
-    const float* h1 = b.H[0] + (int64_t)i * R;
+    const float* h1 = H1 + (int64_t)i * R;
 #pragma unroll
     for (int r = 0; r < BRC; ++r)
-      if (r < R) acc[r] = fmaf(in[r], __ldg(h1 + r), acc[r]);
+      if (r < R) acc[r] = fmaf(t[r], h1[r], acc[r]);
+  }
+}
+
+// one chunk of the item: the unit's sums (persistent units) or the rows'
+// weighted sums (long first modes)
+template <int NT, int BRC, bool BF16>
+__device__ __forceinline__ void right_chunk(const unsigned char* stage, int sh, const float* hs,
+                                            const float* __restrict__ H1, int I1, int R, int j0,
+                                            int nj, float* in0, float* in1) {
+  const int P = (I1 + 1) >> 1;
+  if (P <= NT) {
+    const int ng = NT / P;
+    const int u = threadIdx.x;
+    if (u < P * ng) {
+      const int i = 2 * (u % P);
+      right_sums<BRC, BF16>(stage, sh, hs, I1, i, i + 1 < I1, u / P, ng, j0, nj, in0, in1);
+    }
+  } else {
+    right_rows<NT, BRC, BF16>(stage, sh, hs, H1, I1, R, j0, nj, in0);
   }
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT)
 batch_pm_right_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                      int nitems, int sched) {
-  extern __shared__ __align__(16) float bsm[];
+                      const int64_t* __restrict__ cumw, int nitems, int sched) {
+  extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ float red[NT / 32][BR];
+  float* hs = reinterpret_cast<float*>(bsm + (size_t)NSTG * SW * 4);
+  const uint32_t stg = (uint32_t)__cvta_generic_to_shared(bsm);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int i0, i1;
-  item_run(nitems, i0, i1);
-  int cur = -1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int it = i0; it < i1; ++it) {
+  work_run(cumw, nitems, i0, i1);
+
+  int pit = i0, pj = 0;  // next chunk to copy: item, first column i2
+  auto issue = [&](int slot) {
+    if (pit < i1) {
+      const BatchInst& b = tab[items[pit].x];
+      const int I1 = (int)b.I[0], I2 = (int)b.I[1];
+      const int64_t L = (int64_t)I1 * I2;
+      const int es = b.xbf16 ? 2 : 4;
+      const int nj = min(right_kc(I1, es), I2 - pj);
+      const int64_t byte0 = (int64_t)es * (L * items[pit].y + (int64_t)I1 * pj);
+      stage_range(stg + (uint32_t)(slot * SW * 4), reinterpret_cast<const char*>(b.X), byte0,
+                  byte0 + (int64_t)es * I1 * nj, tid, NT);
+      pj += nj;
+      if (pj >= I2) {
+        ++pit;
+        pj = 0;
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < NSTG - 1; ++s) issue(s);
+
+  // persistent units: the unit's row sums; long first modes: the thread's
+  // weighted sums (in0) only
+  float in0[BR], in1[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+    in0[r] = 0.f;
+    in1[r] = 0.f;
+  }
+  int cur = -1, cj = 0, cls = 32;
+  for (int it = i0, k = 0; it < i1; ++k) {
+    cp_async_wait<NSTG - 2>();
+    __syncthreads();  // chunk k visible; chunk k - 1 consumed by every thread
+    issue((k + NSTG - 1) % NSTG);
     const int bi = items[it].x;
     const BatchInst& b = tab[bi];
     const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
     const int64_t L = (int64_t)I1 * I2;
-    const int64_t c = items[it].y;
-    const int cls = rank_class(R, sched);
-    if (bi != cur) {
-      __syncthreads();
-      stage_factor(bsm, b.H[1], I2, R, cls);
+    const bool bf = b.xbf16 != 0;
+    const int es = bf ? 2 : 4;
+    const int nj = min(right_kc(I1, es), I2 - cj);
+    if (cj == 0 && bi != cur) {  // H2 of a new instance (the old one is no longer read)
+      cls = rank_class(R, sched);
+      stage_factor(hs, b.H[1], I2, R, cls);
       __syncthreads();
       cur = bi;
     }
-    float acc[BR];
-#pragma unroll
-    for (int r = 0; r < BR; ++r) acc[r] = 0.f;
-    if (cls == 8) right_sums<NT, 8>(b, c, I1, I2, L, R, bsm, acc);
-    else if (cls == 16) right_sums<NT, 16>(b, c, I1, I2, L, R, bsm, acc);
-    else right_sums<NT, 32>(b, c, I1, I2, L, R, bsm, acc);
-    const float v = reduce_scatter32(acc, lane);
-    red[warp][lane] = v;
-    __syncthreads();
-    if (threadIdx.x < R) {
-      float s = 0.f;
-#pragma unroll
-      for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-      b.M[c * R + threadIdx.x] = s;
+    // the chunk's first element within its copy (X starts on 16 bytes)
+    const int sh = (int)((L * items[it].y + (int64_t)I1 * cj) & (16 / es - 1));
+    const unsigned char* stage = bsm + (size_t)(k % NSTG) * SW * 4;
+    if (cls == 8) {
+      if (bf) right_chunk<NT, 8, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 8, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+    } else if (cls == 16) {
+      if (bf) right_chunk<NT, 16, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 16, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+    } else {
+      if (bf) right_chunk<NT, 32, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 32, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
     }
-    __syncthreads();
+    cj += nj;
+    if (cj >= I2) {  // the item's sums are complete
+      const int P = (I1 + 1) >> 1;
+      if (P <= NT) {  // weight the unit's sums by H1 (once per item)
+        const int ng = NT / P;
+        const int i = 2 * (tid % P);
+        const bool live = tid < P * ng, live1 = live && i + 1 < I1;
+        const float* h1 = b.H[0] + (int64_t)i * R;
+#pragma unroll
+        for (int r = 0; r < BR; ++r) {
+          float v = 0.f;
+          if (live && r < R) v = in0[r] * h1[r];
+          if (live1 && r < R) v = fmaf(in1[r], h1[R + r], v);
+          in0[r] = v;
+        }
+      }
+      const float v = reduce_scatter32(in0, lane);
+      red[warp][lane] = v;
+      __syncthreads();
+      if (tid < R) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) sum += red[w][tid];
+        b.M[(int64_t)items[it].y * R + tid] = sum;
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        in0[r] = 0.f;
+        in1[r] = 0.f;
+      }
+      ++it;
+      cj = 0;
+    }
   }
+  cp_async_wait<0>();
 }
 
 // ---- M^(1)[i1, r] = sum_{i2} T[i1 + I1 i2, r] H2[i2, r]: items (b, r) -----------------
-__global__ void __launch_bounds__(128)
+// Units (i1, group of i2): groups split the i2 range when I1 is short; the
+// column H2[:, r] is staged in shared memory; eight loads in flight per unit.
+constexpr int CT = 256;  // threads of the contraction kernels
+
+__global__ void __launch_bounds__(CT)
 batch_contract_rest_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
                            int nitems) {
+  __shared__ float hcol[1024];
+  __shared__ float part[CT];
+  const int tid = threadIdx.x;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BatchInst& b = tab[items[it].x];
     const int r = items[it].y;
     const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
     const float* Tr = b.T + (int64_t)I1 * I2 * r;
-    for (int i = threadIdx.x; i < I1; i += blockDim.x) {
-      float a0 = 0.f, a1 = 0.f;
-      int j = 0;
-      for (; j + 2 <= I2; j += 2) {
-        a0 = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[1] + (int64_t)j * R + r), a0);
-        a1 = fmaf(Tr[i + (int64_t)I1 * (j + 1)], __ldg(b.H[1] + (int64_t)(j + 1) * R + r), a1);
+    __syncthreads();  // the previous item's reads of hcol and part are done
+    for (int j = tid; j < I2; j += CT) hcol[j] = b.H[1][(int64_t)j * R + r];
+    __syncthreads();
+    const int ng = I1 >= CT ? 1 : CT / I1;
+    const int js = (I2 + ng - 1) / ng;
+    for (int u = tid; u < I1 * ng; u += CT) {
+      const int i = u % I1, g = u / I1;
+      const int ja = g * js, jb = min(I2, ja + js);
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
+      int j = ja;
+      for (; j + 8 <= jb; j += 8) {
+        float x[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) x[v] = Tr[i + (int64_t)I1 * (j + v)];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) a[v & 3] = fmaf(x[v], hcol[j + v], a[v & 3]);
       }
-      if (j < I2) a0 = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[1] + (int64_t)j * R + r), a0);
-      b.M[(int64_t)i * R + r] = a0 + a1;
+      for (; j < jb; ++j) a[0] = fmaf(Tr[i + (int64_t)I1 * j], hcol[j], a[0]);
+      const float s = (a[0] + a[1]) + (a[2] + a[3]);
+      if (ng == 1) b.M[(int64_t)i * R + r] = s;
+      else part[u] = s;
+    }
+    if (ng > 1) {
+      __syncthreads();
+      for (int i = tid; i < I1; i += CT) {
+        float s = 0.f;
+        for (int g = 0; g < ng; ++g) s += part[i + I1 * g];
+        b.M[(int64_t)i * R + r] = s;
+      }
     }
   }
 }
 
 // ---- M^(2)[i2, r] = sum_{i1} T[i1 + I1 i2, r] H1[i1, r]: items (b, r) -----------------
-// one warp per i2, lanes across i1
-__global__ void __launch_bounds__(128)
+// a warp per four i2 (lanes across i1, four columns' loads in flight
+// together); the column H1[:, r] is staged in shared memory
+__global__ void __launch_bounds__(CT)
 batch_contract_first_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
                             int nitems) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float hcol[1024];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = CT / 32;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BatchInst& b = tab[items[it].x];
     const int r = items[it].y;
     const int I1 = (int)b.I[0], I2 = (int)b.I[1], R = b.R;
     const float* Tr = b.T + (int64_t)I1 * I2 * r;
-    for (int j = warp; j < I2; j += blockDim.x / 32) {
-      float a = 0.f;
-      for (int i = lane; i < I1; i += 32)
-        a = fmaf(Tr[i + (int64_t)I1 * j], __ldg(b.H[0] + (int64_t)i * R + r), a);
-      a = warp_sum(a);
-      if (lane == 0) b.M[(int64_t)j * R + r] = a;
+    __syncthreads();  // the previous item's reads of hcol are done
+    for (int i = tid; i < I1; i += CT) hcol[i] = b.H[0][(int64_t)i * R + r];
+    __syncthreads();
+    for (int j0 = 4 * warp; j0 < I2; j0 += 4 * NW) {
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = lane; i < I1; i += 32) {
+        const float h = hcol[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j0 + q < I2) a[q] = fmaf(Tr[i + (int64_t)I1 * (j0 + q)], h, a[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = warp_sum(a[q]);
+      if (lane < 4 && j0 + lane < I2) {
+        const float v = lane == 0 ? a[0] : lane == 1 ? a[1] : lane == 2 ? a[2] : a[3];
+        b.M[(int64_t)(j0 + lane) * R + r] = v;
+      }
     }
   }
 }
@@ -413,65 +636,65 @@ cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// tl: threads per item (64, 128 or 256; two rows each); smem_floats: max C x 32 over the batch;
-// sched: rank-class schedule (see rank_class)
-cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
-                                 int grid, size_t smem_floats, int sched, cudaStream_t st) {
-  const size_t smem = smem_floats * sizeof(float);
-  cudaError_t e = cudaSuccess;
-  switch (tl) {
-    case 64:
-      e = cudaFuncSetAttribute(batch_pm_left_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems, sched);
-      break;
-    case 128:
-      e = cudaFuncSetAttribute(batch_pm_left_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems, sched);
-      break;
-    case 256:
-      e = cudaFuncSetAttribute(batch_pm_left_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_left_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems, sched);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+size_t batch_pm_smem(int hmax) { return (size_t)NSTG * SW * 4 + (size_t)hmax * BR * 4; }
+
+namespace {
+// a persistent grid: as many CTAs as fit on the device at once (at least one
+// per SM), each walking its balanced run of items
+template <typename K>
+cudaError_t launch_staged(K kern, int nt, size_t smem, int sm_count, const BatchInst* tab,
+                          const int2* items, const int64_t* cumw, int nitems, int sched,
+                          cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the whole unified L1 as shared memory, so that every CTA of the grid is
+  // resident at once (the default carveout may hold fewer)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sm_count));
+  kern<<<grid, nt, smem, st>>>(tab, items, cumw, nitems, sched);
   note_launches(1);
   return cudaGetLastError();
 }
+}  // namespace
 
-// nt: threads per item (64, 128 or 256); smem_floats: max I2 x 32 over the batch;
-// sched: rank-class schedule (see rank_class)
-cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
-                                  int grid, size_t smem_floats, int sched, cudaStream_t st) {
-  const size_t smem = smem_floats * sizeof(float);
-  cudaError_t e = cudaSuccess;
-  switch (nt) {
-    case 64:
-      e = cudaFuncSetAttribute(batch_pm_right_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<64><<<grid, 64, smem, st>>>(tab, items, nitems, sched);
-      break;
-    case 128:
-      e = cudaFuncSetAttribute(batch_pm_right_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<128><<<grid, 128, smem, st>>>(tab, items, nitems, sched);
-      break;
-    case 256:
-      e = cudaFuncSetAttribute(batch_pm_right_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) batch_pm_right_kernel<256><<<grid, 256, smem, st>>>(tab, items, nitems, sched);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+// tl: threads per CTA (64, 128 or 256; two rows each); hmax: longest third
+// mode of the batch; sched: rank-class schedule (see rank_class)
+cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, const int64_t* cumw,
+                                 int nitems, int tl, int hmax, int sched, int sm_count,
+                                 cudaStream_t st) {
+  const size_t smem = batch_pm_smem(hmax);
+  switch (tl) {
+    case 64: return launch_staged(batch_pm_left_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 128: return launch_staged(batch_pm_left_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 256: return launch_staged(batch_pm_left_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    default: return cudaErrorInvalidValue;
   }
-  if (e != cudaSuccess) return e;
-  note_launches(1);
-  return cudaGetLastError();
+}
+
+// nt: threads per CTA (64, 128 or 256); hmax: longest second mode of the
+// batch; sched: rank-class schedule (see rank_class)
+cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, const int64_t* cumw,
+                                  int nitems, int nt, int hmax, int sched, int sm_count,
+                                  cudaStream_t st) {
+  const size_t smem = batch_pm_smem(hmax);
+  switch (nt) {
+    case 64: return launch_staged(batch_pm_right_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 128: return launch_staged(batch_pm_right_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 256: return launch_staged(batch_pm_right_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
                                   int sm_count, cudaStream_t st) {
-  const int grid = std::min(nitems, 16 * sm_count);
-  if (rest) batch_contract_rest_kernel<<<grid, 128, 0, st>>>(tab, items, nitems);
-  else batch_contract_first_kernel<<<grid, 128, 0, st>>>(tab, items, nitems);
+  const int grid = std::min(nitems, 8 * sm_count);
+  if (rest) batch_contract_rest_kernel<<<grid, CT, 0, st>>>(tab, items, nitems);
+  else batch_contract_first_kernel<<<grid, CT, 0, st>>>(tab, items, nitems);
   note_launches(1);
   return cudaGetLastError();
 }

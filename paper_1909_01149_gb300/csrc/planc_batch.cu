@@ -24,10 +24,13 @@ namespace planc {
 cudaError_t launch_batch_sqnorm(const BatchInst* tab, int count, const int2* items, int nitems,
                                 const int* first, double* part, int sm_count, cudaStream_t st);
 cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st);
-cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, int nitems, int tl,
-                                 int grid, size_t smem_floats, int sched, cudaStream_t st);
-cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, int nitems, int nt,
-                                  int grid, size_t smem_floats, int sched, cudaStream_t st);
+cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, const int64_t* cumw,
+                                 int nitems, int tl, int hmax, int sched, int sm_count,
+                                 cudaStream_t st);
+cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, const int64_t* cumw,
+                                  int nitems, int nt, int hmax, int sched, int sm_count,
+                                  cudaStream_t st);
+size_t batch_pm_smem(int hmax);
 cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
                                   int sm_count, cudaStream_t st);
 
@@ -95,6 +98,8 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
       if (in.dims[n] < 1 || in.dims[n] > maxrows) return bfail(PLANC_E_SHAPE, "dims must be 1..1024");
     if (in.x_dtype != PLANC_F32 && in.x_dtype != PLANC_BF16)
       return bfail(PLANC_E_DTYPE, "X must be F32 or BF16");
+    if (reinterpret_cast<uintptr_t>(in.X) & 15u)
+      return bfail(PLANC_E_INVALID, "X must start on a 16-byte boundary");
     maxC = std::max(maxC, in.dims[2]);
     maxI2 = std::max(maxI2, in.dims[1]);
   }
@@ -152,22 +157,38 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   for (int b : by_rank)
     for (int64_t c = 0; c < inst[b].dims[2]; ++c) right_items.push_back(make_int2(b, (int)c));
   sq_first[count] = (int)sq_items.size();
+  // prefix sums of the items' element counts: each CTA of the partial
+  // MTTKRPs takes a contiguous run with an equal share of the elements
+  std::vector<int64_t> right_cum(1, 0);
+  for (int b : by_rank)
+    for (int64_t c = 0; c < inst[b].dims[2]; ++c)
+      right_cum.push_back(right_cum.back() + inst[b].dims[0] * inst[b].dims[1]);
   std::vector<int2> left_items[3];
-  for (int t = 0; t < 3; ++t)
+  std::vector<int64_t> left_cum[3];
+  for (int t = 0; t < 3; ++t) {
+    left_cum[t].push_back(0);
     for (int b : by_rank) {
       const int64_t L = inst[b].dims[0] * inst[b].dims[1];
-      for (int64_t y = 0; y * 2 * kTL[t] < L; ++y) left_items[t].push_back(make_int2(b, (int)y));
+      for (int64_t y = 0; y * 2 * kTL[t] < L; ++y) {
+        left_items[t].push_back(make_int2(b, (int)y));
+        const int64_t rows = std::min<int64_t>(2 * kTL[t], L - y * 2 * kTL[t]);
+        left_cum[t].push_back(left_cum[t].back() + rows * inst[b].dims[2]);
+      }
     }
+  }
   const size_t off_tab = bytes; bytes += align256(sizeof(BatchInst) * count);
   const size_t off_sq = bytes; bytes += align256(sizeof(int2) * sq_items.size());
   const size_t off_sqf = bytes; bytes += align256(sizeof(int) * (count + 1));
   const size_t off_sqp = bytes; bytes += align256(sizeof(double) * sq_items.size());
   const size_t off_right = bytes; bytes += align256(sizeof(int2) * right_items.size());
   const size_t off_rc = bytes; bytes += align256(sizeof(int2) * rc_items.size());
-  size_t off_left[3];
+  const size_t off_rcum = bytes; bytes += align256(sizeof(int64_t) * right_cum.size());
+  size_t off_left[3], off_lcum[3];
   for (int t = 0; t < 3; ++t) {
     off_left[t] = bytes;
     bytes += align256(sizeof(int2) * left_items[t].size());
+    off_lcum[t] = bytes;
+    bytes += align256(sizeof(int64_t) * left_cum[t].size());
   }
   const size_t off_err = bytes; bytes += 256;
 
@@ -212,22 +233,24 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
       h2d(off_sqf, sq_first.data(), sizeof(int) * (count + 1)) != cudaSuccess ||
       h2d(off_right, right_items.data(), sizeof(int2) * right_items.size()) != cudaSuccess ||
       h2d(off_rc, rc_items.data(), sizeof(int2) * rc_items.size()) != cudaSuccess ||
+      h2d(off_rcum, right_cum.data(), sizeof(int64_t) * right_cum.size()) != cudaSuccess ||
       cudaMemsetAsync(base + off_err, 0, 256, st) != cudaSuccess)
     return bfail(PLANC_E_CUDA, "table upload failed");
   for (int t = 0; t < 3; ++t)
-    if (h2d(off_left[t], left_items[t].data(), sizeof(int2) * left_items[t].size()) != cudaSuccess)
+    if (h2d(off_left[t], left_items[t].data(), sizeof(int2) * left_items[t].size()) != cudaSuccess ||
+        h2d(off_lcum[t], left_cum[t].data(), sizeof(int64_t) * left_cum[t].size()) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "table upload failed");
   for (int b = 0; b < count; ++b)
     if (cudaMemsetAsync(base + offHist[b], 0, (size_t)iters * 3 * 8, st) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "memset failed");
 
-  const size_t smem_left = (size_t)maxC * 32, smem_right = (size_t)maxI2 * 32;
-  if (smem_left * 4 > 200 * 1024 || smem_right * 4 > 200 * 1024)
+  const int hmax_left = (int)maxC, hmax_right = (int)maxI2;
+  if (batch_pm_smem(std::max(hmax_left, hmax_right)) > 227 * 1024)
     return bfail(PLANC_E_SHAPE, "a mode is too long for the staged factor");
+  const int64_t* d_rcum = reinterpret_cast<const int64_t*>(base + off_rcum);
   const int nleft[3] = {(int)left_items[0].size(), (int)left_items[1].size(),
                         (int)left_items[2].size()};
   const int nright = (int)right_items.size(), nrc = (int)rc_items.size();
-  auto grid_of = [&](int nitems) { return std::max(1, std::min(nitems, 8 * sms)); };
 
   // ---- schedule: every (tile, rank blocking) candidate of each partial
   // MTTKRP timed on this batch (second of two runs), cached per batch
@@ -273,13 +296,14 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     for (int t = 0; t < 3; ++t)
       for (int sc = 0; sc < kSchedules; ++sc) {
         const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
+        const int64_t* lcum = reinterpret_cast<const int64_t*>(base + off_lcum[t]);
         float ms = 0.f;
-        if (!time_it([&] { return launch_batch_pm_left(d_tab, items, nleft[t], kTL[t],
-                                                       grid_of(nleft[t]), smem_left, sc, st); }, ms))
+        if (!time_it([&] { return launch_batch_pm_left(d_tab, items, lcum, nleft[t], kTL[t],
+                                                       hmax_left, sc, sms, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
         if (ms < best_l) { best_l = ms; ch.tl = t; ch.sched_left = sc; }
-        if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, nright, kNT[t],
-                                                        grid_of(nright), smem_right, sc, st); }, ms))
+        if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, d_rcum, nright, kNT[t],
+                                                        hmax_right, sc, sms, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
         if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
       }
@@ -299,6 +323,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   t_last_choice = ch;
   const int tl_idx = ch.tl;
   const int2* d_left = reinterpret_cast<const int2*>(base + off_left[tl_idx]);
+  const int64_t* d_lcum = reinterpret_cast<const int64_t*>(base + off_lcum[tl_idx]);
   const int tl = kTL[tl_idx], nt = kNT[ch.nt];
 
   const long long c_start = launch_count();
@@ -308,12 +333,12 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     if ((e = launch_batch_sqnorm(d_tab, count, d_sq, (int)sq_items.size(), d_sqf, d_sqp, sms, st)) != cudaSuccess) return e;
     if ((e = launch_batch_gram(d_tab, count, st)) != cudaSuccess) return e;
     for (int it = 0; it < iters; ++it) {
-      if ((e = launch_batch_pm_left(d_tab, d_left, nleft[tl_idx], tl, grid_of(nleft[tl_idx]), smem_left, ch.sched_left, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_left(d_tab, d_left, d_lcum, nleft[tl_idx], tl, hmax_left, ch.sched_left, sms, st)) != cudaSuccess) return e;
       if ((e = launch_batch_contract(d_tab, d_rc, nrc, true, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 0, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
       if ((e = launch_batch_contract(d_tab, d_rc, nrc, false, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 1, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
-      if ((e = launch_batch_pm_right(d_tab, d_right, nright, nt, grid_of(nright), smem_right, ch.sched_right, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_right(d_tab, d_right, d_rcum, nright, nt, hmax_right, ch.sched_right, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 2, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;

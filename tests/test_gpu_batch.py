@@ -106,6 +106,25 @@ def test_batch_edge_sizes():
         np.testing.assert_allclose(res[b]["rel_err"], ref["rel_err"], rtol=0, atol=1e-4)
 
 
+def test_batch_bf16_edge_sizes():
+    """BF16 storage with odd mode lengths (chunks that start in the middle of
+    a 32-bit word), a 1023-row first mode, one-row modes and R = 32."""
+    p = planc()
+    shapes = [((1023, 3, 5), 3), ((7, 9, 11), 5), ((1, 5, 3), 2), ((33, 1, 7), 32),
+              ((5, 7, 1), 1)]
+    Xd, Xs, H0 = [], [], []
+    for i, (dims, R) in enumerate(shapes):
+        X, _ = synth.planted(dims, R, 90 + i, noise=0.02, dtype=np.float32)
+        xd, xs = x_to_device(X, "bf16")
+        Xd.append(xd)
+        Xs.append(xs)
+        H0.append(synth.init_factors(dims, R, 95 + i))
+    res, _ = p.batch_solve(Xd, _dev(H0), "hals", 5)
+    for b, (xs, h0) in enumerate(zip(Xs, _host(H0))):
+        ref = o.nncp(xs, h0, "hals", iters=5)
+        np.testing.assert_allclose(res[b]["rel_err"], ref["rel_err"], rtol=0, atol=1e-4)
+
+
 def test_batch_rejects_bad_input():
     p = planc()
     X = torch.rand(4 * 5 * 6, device="cuda")
@@ -117,6 +136,10 @@ def test_batch_rejects_bad_input():
         p.batch_solve([X], [big], "hals", 2)
     with pytest.raises(ValueError):
         p.batch_solve([X], [good[:2]], "hals", 2)
+    # X must start on a 16-byte boundary (the partial MTTKRPs copy it in 16-byte pieces)
+    Xb = torch.rand(4 * 5 * 6 + 4, device="cuda")[1:1 + 4 * 5 * 6]
+    with pytest.raises(p.PlancError):
+        p.batch_solve([Xb], [good], "hals", 2)
 
 
 def test_batch_rank_blocking_schedules_agree(monkeypatch):
