@@ -144,9 +144,12 @@ def measured_peak():
 
 
 def pm_source_sha(use_tc):
-    f = "kern_pm_tc.cu" if use_tc else "kern_pm_simt.cu"
-    data = open(os.path.join(ROOT, "paper_1909_01149_gb300", "csrc", f), "rb").read()
-    return hashlib.sha256(data).hexdigest()[:16]
+    """Hash of the partial-MTTKRP kernel sources (tensor-core: both files)."""
+    files = ["kern_pm_tc.cu", "kern_pm_krp.cu"] if use_tc else ["kern_pm_simt.cu"]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1909_01149_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(workload, sha):

@@ -1695,6 +1695,10 @@ TcrPlan tcr_plan(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, cons
 
 }  // namespace
 
+// the driver's tensor-map encoder (NULL if the driver lacks it), for the other
+// tensor-core kernels
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                     const KrpHost& kh) {
   if (xdt != PLANC_BF16 && xdt != PLANC_F32) return false;
@@ -1712,6 +1716,7 @@ bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
 size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                              const KrpHost& kh, int sm_count) {
   if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return 0;
+  if (pm_krp_eligible(xdt, left, L, C, R, kh)) return pm_krp_workspace_bytes(L, C, R, sm_count);
   const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
   if (pl.ok) {
     if (pl.blockmode) return (size_t)pl.nblocks * R * sizeof(float);
@@ -1851,6 +1856,10 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
                          const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
                          size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st) {
   if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return cudaErrorNotSupported;
+  if (pm_krp_eligible(xdt, left, L, C, R, kh) &&
+      work_bytes >= pm_krp_workspace_bytes(L, C, R, sm_count))
+    return launch_pm_krp(X, L, C, kh, R, out, out_rowmajor, work, work_bytes, err_flag, sm_count,
+                         st);
   {
     const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
     if (pl.ok && getenv("PLANC_TC_STREAMED_KRP") == nullptr)

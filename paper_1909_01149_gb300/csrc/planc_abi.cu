@@ -937,7 +937,7 @@ planc_status_t planc_nncp_solve(planc_t ctx, const planc_solve_opts* opts, void*
   }
   if (tc_err != 0)
     return fail(ctx, PLANC_E_TIMEOUT,
-                "a pipeline wait gave up (code %d: 1-3 partial MTTKRP, 10 mode update)", tc_err);
+                "a pipeline wait gave up (code %d: 1-3, 21-31, 41-45 partial MTTKRP, 10 mode update)", tc_err);
   if (flags[1] != 0)
     return fail(ctx, PLANC_E_NUMERIC, "S is not positive definite: %d inversion(s) met a non-positive pivot", flags[1]);
   return PLANC_OK;

@@ -36,6 +36,11 @@ TC_CASES = [
     # rows per epilogue round (more items than CTAs, pairs and an odd last item)
     ((32, 128, 400), 16, 2),
     ((32, 128, 333), 12, 2),       # R = 12 padded to 16
+    # BF16 right branch as one GEMM against the split Khatri-Rao image:
+    # R = 1, R = 17 (padded to 32), a single row tile with fewer units than SMs
+    ((24, 40, 130), 1, 2),
+    ((16, 24, 200), 17, 2),
+    ((8, 8, 9, 3), 32, 2),
 ]
 
 
@@ -123,3 +128,24 @@ def test_tc_solve_matches_cuda_core_solve(monkeypatch):
             assert (ctx.tc_mask != 0) == (path == "auto")
             out.append(ctx.solve(Hd, "bpp", 8)["rel_err"])
     np.testing.assert_allclose(out[0], out[1], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("dims,R,split", [((64, 48, 80), 16, -1), ((16, 24, 200), 17, 2),
+                                          ((32, 128, 400), 16, 2), ((128, 8, 97, 5), 32, 2)])
+def test_bf16_right_branch_gemm_matches_weighted_rows(dims, R, split, monkeypatch):
+    """The BF16 right branch as one GEMM against the split Khatri-Rao image
+    and the weighted-row kernel (PLANC_PM_KRP=0) agree, and both match the
+    oracle to 1e-5 per entry."""
+    p = planc()
+    Xd, Xs, Hd, Hs = _ctx_and_refs(dims, R, split, "bf16", seed=3)
+    outs = []
+    for krp in ("1", "0"):
+        monkeypatch.setenv("PLANC_PM_KRP", krp)
+        with p.Context(Xd, dims, R, split) as ctx:
+            assert ctx.tc_mask == 3
+            outs.append(ctx.partial_mttkrp(Hd, 1).double().cpu().numpy())
+            n = len(dims) - 1
+            M = ctx.mttkrp(Hd, n).double().cpu().numpy()
+            assert max_rel(M, o.mttkrp(Xs, Hs, n)) <= 1e-5
+    assert max_rel(outs[0], outs[1]) <= 2e-6
+
