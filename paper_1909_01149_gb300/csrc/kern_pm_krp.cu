@@ -1,19 +1,21 @@
-// Right-branch partial MTTKRP for BF16 X as one tcgen05 GEMM (Alg. 3, the
-// partial MTTKRP T^{S+1:N} = X_(1:S)^T K^{1:S} of the right root branch):
+// The partial MTTKRPs of both root branches for BF16 X as one tcgen05 GEMM
+// each (Alg. 3: T^{1:S} = X_(1:S) K^{S+1:N} and T^{S+1:N} = X_(1:S)^T K^{1:S}):
 //
-//   D[c, r] = sum_k X[k + L c] K[k, r],   k over the L = I_1 ... I_S leading
-//   modes, c over the C trailing ones, K = H^(S) (.) ... (.) H^(1).
+//   right: D[c, r] = sum_k X[k + L c] K[k, r]   (k over the L leading entries)
+//   left:  D[l, r] = sum_k X[l + L k] K[k, r]   (k over the C trailing entries)
 //
-// K is formed once per call in FP32 and split into three BF16 terms
+// K (the Khatri-Rao product of the branch's other factors, first mode
+// fastest) is formed once per call in FP32 and split into three BF16 terms
 // hi + mid + lo (exact for FP32 values), stored K-major as the MMA's B
-// operand: 3 R' rows of Kp = L rounded up to 64 elements (1.5 MB for L =
-// 16384, R' = 16; it stays in L2).  A is X itself, rows c with K contiguous,
-// loaded by TMA.  Rows c lie on TMEM lanes, so the whole sum over k happens in
-// the MMA: no per-row weighting or cross-row reduction in the epilogue, which
-// only drains the accumulator every KR_SEG stages into FP32 registers (the
-// tensor core truncates products to the running sum's exponent range, so
-// chains are kept short; 8 MMAs per drain, as in the other partial-MTTKRP
-// kernels).
+// operand: 3 R' rows of Kp = the reduction length rounded up to 64 (1.5 MB
+// for a reduction of 16384 and R' = 16; it stays in L2).  A is X itself,
+// loaded by TMA: K-major for the right branch (rows c, k contiguous),
+// MN-major for the left (rows l contiguous).  Output rows lie on TMEM lanes,
+// so the whole sum over k happens in the MMA: no per-row weighting or
+// cross-row reduction in the epilogue, which only drains the accumulator
+// every KR_SEG stages into FP32 registers (the tensor core truncates products
+// to the running sum's exponent range, so chains are kept short; 8 MMAs per
+// drain, as in the other partial-MTTKRP kernels).
 //
 // Work: units (128-row tile, 64-element k-step), split into equal contiguous
 // ranges, one per CTA of a persistent grid (stream-K); each CTA writes one
@@ -128,7 +130,7 @@ __global__ void krp_reduce_kernel(const float* __restrict__ part, int64_t C, int
 }
 
 // ---- the GEMM: persistent, stream-K over (tile, k-step) units ------------------------
-template <int RB>
+template <int RB, bool LEFT>
 __global__ void __launch_bounds__(KR_THREADS, 1)
 pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
               const __grid_constant__ KrpParams p) {
@@ -205,7 +207,13 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
         mbar_arrive_expect_tx(&full[s], ST_BYTES);
         uint8_t* a = smem + (size_t)s * ST_BYTES;
         const int kx = (int)(u % ks) * KR_BK;
-        tma_load_2d(a, &tA, &full[s], kx, (int)(u / ks) * KR_BM);
+        const int m0 = (int)(u / ks) * KR_BM;
+        if (LEFT) {  // MN-major: two boxes of 64 rows x 64 k (rows contiguous in X)
+          tma_load_2d(a, &tA, &full[s], m0, kx);
+          tma_load_2d(a + A_BYTES / 2, &tA, &full[s], m0 + 64, kx);
+        } else {     // K-major: 128 rows x 64 k
+          tma_load_2d(a, &tA, &full[s], kx, m0);
+        }
         tma_load_2d(a + A_BYTES, &tB, &full[s], kx, 0);
         if (++s == stages) { s = 0; ph ^= 1; }
       }
@@ -221,7 +229,7 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(1u, false, false, KR_BM, N);
+      const uint32_t idesc = instr_desc(1u, LEFT, false, KR_BM, N);
       int s = 0, buf = 0;
       uint32_t ph = 0, eph = 0;
       bool ok = true, issued = false;
@@ -239,7 +247,8 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
           const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < KR_BK / KR_UK; ++kk) {
-            const uint64_t ad = smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
+            const uint64_t ad = LEFT ? smem_desc(a0 + kk * 2048, A_BYTES / 2, 1024, kLayoutSW128)
+                                     : smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
             const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
             mma_f16_ss(d, ad, bd, idesc, acc);
             acc = 1;
@@ -323,13 +332,14 @@ struct KrpPlan {
   size_t img_bytes = 0, part_bytes = 0, smem = 0;
 };
 
-KrpPlan krp_plan(int64_t L, int64_t C, int R, int sm_count) {
+// Mdim: output rows (C right, L left); Kdim: the reduction (L right, C left)
+KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count) {
   KrpPlan pl;
-  if (R < 1 || R > 32 || L < 1 || C < 1) return pl;
+  if (R < 1 || R > 32 || Mdim < 1 || Kdim < 1) return pl;
   pl.RB = R <= 16 ? 16 : 32;
-  pl.Kp = (L + KR_BK - 1) / KR_BK * KR_BK;
+  pl.Kp = (Kdim + KR_BK - 1) / KR_BK * KR_BK;
   pl.ks = (int)(pl.Kp / KR_BK);
-  const int64_t m_tiles = (C + KR_BM - 1) / KR_BM;
+  const int64_t m_tiles = (Mdim + KR_BM - 1) / KR_BM;
   pl.U = m_tiles * pl.ks;
   pl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.U, sm_count));
   int tmax = 1;
@@ -348,7 +358,7 @@ KrpPlan krp_plan(int64_t L, int64_t C, int R, int sm_count) {
   return pl;
 }
 
-// PLANC_PM_KRP=0 keeps the BF16 right branch on the weighted-row kernel (read
+// PLANC_PM_KRP=0 keeps both BF16 branches on the weighted-row kernels (read
 // when a context is created and at every launch)
 bool krp_enabled() {
   const char* v = getenv("PLANC_PM_KRP");
@@ -359,22 +369,24 @@ bool krp_enabled() {
 
 bool pm_krp_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                      const KrpHost& kh) {
-  if (xdt != PLANC_BF16 || left || !krp_enabled()) return false;
+  (void)left;
+  if (xdt != PLANC_BF16 || !krp_enabled()) return false;
   if (R < 1 || R > 32 || kh.nm < 1 || kh.nm > PLANC_MAX_N) return false;
   // TMA: the row stride of X (L BF16 elements) a multiple of 16 bytes
   if (L % 8 != 0 || L >= (1LL << 31) || C >= (1LL << 31)) return false;
   return tensor_map_encoder() != nullptr;
 }
 
-size_t pm_krp_workspace_bytes(int64_t L, int64_t C, int R, int sm_count) {
-  const KrpPlan pl = krp_plan(L, C, R, sm_count);
+size_t pm_krp_workspace_bytes(bool left, int64_t L, int64_t C, int R, int sm_count) {
+  const KrpPlan pl = left ? krp_plan(L, C, R, sm_count) : krp_plan(C, L, R, sm_count);
   return pl.ok ? pl.img_bytes + pl.part_bytes : 0;
 }
 
-cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, const KrpHost& kh, int R,
-                          void* out, bool out_rowmajor, void* work, size_t work_bytes,
+cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, bool left, const KrpHost& kh,
+                          int R, void* out, bool out_rowmajor, void* work, size_t work_bytes,
                           int* err_flag, int sm_count, cudaStream_t st) {
-  const KrpPlan pl = krp_plan(L, C, R, sm_count);
+  const int64_t Mdim = left ? L : C, Kdim = left ? C : L;
+  const KrpPlan pl = krp_plan(Mdim, Kdim, R, sm_count);
   if (!pl.ok || work_bytes < pl.img_bytes + pl.part_bytes) return cudaErrorInvalidValue;
   if (((uintptr_t)X & 15) != 0 || ((uintptr_t)work & 255) != 0) return cudaErrorInvalidValue;
   __nv_bfloat16* img = static_cast<__nv_bfloat16*>(work);
@@ -388,18 +400,20 @@ cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, const KrpHost& kh
   }
   {
     const int64_t n = pl.Kp * pl.RB;
-    krp_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, L, pl.Kp, img);
+    krp_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim, pl.Kp, img);
     note_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // tensor maps: A = X as L x C (K contiguous), B = the image as Kp x 3 RB
+  // tensor maps: A = X as L x C (L contiguous; right: rows c, 64 x 128 boxes
+  // along L; left: rows l, two 64 x 64 boxes per stage), B = the image as
+  // Kp x 3 RB
   CUtensorMap tA, tB;
   cuuint32_t estr[2] = {1u, 1u};
   {
     cuuint64_t gdim[2] = {(cuuint64_t)L, (cuuint64_t)C};
     cuuint64_t gstride[1] = {(cuuint64_t)L * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KR_BK, (cuuint32_t)KR_BM};
+    cuuint32_t box[2] = {(cuuint32_t)KR_BK, (cuuint32_t)(left ? 64 : KR_BM)};
     if (tensor_map_encoder()(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(X), gdim, gstride,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -417,7 +431,7 @@ cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, const KrpHost& kh
       return cudaErrorInvalidValue;
   }
   KrpParams p{};
-  p.C = C;
+  p.C = Mdim;
   p.U = pl.U;
   p.ks = pl.ks;
   p.R = R;
@@ -425,16 +439,17 @@ cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, const KrpHost& kh
   p.tmax = pl.tmax;
   p.part = part;
   p.err = err_flag;
-  auto k = pl.RB == 16 ? pm_krp_kernel<16> : pm_krp_kernel<32>;
+  auto k = pl.RB == 16 ? (left ? pm_krp_kernel<16, true> : pm_krp_kernel<16, false>)
+                       : (left ? pm_krp_kernel<32, true> : pm_krp_kernel<32, false>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
   e = launch_pdl(k, dim3(pl.grid), dim3(KR_THREADS), pl.smem, st, tA, tB, p);
   if (e != cudaSuccess) return e;
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int64_t n = C * R;
+  const int64_t n = Mdim * R;
   krp_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      part, C, R, pl.RB, pl.U, pl.ks, pl.grid, pl.tmax, static_cast<float*>(out),
+      part, Mdim, R, pl.RB, pl.U, pl.ks, pl.grid, pl.tmax, static_cast<float*>(out),
       out_rowmajor ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();

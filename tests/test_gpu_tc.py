@@ -132,10 +132,10 @@ def test_tc_solve_matches_cuda_core_solve(monkeypatch):
 
 @pytest.mark.parametrize("dims,R,split", [((64, 48, 80), 16, -1), ((16, 24, 200), 17, 2),
                                           ((32, 128, 400), 16, 2), ((128, 8, 97, 5), 32, 2)])
-def test_bf16_right_branch_gemm_matches_weighted_rows(dims, R, split, monkeypatch):
-    """The BF16 right branch as one GEMM against the split Khatri-Rao image
-    and the weighted-row kernel (PLANC_PM_KRP=0) agree, and both match the
-    oracle to 1e-5 per entry."""
+def test_bf16_gemm_branches_match_weighted_rows(dims, R, split, monkeypatch):
+    """Both BF16 partial MTTKRPs as one GEMM against the split Khatri-Rao
+    image and the weighted-row kernels (PLANC_PM_KRP=0) agree, and both
+    match the oracle to 1e-5 per entry."""
     p = planc()
     Xd, Xs, Hd, Hs = _ctx_and_refs(dims, R, split, "bf16", seed=3)
     outs = []
@@ -143,9 +143,10 @@ def test_bf16_right_branch_gemm_matches_weighted_rows(dims, R, split, monkeypatc
         monkeypatch.setenv("PLANC_PM_KRP", krp)
         with p.Context(Xd, dims, R, split) as ctx:
             assert ctx.tc_mask == 3
-            outs.append(ctx.partial_mttkrp(Hd, 1).double().cpu().numpy())
-            n = len(dims) - 1
-            M = ctx.mttkrp(Hd, n).double().cpu().numpy()
-            assert max_rel(M, o.mttkrp(Xs, Hs, n)) <= 1e-5
-    assert max_rel(outs[0], outs[1]) <= 2e-6
+            outs.append([ctx.partial_mttkrp(Hd, s).double().cpu().numpy() for s in (0, 1)])
+            for n in range(len(dims)):
+                M = ctx.mttkrp(Hd, n).double().cpu().numpy()
+                assert max_rel(M, o.mttkrp(Xs, Hs, n)) <= 1e-5, n
+    for a, b in zip(outs[0], outs[1]):
+        assert max_rel(a, b) <= 2e-6
 
