@@ -341,8 +341,12 @@ __device__ __forceinline__ uint64_t ballot64(bool lo, bool hi) {
   return a | (b << 32);
 }
 
-template <typename TA>
-__global__ void __launch_bounds__(32 * BPP_WARPS)
+// RMAX > 0 (FP32 storage, R <= RMAX <= 32): the passive systems are factored
+// and solved in registers (lane p holds row p of S_FF and of its Cholesky
+// factor; pivots and factor entries travel by warp shuffles), without a
+// shared-memory round trip per elimination step.
+template <typename TA, int RMAX>
+__global__ void __launch_bounds__(32 * BPP_WARPS, 1)
 nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
                TA* __restrict__ H, const double* __restrict__ lam, int max_iter,
                int32_t* __restrict__ inner, int* __restrict__ flags) {
@@ -378,9 +382,10 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
   // pipe is narrow, and the factorisation is a chain of dependent steps) and
   // x_F refined with FP64 residuals m_F - S_FF x_F until the correction is
   // below 1e-11 of x (mixed-precision iterative refinement: the result is the
-  // FP64 solution to that accuracy); a pivot that falls below 1e-5 of its
-  // diagonal entry, or a refinement that does not settle in 6 steps, hands
-  // the system to the FP64 factorisation.
+  // FP64 solution to that accuracy; 1e-9 on the register path, whose results
+  // are stored in FP32); a pivot that falls below 1e-5 of its diagonal
+  // entry, or a refinement that does not settle in 6 steps, hands the system
+  // to the FP64 factorisation.  FP64 storage uses the FP64 factorisation only.
   float* Af = reinterpret_cast<float*>(A);     // FP32 factor (stride LD)
   float* df = reinterpret_cast<float*>(dinv);  // [0, 64): 1 / pivot; [64, 128): diagonal, then rhs
   float* wf = df + 64;
@@ -413,6 +418,98 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     }
   };
 
+  // Register path (RMAX > 0, so R <= 32 and every index j0 is one lane):
+  // x_F into x0, true when the refinement settled (false: FP64 fallback).
+  constexpr int RM = RMAX > 0 ? RMAX : 1;
+  auto solve_reg = [&](int f, int p0, bool in0) -> bool {
+    // position -> index table, zero past f
+    int* tbl = reinterpret_cast<int*>(xs);
+    if (in0) tbl[p0] = j0;
+    if (lane >= f && lane < RM) tbl[lane] = 0;
+    __syncwarp();
+    const bool live = lane < f;
+    const int myi = live ? tbl[lane] : 0;
+    float a[RM];
+#pragma unroll
+    for (int q = 0; q < RM; ++q) a[q] = (live && q < f) ? (float)Ss[myi * LD + tbl[q]] : 0.f;
+    const float d0 = (float)Ss[myi * LD + myi];
+    __syncwarp();  // tbl read by all lanes before xs is reused
+    // Cholesky: after step c, lane i >= c holds L[i][c] in a[c]
+    float inv[RM];
+    int good = 1;
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      inv[c] = 0.f;
+      if (c < f) {
+        float piv = __shfl_sync(0xffffffffu, a[c], c);
+        const float dc = __shfl_sync(0xffffffffu, d0, c);
+        if (!(piv > 1e-5f * dc)) {
+          good = 0;
+          piv = 1.f;
+        }
+        const float ic = rsqrtf(piv);
+        inv[c] = ic;
+        const float lic = a[c] * ic;
+        if (lane >= c) a[c] = lic;
+#pragma unroll
+        for (int j = c + 1; j < RM; ++j) {
+          if (j < f) {
+            const float ljc = __shfl_sync(0xffffffffu, lic, j);
+            if (lane >= j) a[j] = fmaf(-lic, ljc, a[j]);
+          }
+        }
+      }
+    }
+    if (!good) return false;
+    // L by rows into shared memory for the transposed solve
+#pragma unroll
+    for (int q = 0; q < RM; ++q)
+      if (live && q <= lane && q < f) Af[lane * LD + q] = a[q];
+    __syncwarp();
+    x0 = 0.0;
+    double r0 = in0 ? m0 : 0.0;  // residual on F (x = 0)
+    for (int st = 0; st <= 6; ++st) {
+      // right-hand side to the position lanes, then L z = r, L^T d = z
+      float w = __shfl_sync(0xffffffffu, (float)r0, myi);
+      if (!live) w = 0.f;
+#pragma unroll
+      for (int c = 0; c < RM; ++c) {
+        if (c < f) {
+          const float zc = __shfl_sync(0xffffffffu, w, c) * inv[c];
+          if (lane > c) w = fmaf(-a[c], zc, w);
+          else if (lane == c) w = zc;
+        }
+      }
+#pragma unroll
+      for (int c = RM - 1; c >= 0; --c) {
+        if (c < f) {
+          const float xc = __shfl_sync(0xffffffffu, w, c) * inv[c];
+          if (lane < c) w = fmaf(-Af[c * LD + lane], xc, w);
+          else if (lane == c) w = xc;
+        }
+      }
+      const float dw = __shfl_sync(0xffffffffu, w, p0 & 31);
+      const double d = in0 ? (double)dw : 0.0;
+      x0 += d;
+      double dm = fabs(d), xm = fabs(x0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+      }
+      if (st > 0 && dm <= 1e-9 * xm) return true;
+      if (st == 6) return false;
+      // FP64 residual m_F - S_FF x_F
+      if (v0) zs[j0] = x0;
+      __syncwarp();
+      double s0, s1;
+      sx(s0, s1);
+      r0 = in0 ? m0 - s0 : 0.0;
+      __syncwarp();
+    }
+    return false;
+  };
+
   // x_F = S_FF^{-1} m_F, x_G = 0; y = S x - m on G, 0 on F
   auto solve = [&]() {
     const int f = __popcll(F);
@@ -424,7 +521,10 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     bool done = f == 0;
     x0 = 0.0;
     x1 = 0.0;
-    if (!done) {
+    if constexpr (RMAX > 0) {
+      if (!done) done = solve_reg(f, p0, in0);
+    }
+    if (!done && RMAX == 0 && sizeof(TA) == 4) {
       // FP32 S_FF: each lane owns the columns of its indices, A[p_a][p_b] = S[a][b]
       for (int a = 0; a < R; ++a) {
         if (!((F >> a) & 1ull)) continue;
@@ -1005,15 +1105,26 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
     const int blocks = (int)((a.rows + BPP_WARPS - 1) / BPP_WARPS);
     const size_t rl = (size_t)a.R * (a.R + 1);  // R x R with leading dimension R + 1
     size_t smem = (rl + BPP_WARPS * (rl + 3 * 64)) * sizeof(double);
-    cudaFuncSetAttribute(nls_bpp_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(nls_bpp_kernel<TA, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+    if constexpr (sizeof(TA) == 4) {
+      cudaFuncSetAttribute(nls_bpp_kernel<TA, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      cudaFuncSetAttribute(nls_bpp_kernel<TA, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    }
     if (a.inner && a.reset_inner) {
       set_int_kernel<<<1, 32, 0, st>>>(a.inner, 0, 1);
       note_launches(1);
     }
     int max_iter = a.opts.bpp_max_iter > 0 ? a.opts.bpp_max_iter : 10 * a.R;
-    nls_bpp_kernel<TA><<<blocks, 32 * BPP_WARPS, smem, st>>>(
-        a.rows, a.R, a.S, (const TA*)a.M, (TA*)a.H, a.lambda, max_iter, a.inner, a.flags);
+    auto k = nls_bpp_kernel<TA, 0>;
+    if constexpr (sizeof(TA) == 4) {
+      if (a.R <= 16) k = nls_bpp_kernel<TA, 16>;
+      else if (a.R <= 32) k = nls_bpp_kernel<TA, 32>;
+    }
+    k<<<blocks, 32 * BPP_WARPS, smem, st>>>(a.rows, a.R, a.S, (const TA*)a.M, (TA*)a.H, a.lambda,
+                                           max_iter, a.inner, a.flags);
     note_launches(1);
     return cudaGetLastError();
   }
