@@ -12,10 +12,11 @@
 // loaded by TMA: K-major for the right branch (rows c, k contiguous),
 // MN-major for the left (rows l contiguous).  Output rows lie on TMEM lanes,
 // so the whole sum over k happens in the MMA: no per-row weighting or
-// cross-row reduction in the epilogue, which only drains the accumulator
+// cross-row reduction in the epilogue, which only drains the accumulators
 // every KR_SEG stages into FP32 registers (the tensor core truncates products
-// to the running sum's exponent range, so chains are kept short; 8 MMAs per
-// drain, as in the other partial-MTTKRP kernels).
+// to the running sum's exponent range, so chains are kept short: two
+// alternating sub-accumulators of 8 MMAs each per drain, the chain length of
+// the other partial-MTTKRP kernels).
 //
 // Work: units (128-row tile, 64-element k-step), split into equal contiguous
 // ranges, one per CTA of a persistent grid (stream-K); each CTA writes one
@@ -45,10 +46,10 @@ using namespace tc;
 constexpr int KR_BM = 128;               // output rows (c) per tile
 constexpr int KR_BK = 64;                // k per stage: 128 bytes of BF16, one swizzle row
 constexpr int KR_UK = 16;                // k per MMA
-constexpr int KR_SEG = 2;                // stages per accumulator drain (8 MMAs)
+constexpr int KR_SEG = 4;                // stages per accumulator drain (two chains of 8 MMAs)
 constexpr int KR_THREADS = 192;          // TMA warp, MMA warp, 4 epilogue warps
 constexpr int KR_MAX_STAGES = 8;
-constexpr uint32_t KR_TMEM_COLS = 256;   // two accumulators of up to 128 columns
+constexpr uint32_t KR_TMEM_COLS = 512;   // accumulator buffers: [even | odd k-steps] x N
 
 struct KrpDev {
   int nm;
@@ -139,6 +140,14 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
   constexpr uint32_t B_BYTES = N * KR_BK * 2;         // multiple of 1024
   constexpr uint32_t ST_BYTES = A_BYTES + B_BYTES;
   static_assert(B_BYTES % 1024 == 0 && N % 16 == 0 && N <= 128, "tile shape");
+  // An accumulator buffer holds two sub-accumulators of N columns: the even
+  // and the odd k-steps of a drain segment go to different ones, so each
+  // FP32 accumulation chain is 8 MMAs long (the tensor core truncates
+  // products to the running sum's exponent range: short chains keep the
+  // bias at a few 1e-7) while drains, whose fixed cost showed in the launch
+  // time, come every KR_SEG = 4 stages.
+  constexpr uint32_t BSTRIDE = 2 * N <= 128 ? 128u : 256u;  // columns per buffer
+  constexpr int KR_NACC = (int)(KR_TMEM_COLS / BSTRIDE);     // 4 or 2 buffers
   extern __shared__ uint8_t kr_raw[];
   const uint32_t raw = smem_u32(kr_raw);
   uint8_t* smem = kr_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -147,8 +156,8 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
   uint64_t* full = bars;                 // TMA -> MMA
   uint64_t* empty = full + stages;       // MMA -> TMA
   uint64_t* acc_full = empty + stages;   // MMA -> epilogue
-  uint64_t* acc_empty = acc_full + 2;    // epilogue -> MMA
-  uint64_t* drain = acc_empty + 2;
+  uint64_t* acc_empty = acc_full + KR_NACC;  // epilogue -> MMA
+  uint64_t* drain = acc_empty + KR_NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   {
@@ -167,7 +176,7 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < KR_NACC; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);
     }
@@ -238,9 +247,9 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
         if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 43)) break;
         eph ^= 1u << buf;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)buf * 128u;
-        uint32_t acc = 0;
-        for (; u < ue; ++u) {
+        const uint32_t d = tmem + (uint32_t)buf * BSTRIDE;
+        for (int i = 0; u < ue; ++u, ++i) {
+          const uint32_t dsub = d + (uint32_t)(i & 1) * N;
           if (!mbar_wait(&full[s], ph, abort, p.err, 44)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + (size_t)s * ST_BYTES);
@@ -250,8 +259,7 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
             const uint64_t ad = LEFT ? smem_desc(a0 + kk * 2048, A_BYTES / 2, 1024, kLayoutSW128)
                                      : smem_desc(a0 + kk * 32, 16, 1024, kLayoutSW128);
             const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
-            mma_f16_ss(d, ad, bd, idesc, acc);
-            acc = 1;
+            mma_f16_ss(dsub, ad, bd, idesc, (i >= 2 || kk > 0) ? 1u : 0u);
           }
           mma_commit(&empty[s]);
           issued = true;
@@ -259,7 +267,7 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
         }
         if (!ok) break;
         mma_commit(&acc_full[buf]);
-        buf ^= 1;
+        buf = (buf + 1) % KR_NACC;
       }
       if (issued) {  // no MMA may be in flight when TMEM is freed
         mma_commit(drain);
@@ -284,7 +292,8 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
       if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 45)) break;
       fph ^= 1u << buf;
       tc_fence_after();
-      const uint32_t taddr = tmem + (uint32_t)buf * 128u + lane_base;
+      const uint32_t taddr = tmem + (uint32_t)buf * BSTRIDE + lane_base;
+      const bool two = ue - u >= 2;  // the odd sub-accumulator was written
 #pragma unroll
       for (int c = 0; c < RB / 16; ++c) {
         float hi[16], mid[16], lo[16];
@@ -294,11 +303,19 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 16; ++j) sum[c * 16 + j] += hi[j] + (mid[j] + lo[j]);
+        if (two) {
+          tmem_ld16(taddr + N + c * 16, hi);
+          tmem_ld16(taddr + N + RB + c * 16, mid);
+          tmem_ld16(taddr + N + 2 * RB + c * 16, lo);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[c * 16 + j] += hi[j] + (mid[j] + lo[j]);
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
-      buf ^= 1;
+      buf = (buf + 1) % KR_NACC;
       const int64_t t = (ue - 1) / ks;
       u = ue;
       if (u == u1 || u % ks == 0) {  // this CTA is done with tile t: its partial block
@@ -351,7 +368,7 @@ KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count) {
   pl.img_bytes = ((size_t)3 * pl.RB * pl.Kp * 2 + 255) / 256 * 256;
   pl.part_bytes = (size_t)pl.grid * tmax * KR_BM * pl.RB * 4;
   const size_t st_bytes = (size_t)KR_BM * KR_BK * 2 + (size_t)3 * pl.RB * KR_BK * 2;
-  const size_t fixed = 1024 + 8 * (2 * KR_MAX_STAGES + 5) + 16;
+  const size_t fixed = 1024 + 8 * (2 * KR_MAX_STAGES + 2 * 4 + 1) + 16;
   pl.stages = (int)std::min<size_t>(KR_MAX_STAGES, (227 * 1024 - fixed) / st_bytes);
   pl.smem = fixed + (size_t)pl.stages * st_bytes;
   pl.ok = pl.stages >= 3;
