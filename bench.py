@@ -62,6 +62,17 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def oracle_tensor(cfg, X):
+    """The values the library stores, as the FP64 array the oracle solves on:
+    BF16 storage rounds X to nearest even once (the mixed-precision reading),
+    so the oracle sees the rounded tensor."""
+    if cfg["dtype"] != "bf16":
+        return np.asarray(X, dtype=np.float64)
+    from paper_1909_01149_gb300 import synth
+    flat = synth.from_bf16_bits(synth.to_bf16_bits(synth.flat(np.asarray(X, dtype=np.float32))))
+    return np.reshape(flat.astype(np.float64), X.shape, order="F")
+
+
 def make_inputs(cfg, seed=1):
     from paper_1909_01149_gb300 import synth
     if cfg["kind"] == "mouse":
@@ -697,7 +708,7 @@ def oracle_one_iteration(config, alg):
     workload (inputs regenerated here, not timed)."""
     import oracle as o
     X, H0 = make_inputs(CONFIGS[config])
-    Xs = np.asarray(X, dtype=np.float64)
+    Xs = oracle_tensor(CONFIGS[config], X)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     t = time.time()
     ref = o.nncp(Xs, Hs, alg, iters=1)
@@ -710,7 +721,7 @@ def cpu_baseline(cfg, X, H0, alg, config):
     with BLAS on all host cores (this process) and on one thread (a fresh
     interpreter started with the BLAS and OpenMP thread counts set to 1)."""
     import oracle as o
-    Xs = np.asarray(X, dtype=np.float64)
+    Xs = oracle_tensor(cfg, X)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     t = time.time()
     ref = o.nncp(Xs, Hs, alg, iters=1)
@@ -739,9 +750,10 @@ def golden_history(config, cfg, alg):
     """The oracle's error history for this workload from the committed golden
     file (tests/golden/fullsize_oracle.json), or None."""
     path = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
-    if config != "dense512-f32" or not os.path.exists(path):
+    key = {"dense512-f32": "dense512", "mouse4d-bf16": "mouse4d_bf16"}.get(config)
+    if key is None or not os.path.exists(path):
         return None
-    g = json.load(open(path)).get("dense512", {})
+    g = json.load(open(path)).get(key, {})
     if tuple(g.get("dims", ())) != tuple(cfg["dims"]) or g.get("iters") != cfg["iters"]:
         return None
     return g.get(alg, {}).get("rel_err")
@@ -756,7 +768,7 @@ def run_reference(args, cfg):
         return None, rank
     import oracle as o
     X, H0 = make_inputs(cfg)
-    Xs = np.asarray(X, dtype=np.float64)
+    Xs = oracle_tensor(cfg, X)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     alg = args.alg or cfg["alg"]
     for _ in range(args.warmup):
