@@ -345,9 +345,10 @@ def run_planc(args, cfg):
         # live: the oracle's first outer iteration against the GPU's
         o1 = cb.pop("rel_err_iter1")
         out["cpu_baseline"] = cb
-        out.setdefault("oracle_check", {})["live_iter1"] = {
-            "gpu_rel_err": res["rel_err"][0], "oracle_rel_err": o1,
-            "abs_diff": abs(res["rel_err"][0] - o1), "tolerance": tol}
+        if o1 is not None:
+            out.setdefault("oracle_check", {})["live_iter1"] = {
+                "gpu_rel_err": res["rel_err"][0], "oracle_rel_err": o1,
+                "abs_diff": abs(res["rel_err"][0] - o1), "tolerance": tol}
     return out, rank
 
 
@@ -571,6 +572,20 @@ def run_batch(args):
         os.environ.pop("PLANC_BATCH_RANK_BLOCKING", None)
         out[dtn]["batched_s_by_rank_blocking"] = per
         del Xd
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on a bounded sample: the first 8 instances, two HALS
+        # outer iterations each, BLAS on all host cores
+        import oracle as o
+        ns, its = 8, 2
+        t0 = time.time()
+        for (X, _, R), H in zip(insts[:ns], H0[:ns]):
+            o.nncp(np.asarray(X, dtype=np.float64), [np.asarray(h, dtype=np.float64) for h in H],
+                   "hals", iters=its)
+        dt = time.time() - t0
+        out["cpu_baseline"] = {
+            "value": round(ns * its / dt, 2), "unit": "instance-iterations/s",
+            "cores": os.cpu_count(), "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"the first {ns} instances, {its} HALS outer iterations each, NumPy FP64"}
     return out, 0
 
 
@@ -715,12 +730,29 @@ def oracle_one_iteration(config, alg):
     return time.time() - t, ref["rel_err"][0]
 
 
+# the oracle forms each mode's Khatri-Rao product explicitly; above this size
+# (FP64 bytes) its legs are skipped rather than run (the largest configured
+# workload, 96^4 R=64, needs 453 MB a mode)
+ORACLE_KRP_LIMIT = 4 << 30
+
+
+def oracle_krp_bytes(cfg):
+    dims, R = cfg["dims"], cfg["R"]
+    return max(int(np.prod([d for k, d in enumerate(dims) if k != n])) * R * 8
+               for n in range(len(dims)))
+
+
 def cpu_baseline(cfg, X, H0, alg, config):
     """The FP64 oracle, as it stands, on a bounded sample: one outer iteration
     of the full workload (every mode's MTTKRP, NNLS, normalisation, error),
     with BLAS on all host cores (this process) and on one thread (a fresh
     interpreter started with the BLAS and OpenMP thread counts set to 1)."""
     import oracle as o
+    if oracle_krp_bytes(cfg) > ORACLE_KRP_LIMIT:
+        return {"value": None, "unit": "iter/s", "kind": "oracle",
+                "skipped": "the oracle's explicit Khatri-Rao product would take "
+                           f"{oracle_krp_bytes(cfg) / 2**30:.0f} GiB per mode",
+                "rel_err_iter1": None}
     Xs = oracle_tensor(cfg, X)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
     t = time.time()
@@ -767,6 +799,10 @@ def run_reference(args, cfg):
     if rank != 0:
         return None, rank
     import oracle as o
+    if oracle_krp_bytes(cfg) > ORACLE_KRP_LIMIT:
+        return {"impl": "reference", "unavailable":
+                "the oracle's explicit Khatri-Rao product would take "
+                f"{oracle_krp_bytes(cfg) / 2**30:.0f} GiB per mode on this workload"}, rank
     X, H0 = make_inputs(cfg)
     Xs = oracle_tensor(cfg, X)
     Hs = [np.asarray(h, dtype=np.float64) for h in H0]
