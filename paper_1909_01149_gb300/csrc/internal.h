@@ -71,15 +71,17 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
                          bool left, const KrpHost& krp, int R, void* out,
                          bool out_rowmajor, void* work, size_t work_bytes,
                          int* err_flag, int sm_count, cudaStream_t st);
-// BF16 partial MTTKRPs (both root branches) as one GEMM against the split
-// Khatri-Rao image (kern_pm_krp.cu); launch_pm_tc takes it when eligible and
-// the workspace holds it (PLANC_PM_KRP=0 turns it off)
+// Partial MTTKRPs as one GEMM against the split Khatri-Rao image
+// (kern_pm_krp.cu): BF16 X both root branches, FP32 X the right branch when
+// the image is small next to X; launch_pm_tc takes it when eligible and the
+// workspace holds it (PLANC_PM_KRP=0 turns it off)
 bool pm_krp_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                      const KrpHost& krp_dims);
-size_t pm_krp_workspace_bytes(bool left, int64_t L, int64_t C, int R, int sm_count);
-cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, bool left, const KrpHost& krp,
-                          int R, void* out, bool out_rowmajor, void* work, size_t work_bytes,
-                          int* err_flag, int sm_count, cudaStream_t st);
+size_t pm_krp_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
+                              int sm_count);
+cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
+                          const KrpHost& krp, int R, void* out, bool out_rowmajor, void* work,
+                          size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st);
 
 // ---- multi-TTV (Sec. 4.2.2) --------------------------------------------------
 // T is the node tensor T^{a:b} viewed as T[p + P1 q + P1 Q r].

@@ -337,25 +337,393 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
   }
 }
 
+
+// ---- FP32 X: the right branch with converter warps (3xTF32) ---------------------------
+// The same GEMM for FP32 storage: converter warps split every X value of a
+// stage into TF32 hi + lo in TMEM (the MMA's A operand), and two MMA warps
+// issue x_hi [k_hi | k_lo] and x_lo k_hi (dropped x_lo k_lo below 2^-22), K
+// carried in the image as TF32 hi and lo rows.  Rows are centred per drain
+// segment as in the weighted-row kernel: the converters subtract the mean
+// c_g of the row's values in the segment's first stage, so the tensor core's
+// truncating accumulation sees small mixed-sign partial sums, and the
+// epilogue adds c_g sum_{k in segment} K[k, r] back (the image kernel writes
+// the column sums of K per 32-element k-step, TwoSum-compensated).
+constexpr int K3_BK = 32;               // FP32 elements per stage (128 bytes)
+constexpr int K3_UK = 8;                // per kind::tf32 MMA
+constexpr int K3_THREADS = 352;         // TMA, MMA, 4 converters, 4 epilogue, second MMA
+constexpr int K3_W_CONV0 = 2, K3_W_EPI0 = 6, K3_W_MMA2 = 10;
+constexpr int K3_SEG = 8;               // stages per drain segment (centred)
+constexpr int K3_MAX_STAGES = 6;
+
+__device__ __forceinline__ float k3_tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// row `row` of a K-major 128-byte-swizzled tile of 32 fp32 per row
+__device__ __forceinline__ void k3_lds_row(uint32_t x, int row, float* v) {
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const uint32_t a = x + row * 128 + (((jj ^ (row & 7)) & 7) << 4);
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[4 * jj + 0]), "=f"(v[4 * jj + 1]), "=f"(v[4 * jj + 2]),
+                   "=f"(v[4 * jj + 3])
+                 : "r"(a)
+                 : "memory");
+  }
+}
+
+// mean of a row's 32 values (pairwise sum)
+__device__ __forceinline__ float k3_mean32(const float* v) {
+  float t[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) t[c] = v[2 * c] + v[2 * c + 1];
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int c = 0; c < w; ++c) t[c] += t[c + w];
+  return t[0] * (1.f / 32.f);
+}
+
+// Image for FP32: Bt rows r (TF32 hi) and RB + r (TF32 lo) of Kp FP32 values,
+// and cs[q RB + r] = sum of K[k, r] over the 32 k of k-step q (each warp
+// covers one k-step of one r: Kp is a multiple of 32)
+__global__ void krp32_image_kernel(KrpDev kd, int R, int RB, int64_t L, int64_t Kp,
+                                   float* __restrict__ Bt, float* __restrict__ cs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = idx < Kp * RB;  // whole warps are in or out (Kp * RB % 32 == 0)
+  if (!__any_sync(0xffffffffu, in)) return;
+  const int64_t k = in ? idx % Kp : 0;
+  const int r = in ? (int)(idx / Kp) : 0;
+  float v = 0.f;
+  if (in && k < L && r < R) {
+    int64_t rest = k;
+    const int64_t i0 = rest % kd.dim[0];
+    rest /= kd.dim[0];
+    v = kd.H[0][i0 * R + r];
+    for (int m = 1; m < kd.nm; ++m) {
+      const int64_t im = rest % kd.dim[m];
+      rest /= kd.dim[m];
+      v *= kd.H[m][im * R + r];
+    }
+  }
+  if (in) {
+    const float hi = k3_tf32_rn(v);
+    Bt[(int64_t)r * Kp + k] = hi;
+    Bt[(int64_t)(RB + r) * Kp + k] = k3_tf32_rn(v - hi);
+  }
+  // column sum over the warp's 32 k, with the rounding errors carried (TwoSum)
+  float s = v, e = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float t = __shfl_xor_sync(0xffffffffu, s, o);
+    const float te = __shfl_xor_sync(0xffffffffu, e, o);
+    const float sum = s + t;
+    const float bb = sum - s;
+    const float err = (s - (sum - bb)) + (t - bb);
+    s = sum;
+    e = e + te + err;
+  }
+  if (in && (threadIdx.x & 31) == 0) cs[(k / 32) * RB + r] = s + e;
+}
+
+// KrpParams with the FP32 extras
+struct Krp32Params {
+  int64_t C, U;
+  int ks, R, stages, tmax, aslots;
+  float* part;       // [grid][tmax][128][RB]
+  const float* cs;   // column sums of K per k-step: [ks][RB]
+  int* err;
+};
+
+template <int RB>
+__global__ void __launch_bounds__(K3_THREADS, 1)
+pm_krp32_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                const __grid_constant__ Krp32Params p) {
+  constexpr uint32_t A_BYTES = KR_BM * K3_BK * 4;   // 16 KB
+  constexpr uint32_t B_BYTES = 2 * RB * K3_BK * 4;  // [hi | lo] rows
+  constexpr uint32_t ST_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t ACC = 3 * RB;                  // [x_hi k_hi | x_hi k_lo | x_lo k_hi]
+  static_assert(B_BYTES % 1024 == 0 && RB % 16 == 0 && RB <= 64, "tile shape");
+  extern __shared__ uint8_t kr_raw[];
+  const uint32_t raw = smem_u32(kr_raw);
+  uint8_t* smem = kr_raw + (((raw + 1023u) & ~1023u) - raw);
+  const int stages = p.stages, aslots = p.aslots;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * ST_BYTES);
+  uint64_t* full = bars;                  // TMA -> converters (A and B landed)
+  uint64_t* x_empty = full + stages;      // converters (4) + MMA commits (2) -> TMA
+  uint64_t* a_full = x_empty + stages;    // converters -> MMA warps
+  uint64_t* a_empty = a_full + 4;         // MMA commits (2) -> converters
+  uint64_t* acc_full = a_empty + 4;       // MMA commits (2) -> epilogue
+  uint64_t* acc_empty = acc_full + 2;     // epilogue (4) -> MMA warps
+  uint64_t* c_full = acc_empty + 2;       // converters (4) -> epilogue: centres
+  uint64_t* c_empty = c_full + 4;         // epilogue (4) -> converters
+  uint64_t* drain = c_empty + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* cring = reinterpret_cast<float*>(tmem_slot + 4);  // 4 slots x 128 rows
+  float* segcs = cring + 4 * KR_BM;                         // 2 x RB: a segment's column sums
+  {
+    uint32_t dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const uintptr_t end = reinterpret_cast<uintptr_t>(segcs + 2 * RB);
+    if (end - reinterpret_cast<uintptr_t>(kr_raw) > (uintptr_t)dyn || aslots < 1 || aslots > 4) {
+      if (threadIdx.x == 0) atomicExch(p.err, 46);
+      return;  // uniform: no barrier, TMEM or memory access has happened yet
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&x_empty[s], 6);
+    }
+    for (int a = 0; a < 4; ++a) {
+      mbar_init(&a_full[a], 4);
+      mbar_init(&a_empty[a], 2);
+      mbar_init(&c_full[a], 4);
+      mbar_init(&c_empty[a], 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 2);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&drain[0], 1);
+    mbar_init(&drain[1], 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  pdl_wait();  // the image (previous launch) is complete
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t acc0 = (uint32_t)aslots * 64u;  // accumulators after the A slots
+  const int64_t u0 = unit0(p.U, blockIdx.x, gridDim.x);
+  const int64_t u1 = unit0(p.U, blockIdx.x + 1, gridDim.x);
+  const int ks = p.ks;
+  auto seg_end = [&](int64_t u) {
+    const int64_t tile_end = (u / ks + 1) * ks;
+    return min(u1, min(tile_end, u + K3_SEG));
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tA);
+      prefetch_tmap(&tB);
+      int s = 0;
+      uint32_t ph = 0, armed = 0, armed_ph = 0;
+      bool ok = true;
+      for (int64_t u = u0; u < u1; ++u) {
+        if (!mbar_wait(&x_empty[s], ph ^ 1, abort, p.err, 47)) { ok = false; break; }
+        armed |= 1u << s;
+        armed_ph = (armed_ph & ~(1u << s)) | (ph << s);
+        mbar_arrive_expect_tx(&full[s], ST_BYTES);
+        uint8_t* a = smem + (size_t)s * ST_BYTES;
+        const int kx = (int)(u % ks) * K3_BK;
+        tma_load_2d(a, &tA, &full[s], kx, (int)(u / ks) * KR_BM);
+        tma_load_2d(a + A_BYTES, &tB, &full[s], kx, 0);
+        if (++s == stages) { s = 0; ph ^= 1; }
+      }
+      if (!ok) {
+        for (int t = 0; t < stages; ++t) {
+          if (!((armed >> t) & 1u)) continue;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[t], (armed_ph >> t) & 1u) && clock64() - t0 < kWaitCycles / 16) {
+          }
+        }
+      }
+    }
+  } else if (warp >= K3_W_CONV0 && warp < K3_W_EPI0) {
+    // converters: row m of the tile (TMEM lane m) -> centred TF32 hi | lo
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int s = 0, as = 0, cb = 0;
+    uint32_t ph = 0, aph = 0, cph = 0;
+    bool ok = true;
+    for (int64_t u = u0; u < u1 && ok;) {
+      const int64_t ue = seg_end(u);
+      float cseg = 0.f;
+      for (int i = 0; u < ue; ++u, ++i) {
+        if (!mbar_wait(&full[s], ph, abort, p.err, 48)) { ok = false; break; }
+        if (!mbar_wait(&a_empty[as], aph ^ 1, abort, p.err, 49)) { ok = false; break; }
+        float v[K3_BK];
+        k3_lds_row(smem_u32(smem + (size_t)s * ST_BYTES), row, v);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&x_empty[s]);
+        tc_fence_after();
+        if (i == 0) {
+          // the segment's centre goes to a ring slot once the drain that last
+          // read the slot (four segments back) has taken it
+          if (!mbar_wait(&c_empty[cb], ((cph >> cb) & 1u) ^ 1u, abort, p.err, 50)) { ok = false; break; }
+          cph ^= 1u << cb;
+          cseg = k3_mean32(v);
+          cring[cb * KR_BM + row] = cseg;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&c_full[cb]);
+          cb = (cb + 1) & 3;
+        }
+        // hi = x' with the 13 low mantissa bits cleared (exact in TF32), lo =
+        // x' - hi (exact in FP32; the MMA truncates it, unbiased on centred rows)
+        uint32_t hi[K3_BK], lo[K3_BK];
+#pragma unroll
+        for (int c = 0; c < K3_BK; ++c) {
+          const float x = v[c] - cseg;
+          const uint32_t hb = __float_as_uint(x) & 0xffffe000u;
+          hi[c] = hb;
+          lo[c] = __float_as_uint(x - __uint_as_float(hb));
+        }
+        const uint32_t a = tmem + lane_base + (uint32_t)as * 64u;
+        tmem_st16(a, hi);
+        tmem_st16(a + 16, hi + 16);
+        tmem_st16(a + 32, lo);
+        tmem_st16(a + 48, lo + 16);
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[as]);
+        if (++s == stages) { s = 0; ph ^= 1; }
+        if (++as == aslots) { as = 0; aph ^= 1; }
+      }
+    }
+  } else if (warp == 1 || warp == K3_W_MMA2) {
+    if (lane == 0) {
+      // warp 1: x_hi [k_hi | k_lo] (N = 2 RB); the second warp: x_lo k_hi (N = RB)
+      const bool lo_warp = warp == K3_W_MMA2;
+      const uint32_t idesc = lo_warp ? instr_desc(2u, false, false, KR_BM, RB)
+                                     : instr_desc(2u, false, false, KR_BM, 2 * RB);
+      int s = 0, as = 0, buf = 0;
+      uint32_t aph = 0, eph = 0;
+      bool ok = true, issued = false;
+      for (int64_t u = u0; u < u1 && ok;) {
+        const int64_t ue = seg_end(u);
+        if (!mbar_wait(&acc_empty[buf], ((eph >> buf) & 1u) ^ 1u, abort, p.err, 51)) break;
+        eph ^= 1u << buf;
+        tc_fence_after();
+        const uint32_t d = tmem + acc0 + (uint32_t)buf * ACC + (lo_warp ? 2u * RB : 0u);
+        for (int i = 0; u < ue; ++u, ++i) {
+          if (!mbar_wait(&a_full[as], aph, abort, p.err, 52)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t acol = tmem + (uint32_t)as * 64u + (lo_warp ? 32u : 0u);
+          const uint32_t b0 = smem_u32(smem + (size_t)s * ST_BYTES + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < K3_BK / K3_UK; ++kk) {
+            const uint64_t bd = smem_desc(b0 + kk * 32, 16, 1024, kLayoutSW128);
+            mma_tf32_ts(d, acol + kk * K3_UK, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(&a_empty[as]);
+          mma_commit(&x_empty[s]);
+          issued = true;
+          if (++s == stages) s = 0;
+          if (++as == aslots) { as = 0; aph ^= 1; }
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[buf]);
+        buf ^= 1;
+      }
+      if (issued) {
+        uint64_t* dr = &drain[lo_warp ? 1 : 0];
+        mma_commit(dr);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(dr, 0) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp >= K3_W_EPI0 && warp < K3_W_EPI0 + 4) {
+    // epilogue: TMEM lane quarter q holds rows 32 q .. 32 q + 31
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float sum[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) sum[r] = 0.f;
+    const int64_t t_first = u0 / ks;
+    int buf = 0, eb = 0;
+    uint32_t fph = 0, ecph = 0;
+    for (int64_t u = u0; u < u1;) {
+      const int64_t ue = seg_end(u);
+      // the segment's column sums of K: lane l holds columns l and 32 + l
+      // (the segment's k-steps: u mod ks onwards; segments stay within a tile)
+      float cs0 = 0.f, cs1 = 0.f;
+      const int64_t q0 = u % ks;
+      for (int64_t qq = q0; qq < q0 + (ue - u); ++qq) {
+        if (lane < RB) cs0 += p.cs[qq * RB + lane];
+        if (RB > 32 && lane + 32 < RB) cs1 += p.cs[qq * RB + 32 + lane];
+      }
+      if (!mbar_wait(&acc_full[buf], (fph >> buf) & 1u, abort, p.err, 53)) break;
+      fph ^= 1u << buf;
+      if (!mbar_wait(&c_full[eb], (ecph >> eb) & 1u, abort, p.err, 54)) break;
+      ecph ^= 1u << eb;
+      const float cseg = cring[eb * KR_BM + row];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c_empty[eb]);
+      eb = (eb + 1) & 3;
+      tc_fence_after();
+      const uint32_t taddr = tmem + acc0 + (uint32_t)buf * ACC + lane_base;
+#pragma unroll
+      for (int c = 0; c < RB / 16; ++c) {
+        float a[16], b[16], e[16];
+        tmem_ld16(taddr + c * 16, a);
+        tmem_ld16(taddr + RB + c * 16, b);
+        tmem_ld16(taddr + 2 * RB + c * 16, e);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = c * 16 + j;
+          const float k = __shfl_sync(0xffffffffu, col < 32 ? cs0 : cs1, col & 31);
+          sum[col] += fmaf(cseg, k, a[j] + (b[j] + e[j]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      buf ^= 1;
+      const int64_t t = (ue - 1) / ks;
+      u = ue;
+      if (u == u1 || u % ks == 0) {
+        float4* dst = reinterpret_cast<float4*>(
+            p.part + (((int64_t)blockIdx.x * p.tmax + (t - t_first)) * KR_BM + row) * RB);
+#pragma unroll
+        for (int r4 = 0; r4 < RB / 4; ++r4) {
+          dst[r4] = make_float4(sum[4 * r4], sum[4 * r4 + 1], sum[4 * r4 + 2], sum[4 * r4 + 3]);
+          sum[4 * r4] = sum[4 * r4 + 1] = sum[4 * r4 + 2] = sum[4 * r4 + 3] = 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 }  // namespace
 
 namespace {
 
 struct KrpPlan {
-  bool ok = false;
+  bool ok = false, f32 = false;
   int RB = 16;
   int64_t Kp = 0, U = 0;
-  int ks = 0, grid = 0, tmax = 0, stages = 0;
-  size_t img_bytes = 0, part_bytes = 0, smem = 0;
+  int ks = 0, grid = 0, tmax = 0, stages = 0, aslots = 4;
+  size_t img_bytes = 0, cs_bytes = 0, part_bytes = 0, smem = 0;
 };
 
-// Mdim: output rows (C right, L left); Kdim: the reduction (L right, C left)
-KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count) {
+// Mdim: output rows (C right, L left); Kdim: the reduction (L right, C left);
+// f32: FP32 X (converter kernel; 32-element stages)
+KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count, bool f32 = false) {
   KrpPlan pl;
-  if (R < 1 || R > 32 || Mdim < 1 || Kdim < 1) return pl;
-  pl.RB = R <= 16 ? 16 : 32;
-  pl.Kp = (Kdim + KR_BK - 1) / KR_BK * KR_BK;
-  pl.ks = (int)(pl.Kp / KR_BK);
+  pl.f32 = f32;
+  if (R < 1 || R > (f32 ? 64 : 32) || Mdim < 1 || Kdim < 1) return pl;
+  pl.RB = R <= 16 ? 16 : R <= 32 ? 32 : 64;
+  const int bk = f32 ? K3_BK : KR_BK;
+  pl.Kp = (Kdim + 63) / 64 * 64;
+  pl.ks = (int)(pl.Kp / bk);
   const int64_t m_tiles = (Mdim + KR_BM - 1) / KR_BM;
   pl.U = m_tiles * pl.ks;
   pl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.U, sm_count));
@@ -365,14 +733,30 @@ KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count) {
     if (u1 > u0) tmax = std::max<int>(tmax, (int)((u1 - 1) / pl.ks - u0 / pl.ks + 1));
   }
   pl.tmax = tmax;
-  pl.img_bytes = ((size_t)3 * pl.RB * pl.Kp * 2 + 255) / 256 * 256;
   pl.part_bytes = (size_t)pl.grid * tmax * KR_BM * pl.RB * 4;
-  const size_t st_bytes = (size_t)KR_BM * KR_BK * 2 + (size_t)3 * pl.RB * KR_BK * 2;
-  const size_t fixed = 1024 + 8 * (2 * KR_MAX_STAGES + 2 * 4 + 1) + 16;
-  pl.stages = (int)std::min<size_t>(KR_MAX_STAGES, (227 * 1024 - fixed) / st_bytes);
-  pl.smem = fixed + (size_t)pl.stages * st_bytes;
+  if (f32) {
+    pl.aslots = pl.RB == 64 ? 2 : 4;  // TMEM: A slots of 64 columns + two accumulators of 3 RB
+    pl.img_bytes = ((size_t)2 * pl.RB * pl.Kp * 4 + 255) / 256 * 256;
+    pl.cs_bytes = ((size_t)pl.ks * pl.RB * 4 + 255) / 256 * 256;
+    const size_t st_bytes = (size_t)KR_BM * K3_BK * 4 + (size_t)2 * pl.RB * K3_BK * 4;
+    const size_t fixed = 1024 + 8 * (2 * K3_MAX_STAGES + 22) + 16 + 4 * (4 * KR_BM + 2 * 64);
+    pl.stages = (int)std::min<size_t>(K3_MAX_STAGES, (227 * 1024 - fixed) / st_bytes);
+    pl.smem = fixed + (size_t)pl.stages * st_bytes;
+  } else {
+    if (pl.RB > 32) return pl;
+    pl.img_bytes = ((size_t)3 * pl.RB * pl.Kp * 2 + 255) / 256 * 256;
+    const size_t st_bytes = (size_t)KR_BM * KR_BK * 2 + (size_t)3 * pl.RB * KR_BK * 2;
+    const size_t fixed = 1024 + 8 * (2 * KR_MAX_STAGES + 2 * 4 + 1) + 16;
+    pl.stages = (int)std::min<size_t>(KR_MAX_STAGES, (227 * 1024 - fixed) / st_bytes);
+    pl.smem = fixed + (size_t)pl.stages * st_bytes;
+  }
   pl.ok = pl.stages >= 3;
   return pl;
+}
+
+KrpPlan krp_plan_for(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, int sm_count) {
+  const bool f32 = xdt == PLANC_F32;
+  return left ? krp_plan(L, C, R, sm_count, f32) : krp_plan(C, L, R, sm_count, f32);
 }
 
 // PLANC_PM_KRP=0 keeps both BF16 branches on the weighted-row kernels (read
@@ -386,28 +770,42 @@ bool krp_enabled() {
 
 bool pm_krp_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                      const KrpHost& kh) {
-  (void)left;
-  if (xdt != PLANC_BF16 || !krp_enabled()) return false;
-  if (R < 1 || R > 32 || kh.nm < 1 || kh.nm > PLANC_MAX_N) return false;
-  // TMA: the row stride of X (L BF16 elements) a multiple of 16 bytes
-  if (L % 8 != 0 || L >= (1LL << 31) || C >= (1LL << 31)) return false;
+  if (!krp_enabled() || kh.nm < 1 || kh.nm > PLANC_MAX_N) return false;
+  if (L >= (1LL << 31) || C >= (1LL << 31)) return false;
+  if (xdt == PLANC_BF16) {
+    // TMA: the row stride of X (L BF16 elements) a multiple of 16 bytes
+    if (R < 1 || R > 32 || L % 8 != 0) return false;
+  } else if (xdt == PLANC_F32) {
+    // the right branch only (the left one's converters already set its pace),
+    // and only where the FP32 image is small next to X (it is written and
+    // read once per call: 2 R' x L x 4 bytes)
+    if (left || R < 1 || R > 64 || L % 4 != 0) return false;
+    const KrpPlan pl = krp_plan(C, L, R, 148, true);
+    if (!pl.ok || (pl.img_bytes + pl.cs_bytes) * 16 > (size_t)L * C * 4) return false;
+  } else {
+    return false;
+  }
   return tensor_map_encoder() != nullptr;
 }
 
-size_t pm_krp_workspace_bytes(bool left, int64_t L, int64_t C, int R, int sm_count) {
-  const KrpPlan pl = left ? krp_plan(L, C, R, sm_count) : krp_plan(C, L, R, sm_count);
-  return pl.ok ? pl.img_bytes + pl.part_bytes : 0;
+size_t pm_krp_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
+                              int sm_count) {
+  const KrpPlan pl = krp_plan_for(xdt, left, L, C, R, sm_count);
+  return pl.ok ? pl.img_bytes + pl.cs_bytes + pl.part_bytes : 0;
 }
 
-cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, bool left, const KrpHost& kh,
-                          int R, void* out, bool out_rowmajor, void* work, size_t work_bytes,
-                          int* err_flag, int sm_count, cudaStream_t st) {
+cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
+                          const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
+                          size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st) {
+  const bool f32 = xdt == PLANC_F32;
+  if (f32 && left) return cudaErrorInvalidValue;
   const int64_t Mdim = left ? L : C, Kdim = left ? C : L;
-  const KrpPlan pl = krp_plan(Mdim, Kdim, R, sm_count);
-  if (!pl.ok || work_bytes < pl.img_bytes + pl.part_bytes) return cudaErrorInvalidValue;
+  const KrpPlan pl = krp_plan(Mdim, Kdim, R, sm_count, f32);
+  if (!pl.ok || work_bytes < pl.img_bytes + pl.cs_bytes + pl.part_bytes) return cudaErrorInvalidValue;
   if (((uintptr_t)X & 15) != 0 || ((uintptr_t)work & 255) != 0) return cudaErrorInvalidValue;
-  __nv_bfloat16* img = static_cast<__nv_bfloat16*>(work);
-  float* part = reinterpret_cast<float*>(static_cast<char*>(work) + pl.img_bytes);
+  char* wb = static_cast<char*>(work);
+  float* cs = reinterpret_cast<float*>(wb + pl.img_bytes);
+  float* part = reinterpret_cast<float*>(wb + pl.img_bytes + pl.cs_bytes);
   // the split Khatri-Rao image
   KrpDev kd{};
   kd.nm = kh.nm;
@@ -417,50 +815,78 @@ cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, bool left, const 
   }
   {
     const int64_t n = pl.Kp * pl.RB;
-    krp_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim, pl.Kp, img);
+    if (f32)
+      krp32_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          kd, R, pl.RB, Kdim, pl.Kp, reinterpret_cast<float*>(wb), cs);
+    else
+      krp_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          kd, R, pl.RB, Kdim, pl.Kp, reinterpret_cast<__nv_bfloat16*>(wb));
     note_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // tensor maps: A = X as L x C (L contiguous; right: rows c, 64 x 128 boxes
-  // along L; left: rows l, two 64 x 64 boxes per stage), B = the image as
-  // Kp x 3 RB
+  // tensor maps: A = X as L x C (L contiguous; right: rows c, boxes of one
+  // 128-byte row of k by 128 rows; left: rows l, two 64 x 64 boxes per
+  // stage), B = the image, K-major
+  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t es = f32 ? 4 : 2;
+  const cuuint32_t bk = f32 ? K3_BK : KR_BK;
+  const int nrows_b = (f32 ? 2 : 3) * pl.RB;
   CUtensorMap tA, tB;
   cuuint32_t estr[2] = {1u, 1u};
   {
     cuuint64_t gdim[2] = {(cuuint64_t)L, (cuuint64_t)C};
-    cuuint64_t gstride[1] = {(cuuint64_t)L * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KR_BK, (cuuint32_t)(left ? 64 : KR_BM)};
-    if (tensor_map_encoder()(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(X), gdim, gstride,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    cuuint64_t gstride[1] = {(cuuint64_t)L * es};
+    cuuint32_t box[2] = {bk, (cuuint32_t)(left ? 64 : KR_BM)};
+    if (tensor_map_encoder()(&tA, dt, 2, const_cast<void*>(X), gdim, gstride, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   {
-    cuuint64_t gdim[2] = {(cuuint64_t)pl.Kp, (cuuint64_t)(3 * pl.RB)};
-    cuuint64_t gstride[1] = {(cuuint64_t)pl.Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KR_BK, (cuuint32_t)(3 * pl.RB)};
-    if (tensor_map_encoder()(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, img, gdim, gstride, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    cuuint64_t gdim[2] = {(cuuint64_t)pl.Kp, (cuuint64_t)nrows_b};
+    cuuint64_t gstride[1] = {(cuuint64_t)pl.Kp * es};
+    cuuint32_t box[2] = {bk, (cuuint32_t)nrows_b};
+    if (tensor_map_encoder()(&tB, dt, 2, wb, gdim, gstride, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  KrpParams p{};
-  p.C = Mdim;
-  p.U = pl.U;
-  p.ks = pl.ks;
-  p.R = R;
-  p.stages = pl.stages;
-  p.tmax = pl.tmax;
-  p.part = part;
-  p.err = err_flag;
-  auto k = pl.RB == 16 ? (left ? pm_krp_kernel<16, true> : pm_krp_kernel<16, false>)
-                       : (left ? pm_krp_kernel<32, true> : pm_krp_kernel<32, false>);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(k, dim3(pl.grid), dim3(KR_THREADS), pl.smem, st, tA, tB, p);
+  cudaError_t e;
+  if (f32) {
+    Krp32Params p{};
+    p.C = Mdim;
+    p.U = pl.U;
+    p.ks = pl.ks;
+    p.R = R;
+    p.stages = pl.stages;
+    p.tmax = pl.tmax;
+    p.aslots = pl.aslots;
+    p.part = part;
+    p.cs = cs;
+    p.err = err_flag;
+    auto k = pl.RB == 16 ? pm_krp32_kernel<16> : pl.RB == 32 ? pm_krp32_kernel<32> : pm_krp32_kernel<64>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k, dim3(pl.grid), dim3(K3_THREADS), pl.smem, st, tA, tB, p);
+  } else {
+    KrpParams p{};
+    p.C = Mdim;
+    p.U = pl.U;
+    p.ks = pl.ks;
+    p.R = R;
+    p.stages = pl.stages;
+    p.tmax = pl.tmax;
+    p.part = part;
+    p.err = err_flag;
+    auto k = pl.RB == 16 ? (left ? pm_krp_kernel<16, true> : pm_krp_kernel<16, false>)
+                         : (left ? pm_krp_kernel<32, true> : pm_krp_kernel<32, false>);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k, dim3(pl.grid), dim3(KR_THREADS), pl.smem, st, tA, tB, p);
+  }
   if (e != cudaSuccess) return e;
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -471,5 +897,4 @@ cudaError_t launch_pm_krp(const void* X, int64_t L, int64_t C, bool left, const 
   note_launches(1);
   return cudaGetLastError();
 }
-
 }  // namespace planc

@@ -1717,7 +1717,7 @@ size_t pm_tc_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C,
                              const KrpHost& kh, int sm_count) {
   if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return 0;
   if (pm_krp_eligible(xdt, left, L, C, R, kh))
-    return pm_krp_workspace_bytes(left, L, C, R, sm_count);
+    return pm_krp_workspace_bytes(xdt, left, L, C, R, sm_count);
   const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
   if (pl.ok) {
     if (pl.blockmode) return (size_t)pl.nblocks * R * sizeof(float);
@@ -1858,9 +1858,9 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
                          size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st) {
   if (!pm_tc_eligible(xdt, left, L, C, R, kh)) return cudaErrorNotSupported;
   if (pm_krp_eligible(xdt, left, L, C, R, kh) &&
-      work_bytes >= pm_krp_workspace_bytes(left, L, C, R, sm_count))
-    return launch_pm_krp(X, L, C, left, kh, R, out, out_rowmajor, work, work_bytes, err_flag,
-                         sm_count, st);
+      work_bytes >= pm_krp_workspace_bytes(xdt, left, L, C, R, sm_count))
+    return launch_pm_krp(xdt, X, L, C, left, kh, R, out, out_rowmajor, work, work_bytes,
+                         err_flag, sm_count, st);
   {
     const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
     if (pl.ok && getenv("PLANC_TC_STREAMED_KRP") == nullptr)

@@ -41,6 +41,8 @@ TC_CASES = [
     ((24, 40, 130), 1, 2),
     ((16, 24, 200), 17, 2),
     ((8, 8, 9, 3), 32, 2),
+    # FP32 right branch as the converter GEMM with R = 64 (trailing part 2304)
+    ((16, 16, 48, 48), 64, 2),
 ]
 
 
@@ -149,4 +151,24 @@ def test_bf16_gemm_branches_match_weighted_rows(dims, R, split, monkeypatch):
                 assert max_rel(M, o.mttkrp(Xs, Hs, n)) <= 1e-5, n
     for a, b in zip(outs[0], outs[1]):
         assert max_rel(a, b) <= 2e-6
+
+
+@pytest.mark.parametrize("dims,R,split", [((256, 3, 1000), 7, 2), ((16, 16, 5000), 24, 2),
+                                          ((16, 16, 48, 48), 64, 2), ((40, 40, 40, 40), 16, 2)])
+def test_fp32_right_branch_gemm_matches_weighted_rows(dims, R, split, monkeypatch):
+    """FP32 storage, right branch with a long trailing part (the Khatri-Rao
+    image small next to X): the converter GEMM and the weighted-row kernel
+    (PLANC_PM_KRP=0) agree, and every mode matches the oracle to 1e-5."""
+    p = planc()
+    Xd, Xs, Hd, Hs = _ctx_and_refs(dims, R, split, "f32", seed=5)
+    outs = []
+    for krp in ("1", "0"):
+        monkeypatch.setenv("PLANC_PM_KRP", krp)
+        with p.Context(Xd, dims, R, split) as ctx:
+            assert ctx.tc_mask == 3
+            outs.append(ctx.partial_mttkrp(Hd, 1).double().cpu().numpy())
+            for n in range(len(dims)):
+                M = ctx.mttkrp(Hd, n).double().cpu().numpy()
+                assert max_rel(M, o.mttkrp(Xs, Hs, n)) <= 1e-5, n
+    assert max_rel(outs[0], outs[1]) <= 2e-6
 
