@@ -131,7 +131,7 @@ scale_gram_kernel(int64_t rows, int R, int64_t rb, TA* __restrict__ H,
                   const double* __restrict__ colsq_part, int nblk,
                   double* __restrict__ lambda, double* __restrict__ gram_part, int do_scale) {
   extern __shared__ unsigned char smem_raw[];
-  double* s_lam = reinterpret_cast<double*>(smem_raw);               // R
+  double* s_lam = reinterpret_cast<double*>(smem_raw);               // R: 1 / lambda
   TA* s_rows = reinterpret_cast<TA*>(s_lam + R);                      // SG_ROWS x R
   const int tid = threadIdx.x;
   for (int r = tid; r < R; r += blockDim.x) {
@@ -139,7 +139,7 @@ scale_gram_kernel(int64_t rows, int R, int64_t rb, TA* __restrict__ H,
     if (do_scale)
       for (int b = 0; b < nblk; ++b) s += colsq_part[(int64_t)b * R + r];
     double l = do_scale ? sqrt(s) : 1.0;
-    s_lam[r] = l;
+    s_lam[r] = l > 0.0 ? 1.0 / l : 0.0;  // one division per column, not per element
     if (blockIdx.x == 0 && lambda && do_scale) lambda[r] = l;
   }
   __syncthreads();
@@ -157,10 +157,10 @@ scale_gram_kernel(int64_t rows, int R, int64_t rb, TA* __restrict__ H,
     for (int e = tid; e < nr * R; e += blockDim.x) {
       int lr = e / R, r = e - lr * R;
       int64_t gi = (c0 + lr) * R + r;
-      double l = s_lam[r];
+      const double il = s_lam[r];
       TA v = H[gi];
       if (do_scale) {
-        v = l > 0.0 ? (TA)((double)v / l) : TA(0);
+        v = (TA)((double)v * il);  // zero column (lambda 0): stays 0
         H[gi] = v;
       }
       s_rows[lr * R + r] = v;
@@ -314,8 +314,10 @@ cudaError_t launch_gram_hadamard(const double* G, int N, int n, int R, double* S
   return cudaGetLastError();
 }
 
+// row blocks of the general-path normalisation / Gram kernels: 8 rows each up
+// to 256 blocks (few-row factors still spread over many SMs)
 int rowblocks(int64_t rows) {
-  int64_t b = (rows + 31) / 32;
+  int64_t b = (rows + 7) / 8;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 256));
 }
 

@@ -156,6 +156,72 @@ nls_pgd_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
   for (int r = 0; r < R; ++r) H[i * R + r] = rowv(hv, r);
 }
 
+// Projected gradient with one warp per row (R <= 64; used when the factor has
+// few rows, so that one thread per row would leave the GPU idle): lane l owns
+// columns l and l + 32; each step forms g = S h - m from the row's iterate,
+// broadcast from shared memory, and column l of S (S is symmetric, so lanes
+// read consecutive words), then h = max(0, h - eta g) with eta = 1 / ||S||_F.
+constexpr int PGDW_WARPS = 8;
+
+template <typename TA>
+__global__ void __launch_bounds__(32 * PGDW_WARPS)
+nls_pgd_warp_kernel(int64_t rows, int R, const double* __restrict__ S,
+                    const TA* __restrict__ M, TA* __restrict__ H,
+                    const double* __restrict__ lam, int steps) {
+  constexpr int RP = 64;
+  __shared__ __align__(16) TA Ss[RP * RP];
+  __shared__ TA hw[PGDW_WARPS][RP];
+  __shared__ double s_f[PGDW_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double f = 0.0;
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+    const int i = e / RP, j = e - i * RP;
+    const double v = (i < R && j < R) ? S[i * R + j] : 0.0;
+    Ss[e] = (TA)v;
+    f = fma(v, v, f);
+  }
+  f = warp_sum(f);
+  if (lane == 0) s_f[warp] = f;
+  __syncthreads();
+  f = 0.0;
+#pragma unroll
+  for (int w = 0; w < PGDW_WARPS; ++w) f += s_f[w];
+  const int64_t row = (int64_t)blockIdx.x * PGDW_WARPS + warp;
+  if (row >= rows) return;  // (no block-wide barrier follows)
+  const TA eta = (TA)(1.0 / fmax(sqrt(f), 1e-300));
+  const int c0 = lane, c1 = lane + 32;
+  const bool v0 = c0 < R, v1 = c1 < R;
+  TA h0 = v0 ? (TA)((double)H[row * R + c0] * (lam ? lam[c0] : 1.0)) : TA(0);
+  TA h1 = v1 ? (TA)((double)H[row * R + c1] * (lam ? lam[c1] : 1.0)) : TA(0);
+  const TA m0 = v0 ? M[row * R + c0] : TA(0), m1 = v1 ? M[row * R + c1] : TA(0);
+  TA* hr = hw[warp];
+  for (int st = 0; st < steps; ++st) {
+    hr[c0] = h0;
+    hr[c1] = h1;
+    __syncwarp();
+    TA g0a = TA(0), g0b = TA(0), g1a = TA(0), g1b = TA(0);
+    int k = 0;
+    for (; k + 2 <= R; k += 2) {
+      const TA ha = hr[k], hb = hr[k + 1];
+      g0a = fma(Ss[k * RP + c0], ha, g0a);
+      g1a = fma(Ss[k * RP + c1], ha, g1a);
+      g0b = fma(Ss[(k + 1) * RP + c0], hb, g0b);
+      g1b = fma(Ss[(k + 1) * RP + c1], hb, g1b);
+    }
+    if (k < R) {
+      const TA ha = hr[k];
+      g0a = fma(Ss[k * RP + c0], ha, g0a);
+      g1a = fma(Ss[k * RP + c1], ha, g1a);
+    }
+    __syncwarp();  // the iterate is read by every lane before it is overwritten
+    const TA x0 = h0 - eta * ((g0a + g0b) - m0), x1 = h1 - eta * ((g1a + g1b) - m1);
+    h0 = v0 && x0 > TA(0) ? x0 : TA(0);
+    h1 = v1 && x1 > TA(0) ? x1 : TA(0);
+  }
+  if (v0) H[row * R + c0] = h0;
+  if (v1) H[row * R + c1] = h1;
+}
+
 // ---- ADMM (Eq. admmupd) --------------------------------------------------------------
 // Scratch layout (doubles): [0] rho, [1] 1 if a pivot was not positive, [8 ..) W = (S + rho I)^{-1}
 // (R x R, FP64), then W as TA, then per-step per-block norm partials.
@@ -1038,8 +1104,13 @@ cudaError_t run_rowwise(const NlsArgs& a, cudaStream_t st) {
       note_launches(1);
       break;
     case PLANC_PGD:
-      nls_pgd_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(a.rows, a.R, a.S, M, H, a.lambda,
+      if (RP == 64 && a.rows <= 8192)  // few rows, wide rows: one warp per row
+        nls_pgd_warp_kernel<TA><<<(unsigned)((a.rows + PGDW_WARPS - 1) / PGDW_WARPS),
+                                  32 * PGDW_WARPS, 0, st>>>(a.rows, a.R, a.S, M, H, a.lambda,
                                                              std::max(1, a.opts.pgd_steps));
+      else
+        nls_pgd_kernel<TA, RP><<<blocks, ROWS_PER_CTA, 0, st>>>(a.rows, a.R, a.S, M, H, a.lambda,
+                                                               std::max(1, a.opts.pgd_steps));
       note_launches(1);
       break;
     case PLANC_ADMM: {
