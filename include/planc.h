@@ -307,7 +307,9 @@ planc_solve_opts planc_solve_opts_default(void);
  * (2 passes over X for any N) and the multi-TTV chains are recomputed per
  * mode; nothing else is stored.  The loss uses the identity
  * f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1, evaluated in
- * FP64.  Overwrites the context's lambda buffer (the next solve resets it).
+ * FP64; ||X||^2 is computed on the context's first call with a loss and
+ * reused (X is unchanged while the context lives).  Overwrites the context's
+ * lambda buffer (the next solve resets it).
  * Asynchronous when loss is NULL; synchronises the stream otherwise.
  * Errors: PLANC_E_INVALID (NULL pointers), PLANC_E_UNSUPPORTED (R > 64). */
 planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH,

@@ -124,8 +124,11 @@ cudaError_t launch_fit(int R, const double* Gall, int N, const double* lambda,
 cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, const void* H,
                               const double* lambda, double* dot_part, int nblk,
                               cudaStream_t st);
-cudaError_t launch_cp_grad_rows(bool f64, int64_t rows, int R, const void* H, const double* S,
-                                void* G, cudaStream_t st);
+// dH^(n) = 2 (H^(n) S^(n) - M^(n)) for all N modes in one launch (S^(n) from
+// the Grams: FP32 copies G32 for FP32 factors, G64 for FP64)
+cudaError_t launch_cp_grad_all(bool f64, int N, const int64_t* rows, int R,
+                               void* const* H, void* const* dH, const double* G64,
+                               const float* G32, int sm_count, cudaStream_t st);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st);
 
 // outer acceleration of the Nesterov-type solve: every factor of the model,
@@ -265,6 +268,7 @@ struct planc_ctx {
   double* Sm = nullptr;                  // R x R
   double* lam = nullptr;                 // R
   double* scal = nullptr;                // [0] alpha, [1..] scratch
+  double grad_alpha = -1.0;              // ||X||^2 for planc_cp_grad's loss (< 0: not yet)
   double* hist = nullptr;                // per-iteration rel. error (device)
   int hist_cap = 0;
   double* red = nullptr;                 // reduction partials

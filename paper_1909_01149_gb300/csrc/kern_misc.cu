@@ -251,18 +251,32 @@ dot_lambda_kernel(int64_t rows, int R, int64_t rb, const TA* __restrict__ M,
 }
 
 // ---- CP-loss gradient (Eq. nncp objective) -------------------------------------------
-// G[i, r] <- 2 (sum_k H[i, k] S[k, r] - G[i, r]) for an I x R block whose G
-// holds M^(n) on entry: df/dH^(n) = 2 (H^(n) S^(n) - M^(n)).  S (R x R, FP64)
-// is staged in shared memory in the factor precision.
+// dH^(n) = 2 (H^(n) S^(n) - M^(n)) for every mode in one launch (blockIdx.y =
+// n): each CTA forms S^(n), the Hadamard product of the other modes' Grams
+// (FP32 copies for FP32 factors, FP64 otherwise), in shared memory first.
+struct GradModes {
+  int64_t rows[PLANC_MAX_N];
+  const void* H[PLANC_MAX_N];
+  void* G[PLANC_MAX_N];  // in: M^(n); out: the gradient
+};
+
 template <typename TA>
-__global__ void __launch_bounds__(256)
-cp_grad_rows_kernel(int64_t rows, int R, const TA* __restrict__ H, const double* __restrict__ S,
-                    TA* __restrict__ G) {
+__global__ void cp_grad_all_kernel(GradModes gm, int N, int R, const double* __restrict__ G64,
+                                   const float* __restrict__ G32) {
   extern __shared__ __align__(16) unsigned char cg_smem[];
   TA* Ss = reinterpret_cast<TA*>(cg_smem);
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ss[e] = (TA)S[e];
+  const int n = blockIdx.y;
+  const int RR = R * R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    TA v = TA(1);
+    for (int k = 0; k < N; ++k)
+      if (k != n) v *= sizeof(TA) == 4 ? (TA)G32[(size_t)k * RR + e] : (TA)G64[(size_t)k * RR + e];
+    Ss[e] = v;
+  }
   __syncthreads();
-  const int64_t total = rows * (int64_t)R;
+  const TA* H = static_cast<const TA*>(gm.H[n]);
+  TA* Gd = static_cast<TA*>(gm.G[n]);
+  const int64_t total = gm.rows[n] * (int64_t)R;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / R;
@@ -270,7 +284,7 @@ cp_grad_rows_kernel(int64_t rows, int R, const TA* __restrict__ H, const double*
     const TA* h = H + i * R;
     TA acc = TA(0);
     for (int k = 0; k < R; ++k) acc = fma(h[k], Ss[k * R + r], acc);
-    G[e] = TA(2) * (acc - G[e]);
+    Gd[e] = TA(2) * (acc - Gd[e]);
   }
 }
 
@@ -387,16 +401,23 @@ cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_cp_grad_rows(bool f64, int64_t rows, int R, const void* H, const double* S,
-                                void* G, cudaStream_t st) {
-  const int64_t total = rows * (int64_t)R;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+cudaError_t launch_cp_grad_all(bool f64, int N, const int64_t* rows, int R,
+                               void* const* H, void* const* dH, const double* G64,
+                               const float* G32, int sm_count, cudaStream_t st) {
+  GradModes gm{};
+  int64_t maxel = 1;
+  for (int n = 0; n < N; ++n) {
+    gm.rows[n] = rows[n];
+    gm.H[n] = H[n];
+    gm.G[n] = dH[n];
+    maxel = std::max<int64_t>(maxel, rows[n] * R);
+  }
+  const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((maxel + 255) / 256, 4LL * sm_count));
+  const dim3 grid(bx, N);
   if (f64)
-    cp_grad_rows_kernel<double><<<blocks, 256, (size_t)R * R * 8, st>>>(
-        rows, R, (const double*)H, S, (double*)G);
+    cp_grad_all_kernel<double><<<grid, 256, (size_t)R * R * 8, st>>>(gm, N, R, G64, G32);
   else
-    cp_grad_rows_kernel<float><<<blocks, 256, (size_t)R * R * 4, st>>>(
-        rows, R, (const float*)H, S, (float*)G);
+    cp_grad_all_kernel<float><<<grid, 256, (size_t)R * R * 4, st>>>(gm, N, R, G64, G32);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -960,8 +960,10 @@ planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH, doubl
                         nullptr, nullptr)) != PLANC_OK)
       return st;
   if (loss) {
-    // f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1  (lambda = 1)
-    if ((st = planc_sqnorm(ctx, ctx->scal)) != PLANC_OK) return st;
+    // f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1  (lambda = 1);
+    // ||X||^2 once per context (X is borrowed unchanged; the context's scalar
+    // slot 0 only ever holds it)
+    if (ctx->grad_alpha < 0.0 && (st = planc_sqnorm(ctx, ctx->scal)) != PLANC_OK) return st;
     CK(launch_fill(ctx->lam, 1.0, R, ctx->stream), "fill launch");
     const int64_t rows = ctx->dims[N - 1];
     const int nb = rowblocks(rows);
@@ -972,15 +974,15 @@ planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH, doubl
     CK(launch_fit(R, ctx->G, N, ctx->lam, dotp, nb, ctx->scal, ctx->scal + 8, ctx->stream),
        "fit launch");
   }
-  for (int n = 0; n < N; ++n) {
-    CK(launch_gram_hadamard(ctx->G, N, n, R, ctx->Sm, ctx->stream), "gram_hadamard launch");
-    CK(launch_cp_grad_rows(is_f64(ctx), ctx->dims[n], R, H[n], ctx->Sm, dH[n], ctx->stream),
-       "gradient launch");
-  }
+  // every mode's gradient rows in one launch (S^(n) formed per CTA)
+  CK(launch_cp_grad_all(is_f64(ctx), N, ctx->dims, R, H, dH, ctx->G, ctx->Gf, ctx->sm_count,
+                        ctx->stream),
+     "gradient launch");
   if (loss) {
     double h[11] = {0};
     CK(cudaMemcpyAsync(h, ctx->scal, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->grad_alpha = h[0];
     *loss = h[0] - 2.0 * h[9] + h[10];
   }
   return PLANC_OK;

@@ -131,3 +131,20 @@ def test_cp_grad_rejects_bad_arguments():
             ctx.cp_grad(Hd[:2])
         with pytest.raises((ValueError, p.PlancError)):
             ctx.cp_grad(Hd, [torch.rand(d, R + 1, device="cuda") for d in dims])
+
+
+def test_cp_grad_repeated_calls_reuse_the_norm():
+    """||X||^2 is computed on the first call with a loss and reused: later
+    calls, also after a solve on the same context, give the oracle's loss."""
+    dims, R = (10, 13, 9), 3
+    p, Xd, Xs, Hd, Hs = _setup(dims, R, "f64", seed=11)
+    ref = o.cp_loss(Xs, Hs)
+    with p.Context(Xd, dims, R) as ctx:
+        l1, _ = ctx.cp_grad(Hd)
+        l2, g2 = ctx.cp_grad(Hd)
+        Hs2 = [h.clone() for h in Hd]
+        ctx.solve(Hs2, "hals", 2)
+        l3, g3 = ctx.cp_grad(Hd)
+    assert abs(l1 - ref) <= 1e-10 * abs(ref) and l2 == l1 and l3 == l1
+    for a, b in zip(g2, g3):
+        assert torch.equal(a, b)
