@@ -129,6 +129,10 @@ cudaError_t launch_dot_lambda(bool f64, int64_t rows, int R, const void* M, cons
 cudaError_t launch_cp_grad_all(bool f64, int N, const int64_t* rows, int R,
                                void* const* H, void* const* dH, const double* G64,
                                const float* G32, int sm_count, cudaStream_t st);
+// G^(n) = H^(n)T H^(n) for all N modes in one launch (FP64 and the FP32
+// copy; a loop over the rows per entry: for factors with few rows)
+cudaError_t launch_gram_all(bool f64, int N, const int64_t* rows, int R, void* const* H,
+                            double* G, float* Gf, cudaStream_t st);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t st);
 
 // outer acceleration of the Nesterov-type solve: every factor of the model,

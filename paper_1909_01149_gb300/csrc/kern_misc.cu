@@ -250,6 +250,37 @@ dot_lambda_kernel(int64_t rows, int R, int64_t rb, const TA* __restrict__ M,
   }
 }
 
+// G^(n) = H^(n)T H^(n) for every mode in one launch (blockIdx.y = n), one
+// thread per entry looping over the rows: FP32 products over 32-row chunks,
+// FP64 across chunks (the precision of the block-partial path), written in
+// FP64 and as the FP32 copy.  For factors with few rows (the loop is per
+// thread).
+struct GramModes {
+  int64_t rows[PLANC_MAX_N];
+  const void* H[PLANC_MAX_N];
+};
+
+template <typename TA>
+__global__ void gram_all_kernel(GramModes gm, int R, double* __restrict__ G,
+                                float* __restrict__ Gf) {
+  const int n = blockIdx.y;
+  const int RR = R * R;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= RR) return;
+  const int r = e / R, s = e - (e / R) * R;
+  const TA* H = static_cast<const TA*>(gm.H[n]);
+  const int64_t rows = gm.rows[n];
+  double g = 0.0;
+  for (int64_t i0 = 0; i0 < rows; i0 += 32) {
+    TA a = TA(0);
+    const int64_t i1 = min(rows, i0 + 32);
+    for (int64_t i = i0; i < i1; ++i) a = fma(H[i * R + r], H[i * R + s], a);
+    g += (double)a;
+  }
+  G[(size_t)n * RR + e] = g;
+  if (Gf) Gf[(size_t)n * RR + e] = (float)g;
+}
+
 // ---- CP-loss gradient (Eq. nncp objective) -------------------------------------------
 // dH^(n) = 2 (H^(n) S^(n) - M^(n)) for every mode in one launch (blockIdx.y =
 // n): each CTA forms S^(n), the Hadamard product of the other modes' Grams
@@ -418,6 +449,20 @@ cudaError_t launch_cp_grad_all(bool f64, int N, const int64_t* rows, int R,
     cp_grad_all_kernel<double><<<grid, 256, (size_t)R * R * 8, st>>>(gm, N, R, G64, G32);
   else
     cp_grad_all_kernel<float><<<grid, 256, (size_t)R * R * 4, st>>>(gm, N, R, G64, G32);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_all(bool f64, int N, const int64_t* rows, int R, void* const* H,
+                            double* G, float* Gf, cudaStream_t st) {
+  GramModes gm{};
+  for (int n = 0; n < N; ++n) {
+    gm.rows[n] = rows[n];
+    gm.H[n] = H[n];
+  }
+  const dim3 grid((unsigned)((R * R + 255) / 256), (unsigned)N);
+  if (f64) gram_all_kernel<double><<<grid, 256, 0, st>>>(gm, R, G, Gf);
+  else gram_all_kernel<float><<<grid, 256, 0, st>>>(gm, R, G, Gf);
   note_launches(1);
   return cudaGetLastError();
 }

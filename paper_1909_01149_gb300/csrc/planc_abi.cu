@@ -955,10 +955,15 @@ planc_status_t planc_cp_grad(planc_t ctx, void* const* H, void* const* dH, doubl
   // each and the multi-TTV chains are recomputed per mode (Alg. 3 with the
   // factors held fixed), so no node is kept beyond its branch
   if ((st = planc_mttkrp_all(ctx, H, dH)) != PLANC_OK) return st;
-  for (int k = 0; k < N; ++k)
-    if ((st = gram_impl(ctx, ctx->dims[k], H[k], ctx->G + (size_t)k * R * R, nullptr, false,
-                        nullptr, nullptr)) != PLANC_OK)
-      return st;
+  if (ctx->max_dim <= 4096) {  // every Gram in one launch (a row loop per entry)
+    CK(launch_gram_all(is_f64(ctx), N, ctx->dims, R, H, ctx->G, ctx->Gf, ctx->stream),
+       "Gram launch");
+  } else {
+    for (int k = 0; k < N; ++k)
+      if ((st = gram_impl(ctx, ctx->dims[k], H[k], ctx->G + (size_t)k * R * R, nullptr, false,
+                          nullptr, nullptr)) != PLANC_OK)
+        return st;
+  }
   if (loss) {
     // f = ||X||^2 - 2 <M^(N), H^(N)> + 1^T (G^(1) * ... * G^(N)) 1  (lambda = 1);
     // ||X||^2 once per context (X is borrowed unchanged; the context's scalar
