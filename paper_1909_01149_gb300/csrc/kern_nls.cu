@@ -421,16 +421,52 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
   // lanes then spreads over the banks (stride R put every lane on one bank)
   const int LD = R + 1;
   double* Ss = bsm;                                   // R x R (stride LD)
+  double* Ws = bsm + R * LD;                          // S^{-1} (stride LD; R <= 32)
+  double* colk = Ws + R * LD;                         // 64: a column of the inversion
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* A = bsm + R * LD + (size_t)warp * (R * LD + 3 * 64);  // f x f (stride LD)
+  double* A = colk + 64 + (size_t)warp * (R * LD + 3 * 64);  // f x f (stride LD)
   double* xs = A + R * LD;                             // 64: passive solution / rhs
   double* zs = xs + 64;                                // 64: full x
   double* dinv = zs + 64;                              // 64: 1 / pivot
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     const int a = e / R, b = e - a * R;
     Ss[a * LD + b] = S[e];
+    if (RMAX > 16) Ws[a * LD + b] = S[e];
+  }
+  // R <= 32: W = S^{-1} in place by Gauss-Jordan elimination (no pivoting: S
+  // is symmetric positive definite; R steps of a rank-1 update spread over
+  // the CTA, FP64, reciprocals from an FP32 seed and two Newton steps).  A
+  // pivot that is not positive leaves W unused (every row then factors S_FF).
+  // (R <= 16: the register factorisation of S_FF alone was faster on the
+  // 4-way mouse-like workload; the inverse pays from R = 32)
+  constexpr bool WPATH = RMAX > 16;
+  __shared__ int s_wbad;
+  if (threadIdx.x == 0) s_wbad = 0;
+  if (WPATH) {
+    for (int k = 0; k < R; ++k) {
+      __syncthreads();
+      const double p = Ws[k * LD + k];
+      if (!(p > 0.0)) {
+        if (threadIdx.x == 0) s_wbad = 1;
+        break;  // uniform: every thread read the same pivot
+      }
+      double ip = (double)(1.0f / (float)p);
+      ip = ip * (2.0 - p * ip);
+      ip = ip * (2.0 - p * ip);
+      for (int i = threadIdx.x; i < R; i += blockDim.x) colk[i] = Ws[i * LD + k];
+      __syncthreads();
+      // row k scaled (its pivot entry becomes 1 / p), then every other row
+      for (int j = threadIdx.x; j < R; j += blockDim.x)
+        Ws[k * LD + j] = (j == k ? 1.0 : Ws[k * LD + j]) * ip;
+      __syncthreads();
+      for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int i = e / R, j = e - (e / R) * R;
+        if (i != k) Ws[i * LD + j] = fma(-colk[i], Ws[k * LD + j], j == k ? 0.0 : Ws[i * LD + j]);
+      }
+    }
   }
   __syncthreads();
+  const bool use_w = WPATH && s_wbad == 0;
   const int64_t row = (int64_t)blockIdx.x * BPP_WARPS + warp;
   if (row >= rows) return;
 
@@ -576,6 +612,78 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     return false;
   };
 
+  // S^{-1} path (R <= 32, the inverse given): with W = S^{-1}, the passive
+  // solution is x_F = u_F - W_FG z, where u = W m_F (m taken as zero on the
+  // inactive set G) and W_GG z = u_G: the inverse of a principal submatrix
+  // from the Schur complement of W.  Only the g x g system of G is solved
+  // (g <= 8, FP64 Gauss-Jordan with the rows on lanes, reciprocals from an
+  // FP32 seed and two Newton steps); false (a non-positive pivot) hands the
+  // system to the factorisation of S_FF.
+  constexpr int GMAX = 8;
+  auto recip = [](double d) {
+    double y = (double)(1.0f / (float)d);
+    y = y * (2.0 - d * y);
+    return y * (2.0 - d * y);
+  };
+  auto solve_w = [&](int g, bool in0) -> bool {
+    if (v0) zs[j0] = in0 ? m0 : 0.0;
+    __syncwarp();
+    double u = 0.0;
+    if (v0)
+      for (int k = 0; k < R; ++k) u = fma(Ws[j0 * LD + k], zs[k], u);
+    __syncwarp();
+    if (g == 0) {
+      x0 = in0 ? u : 0.0;
+      return true;
+    }
+    int* gl = reinterpret_cast<int*>(xs);  // the inactive indices in order
+    const uint64_t Gm = ~F & ((1ull << R) - 1ull);
+    if (v0 && !in0) gl[__popcll(Gm & ((1ull << j0) - 1ull))] = j0;
+    __syncwarp();
+    const bool rw = lane < g;
+    const int gi = rw ? gl[lane] : 0;
+    double a[GMAX];
+#pragma unroll
+    for (int k = 0; k < GMAX; ++k) a[k] = (rw && k < g) ? Ws[gi * LD + gl[k]] : 0.0;
+    double b = __shfl_sync(0xffffffffu, u, gi);
+    double dg = 1.0;
+    bool good = true;
+#pragma unroll
+    for (int c = 0; c < GMAX; ++c) {
+      if (c < g) {
+        const double piv = __shfl_sync(0xffffffffu, a[c], c);
+        if (!(piv > 0.0)) good = false;
+        const double ip = recip(good ? piv : 1.0);
+        const double bc = __shfl_sync(0xffffffffu, b, c);
+        double ac[GMAX];
+#pragma unroll
+        for (int k = 0; k < GMAX; ++k) ac[k] = __shfl_sync(0xffffffffu, a[k], c);
+        if (lane == c) {
+          dg = piv;
+        } else {
+          const double fct = a[c] * ip;
+#pragma unroll
+          for (int k = 0; k < GMAX; ++k)
+            if (k > c) a[k] = fma(-fct, ac[k], a[k]);
+          b = fma(-fct, bc, b);
+        }
+      }
+    }
+    if (!good) {
+      __syncwarp();
+      return false;
+    }
+    const double z = rw ? b * recip(dg) : 0.0;
+    double corr = 0.0;
+    for (int i = 0; i < g; ++i) {
+      const double zi = __shfl_sync(0xffffffffu, z, i);
+      if (v0) corr = fma(Ws[j0 * LD + gl[i]], zi, corr);
+    }
+    __syncwarp();  // gl read by every lane before the scratch is reused
+    x0 = in0 ? u - corr : 0.0;
+    return true;
+  };
+
   // x_F = S_FF^{-1} m_F, x_G = 0; y = S x - m on G, 0 on F
   auto solve = [&]() {
     const int f = __popcll(F);
@@ -588,6 +696,7 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     x0 = 0.0;
     x1 = 0.0;
     if constexpr (RMAX > 0) {
+      if (!done && use_w && R - f <= GMAX && R - f <= f) done = solve_w(R - f, in0);
       if (!done) done = solve_reg(f, p0, in0);
     }
     if (!done && RMAX == 0 && sizeof(TA) == 4) {
@@ -1175,7 +1284,7 @@ cudaError_t run_nls_t(const NlsArgs& a, cudaStream_t st) {
   if (a.alg == PLANC_BPP) {
     const int blocks = (int)((a.rows + BPP_WARPS - 1) / BPP_WARPS);
     const size_t rl = (size_t)a.R * (a.R + 1);  // R x R with leading dimension R + 1
-    size_t smem = (rl + BPP_WARPS * (rl + 3 * 64)) * sizeof(double);
+    size_t smem = (2 * rl + 64 + BPP_WARPS * (rl + 3 * 64)) * sizeof(double);
     cudaFuncSetAttribute(nls_bpp_kernel<TA, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     if constexpr (sizeof(TA) == 4) {

@@ -725,8 +725,9 @@ planc_status_t outer_iteration(planc_t ctx, const planc_solve_opts& o, void* con
         }
       }
       if (o.alg == PLANC_BPP) {
-        // BPP solves the rows (one warp each, FP64 passive-set Cholesky); the
-        // cluster launch below then does the rest of the mode
+        // BPP solves the rows (one warp each; the passive systems through
+        // S^{-1} or a factorisation); the cluster launch below then does the
+        // rest of the mode
         NlsArgs a;
         a.alg = PLANC_BPP;
         a.opts = o.nls;
