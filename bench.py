@@ -509,9 +509,13 @@ def run_algs(args, cfg):
 
 def run_batch(args):
     """256 uneven 3-way instances (I_n ~ U{32..160}, R ~ U{8..32}, planted + 2%
-    noise), HALS 25 outer iterations each: one planc_batch_solve call (all
-    phases batched, one CUDA graph) against a loop of per-instance solves
-    (contexts built before timing).  FP32 and BF16 storage."""
+    noise), HALS 25 outer iterations each: one planc_batch_solve call as the
+    single persistent launch (the default), the same call as one launch per
+    phase over all instances (one CUDA graph), and a loop of per-instance
+    solves (contexts built before timing).  FP32 and BF16 storage.  Times are
+    host wall clock around whole calls (workspace, tables, launch, results),
+    median of the steps; the batched solve's HBM figure counts two X passes
+    per outer iteration (the partial MTTKRPs' algorithmic bytes)."""
     import torch
     from paper_1909_01149_gb300 import planc, synth
     torch.cuda.set_device(0)
@@ -521,21 +525,31 @@ def run_batch(args):
     log(f"batch of {count} generated in {time.time() - t0:.1f}s")
     H0 = [synth.init_factors(X.shape, R, 2000 + i) for i, (X, _, R) in enumerate(insts)]
     elems = sum(int(np.prod(X.shape)) for X, _, _ in insts)
+    peak, peak_kind = measured_peak()
     out = {"mode": "batch", "workload": "nncp-batch-256x3way-U32..160-R8..32-hals25",
            "instances": count, "outer_iters_each": iters, "tensor_elements": elems}
     for dtn, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
         Xd = [torch.from_numpy(synth.flat(X)).to(dt).cuda() for X, _, _ in insts]
+        es = 4 if dtn == "f32" else 2
+
         def fresh():
             return [[torch.from_numpy(h).float().cuda() for h in H] for H in H0]
-        for _ in range(max(1, args.warmup)):
-            planc.batch_solve(Xd, fresh(), "hals", iters)
-        Hs = [fresh() for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            res, rep = planc.batch_solve(Xd, Hs[k], "hals", iters)
-        torch.cuda.synchronize()
-        tb = (time.perf_counter() - t0) / args.steps
+
+        def timed(persistent):
+            for _ in range(max(1, args.warmup)):
+                planc.batch_solve(Xd, fresh(), "hals", iters, persistent=persistent)
+            Hs = [fresh() for _ in range(args.steps)]
+            ts = []
+            for k in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res, rep = planc.batch_solve(Xd, Hs[k], "hals", iters, persistent=persistent)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            return statistics.median(ts), res, rep
+
+        tb, res, rep = timed(True)
+        tp, res_p, rep_p = timed(False)
         # per-instance loop (the single-instance API, one solve per tensor)
         ctxs = [planc.Context(x, X.shape, R) for x, (X, _, R) in zip(Xd, insts)]
         Hl = fresh()
@@ -550,25 +564,27 @@ def run_batch(args):
         tl = time.perf_counter() - t0
         for c in ctxs:
             c.close()
-        out[dtn] = {"batched_s": round(tb, 4), "loop_s": round(tl, 4),
+        gbs = 2.0 * iters * elems * es / tb / 1e9
+        out[dtn] = {"batched_s": round(tb, 5), "per_phase_s": round(tp, 5), "loop_s": round(tl, 4),
                     "batched_inst_iters_per_s": round(count * iters / tb, 1),
+                    "per_phase_inst_iters_per_s": round(count * iters / tp, 1),
                     "loop_inst_iters_per_s": round(count * iters / tl, 1),
-                    "speedup": round(tl / tb, 2), "launches_per_solve": rep["launches"],
+                    "speedup_vs_loop": round(tl / tb, 2), "speedup_vs_per_phase": round(tp / tb, 2),
+                    "launches_per_solve": rep["launches"],
+                    "per_phase_launches_per_solve": rep_p["launches"],
+                    "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
+                            "bytes": "two X passes per outer iteration"},
                     "max_final_rel_err": round(max(r["final"] for r in res), 6),
+                    "max_final_diff_vs_per_phase": float(max(
+                        abs(a["final"] - b["final"]) for a, b in zip(res, res_p))),
                     "schedule": rep["schedule"]}
-        # each rank blocking forced (same tiles): 0 pads every rank to 32
+        # each rank blocking forced on the persistent launch: 0 pads every rank to 32
         per = {}
         for sched in ("0,0", "1,1", "2,2"):
             os.environ["PLANC_BATCH_RANK_BLOCKING"] = sched
-            planc.batch_solve(Xd, fresh(), "hals", iters)
-            Hs = [fresh() for _ in range(args.steps)]
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for k in range(args.steps):
-                planc.batch_solve(Xd, Hs[k], "hals", iters)
-            torch.cuda.synchronize()
             per[{"0,0": "pad32", "1,1": "classes16_32", "2,2": "classes8_16_32"}[sched]] = round(
-                (time.perf_counter() - t0) / args.steps, 4)
+                timed(True)[0], 5)
         os.environ.pop("PLANC_BATCH_RANK_BLOCKING", None)
         out[dtn]["batched_s_by_rank_blocking"] = per
         del Xd

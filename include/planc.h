@@ -103,6 +103,9 @@ typedef struct {
                            factor (lambda absorbed into the last mode),
                            s_i = i^(1/N), accepted iff its relative error
                            (one extra MTTKRP) is lower than iteration i's */
+  int batch_persistent; /* planc_batch_solve only: 1 (default) runs the whole
+                           solve as one persistent launch; 0 as one launch per
+                           phase over all instances */
 } planc_solve_opts;
 
 /* Result record of planc_nncp_solve (host memory). */
@@ -335,14 +338,21 @@ typedef struct {
 
 /* NNCP (Alg. 1 with the dimension tree of Alg. 3 and the normalisation and
  * error identity of Alg. 4) of `count` independent 3-way instances of
- * different sizes, all advanced together: each phase of an outer iteration
- * (left partial MTTKRP, multi-TTVs, right partial MTTKRP, the fused per-mode
- * update) is one launch over a work table of every instance's tiles (the
- * partial MTTKRPs as persistent grids, each CTA a contiguous run of tiles
- * holding an equal share of the elements), and with
- * opts.use_graph the whole solve is one CUDA graph launch.  Tile shapes of the
- * partial-MTTKRP launches are chosen by timing candidates on the first call
- * for a batch of that size (cached per process).  Requirements: each I_n in
+ * different sizes.  With opts.batch_persistent (the default) the whole solve
+ * is one persistent launch: thread-block clusters of 8 CTAs, as many as fit
+ * on the GPU at once, each solving whole instances in turn (every phase of
+ * every outer iteration: alpha, the initial Grams, left partial MTTKRP over
+ * the CTAs' row blocks, the multi-TTVs, right partial MTTKRP over the CTAs'
+ * slabs, the fused per-mode update and the error identity, separated by
+ * cluster barriers); the instances are dealt longest-first onto the
+ * least-loaded cluster by an estimate of their work.  With batch_persistent
+ * 0 each phase of an outer iteration is one launch over a work table of
+ * every instance's tiles (the partial MTTKRPs as persistent grids, each CTA
+ * a contiguous run of tiles holding an equal share of the elements).  With
+ * opts.use_graph the launch sequence is captured and run as one CUDA graph.
+ * The schedule (rank blocking of both partial MTTKRPs; per-phase launches
+ * also their tile shapes) is chosen by timing candidates on the first call
+ * for a batch of that signature (cached per process).  Requirements: each I_n in
  * 1..1024, R in 1..32, x_dtype F32 or BF16, opts.alg MU, HALS or PGD,
  * opts.tol ignored (fixed iterations).  Workspace is allocated and freed
  * inside the call.  cuda_stream NULL: a private stream is used.

@@ -211,6 +211,18 @@ struct BatchInst {
 cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, planc_nls_t alg,
                               const planc_nls_opts& o, int* err, cudaStream_t st);
 int mode_batch_max_rows();
+// The whole batched solve in one persistent launch (kern_mode.cu): nclusters
+// thread-block clusters, cluster q solving the instances clist[coff[q]] ..
+// clist[coff[q + 1] - 1] in turn (alg MU, HALS or PGD); mode 1 / 2 runs only
+// the left / right partial MTTKRPs (schedule timing).  hmax: the longest
+// second or third mode of the batch; sqpart: 8 doubles per instance.
+cudaError_t launch_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
+                                    int nclusters, int iters, planc_nls_t alg,
+                                    const planc_nls_opts& o, int sched_l, int sched_r, int mode,
+                                    int hmax, double* sqpart, int* err, cudaStream_t st);
+// clusters of the persistent launch that fit on the device at once (0 if none)
+int batch_persistent_max_clusters(planc_nls_t alg, int hmax);
+constexpr int kBatchClusterCtas = 8;  // CTAs per cluster of the persistent launch
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64);
 // the per-iteration history record (error triple and inner counts at index
 // *counter, then ++*counter), done by the last mode's fused update when given

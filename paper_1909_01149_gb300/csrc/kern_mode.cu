@@ -21,6 +21,7 @@
 // multi-kernel path.
 #include <algorithm>
 
+#include "batch_dev.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -61,6 +62,14 @@ __device__ __forceinline__ void st_cluster_t(const float* local, uint32_t rank, 
   uint32_t a = (uint32_t)__cvta_generic_to_shared(local), d;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(d), "f"(v) : "memory");
+}
+
+// a load of data that, with COH, another CTA may have written earlier in the
+// same launch: through L2 (__ldcg), never the read-only path
+template <bool COH, typename T>
+__device__ __forceinline__ T ldc(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
 }
 
 // d = sum_k h[k] * S[r][k] with S row r read by explicit vector shared-memory
@@ -180,7 +189,9 @@ __device__ __forceinline__ void tri_unpack(int p, int n, int& r, int& s) {
   s = rr + (p - tri_index(rr, rr, n));
 }
 
-template <typename TA, int RP>
+// LIN: with the landing area of the rows' bulk copies (the persistent batched
+// solve loads the rows directly and has no use for it)
+template <typename TA, int RP, bool LIN = true>
 struct McLayout {
   static constexpr int NB = RP / 4;                     // 4-column blocks
   static constexpr int NBLK = NB * (NB + 1) / 2;        // upper-triangle 4x4 tiles
@@ -193,7 +204,7 @@ struct McLayout {
   static constexpr size_t oHs = oSs + sizeof(TA) * RP * RP;
   static constexpr size_t oMs = oHs + sizeof(TA) * MC_RPC * RP;
   static constexpr size_t oLin = oMs + sizeof(TA) * MC_RPC * RP;  // bulk-copy landing area
-  static constexpr size_t oTp = oLin + sizeof(TA) * 2 * MC_RPC * RP;
+  static constexpr size_t oTp = oLin + (LIN ? sizeof(TA) * 2 * MC_RPC * RP : 0);
   static constexpr size_t oCs = oTp + sizeof(TA) * RCN * NBLK * 16;
   static constexpr size_t oGs = oCs + sizeof(double) * MC_CS * RP;
   static constexpr size_t oBeta = oGs + sizeof(double) * MC_CS * NPO;
@@ -210,7 +221,10 @@ struct McLayout {
 // ALG >= 0 fixes the update at compile time (the kernel then carries only
 // that update's code: the launch is short and runs its code cold, so code
 // size shows up as instruction-fetch stalls); ALG < 0 dispatches on alg.
-template <typename TA, int RP, int ALG = -1>
+// COH: M, H, the Grams, lambda and alpha were written earlier in the same
+// launch (the persistent batched solve), so they are read through L2 and the
+// rows are loaded directly (no bulk copies).
+template <typename TA, int RP, int ALG = -1, bool COH = false>
 __device__ __forceinline__ void mode_update_body(
     int rows, int R, int N, int n, double* __restrict__ G, float* __restrict__ Gf,
     const TA* __restrict__ M, TA* __restrict__ H, double* __restrict__ lam, int alg_rt,
@@ -218,7 +232,7 @@ __device__ __forceinline__ void mode_update_body(
     const double* __restrict__ alpha, double* __restrict__ fit_out, int* __restrict__ err,
     const double* __restrict__ nes_scr, int nes_kmax, double nes_tol,
     const RecArgs& rec = RecArgs(), int* __restrict__ nflags = nullptr) {
-  using L = McLayout<TA, RP>;
+  using L = McLayout<TA, RP, !COH>;
   using S = Swz<TA, RP>;
   const int alg = ALG >= 0 ? ALG : alg_rt;
   extern __shared__ __align__(16) unsigned char mc_smem[];
@@ -255,7 +269,7 @@ __device__ __forceinline__ void mode_update_body(
   // this CTA's rows of M and H arrive by two bulk copies when both ranges
   // start on 16 bytes and span a multiple of 16 bytes
   const uint32_t cbytes = (uint32_t)(nel * sizeof(TA));
-  const bool bulk = nel > 0 && (cbytes & 15u) == 0 &&
+  const bool bulk = !COH && nel > 0 && (cbytes & 15u) == 0 &&
                     ((reinterpret_cast<uintptr_t>(Mrow) | reinterpret_cast<uintptr_t>(Hrow)) & 15u) == 0;
 
   pdl_wait();  // the MTTKRP and the previous mode's Grams are complete
@@ -264,7 +278,7 @@ __device__ __forceinline__ void mode_update_body(
   cluster_arrive_relaxed();
   constexpr int EPT = RP * RP / MC_NT;      // entries of S per thread
 
-  const double lam_t = t < R ? lam[t] : 0.0;
+  const double lam_t = t < R ? ldc<COH>(lam + t) : 0.0;
   // owned pair of this thread (for G^(n) and gamma): p = t * MC_CS + c
   const int p_own = t * MC_CS + (int)c;
   int r_own = 0, s_own = 0;
@@ -278,7 +292,7 @@ __device__ __forceinline__ void mode_update_body(
   const bool pre = fit_out && owns && N - 1 <= QPRE;
 #pragma unroll
   for (int qi = 0; qi < QPRE; ++qi)
-    gq[qi] = (pre && qi + 1 < N) ? G[(size_t)(qi < n ? qi : qi + 1) * RR + r_own * R + s_own] : 1.0;
+    gq[qi] = (pre && qi + 1 < N) ? ldc<COH>(G + (size_t)(qi < n ? qi : qi + 1) * RR + r_own * R + s_own) : 1.0;
   // S^(n) = Hadamard of the other Grams, in TA (from the FP32 copies when TA
   // is FP32); entry (i, k) of S for e = t + j * MC_NT.  With at most QPRE
   // other modes all entries are loaded before the row copies are issued and
@@ -302,8 +316,8 @@ __device__ __forceinline__ void mode_update_body(
     for (int j = 0; j < EPT; ++j) {
       TA x = TA(1);
       if (sfast && qi + 1 < N) {
-        if constexpr (sizeof(TA) == 4) x = Gf[q * RR + off[j]];
-        else x = G[q * RR + off[j]];
+        if constexpr (sizeof(TA) == 4) x = ldc<COH>(Gf + q * RR + off[j]);
+        else x = ldc<COH>(G + q * RR + off[j]);
       }
       gl[qi][j] = x;
     }
@@ -323,8 +337,8 @@ __device__ __forceinline__ void mode_update_body(
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
       const int e = t + j * MC_NT;
-      mv[j] = e < nel ? Mrow[e] : TA(0);
-      hv[j] = e < nel ? Hrow[e] : TA(0);
+      mv[j] = e < nel ? ldc<COH>(Mrow + e) : TA(0);
+      hv[j] = e < nel ? ldc<COH>(Hrow + e) : TA(0);
     }
   }
   if (sfast) {
@@ -337,8 +351,8 @@ __device__ __forceinline__ void mode_update_body(
       const size_t q = (size_t)(qi < n ? qi : qi + 1);
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        if constexpr (sizeof(TA) == 4) v[j] *= Gf[q * RR + off[j]];
-        else v[j] *= G[q * RR + off[j]];
+        if constexpr (sizeof(TA) == 4) v[j] *= ldc<COH>(Gf + q * RR + off[j]);
+        else v[j] *= ldc<COH>(G + q * RR + off[j]);
       }
     }
   }
@@ -744,7 +758,7 @@ __device__ __forceinline__ void mode_update_body(
         for (int qi = 0; qi < QPRE; ++qi) sv *= gq[qi];
       } else {
         for (int q = 0; q < N; ++q)
-          if (q != n) sv *= G[(size_t)q * RR + r * R + s];
+          if (q != n) sv *= ldc<COH>(G + (size_t)q * RR + r * R + s);
       }
       gam = (r == s ? 1.0 : 2.0) * sv * gh;
     }
@@ -770,7 +784,7 @@ __device__ __forceinline__ void mode_update_body(
       gamma += gam_slot[src];
       beta += beta_slot[src];
     }
-    const double a = *alpha;
+    const double a = ldc<COH>(alpha);
     const double rad = a - 2.0 * beta + gamma;
     const double eps = a > 0.0 ? sqrt(fmax(0.0, rad) / a) : 0.0;
     fit_out[0] = eps;
@@ -855,6 +869,171 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+
+// ---- the whole batched solve in one persistent launch ---------------------------------
+// Cluster q of the grid (MC_CS CTAs) solves the instances clist[coff[q]] ..
+// clist[coff[q + 1] - 1] one after another, each through all of its outer
+// iterations: alpha = ||X||^2 and the Grams of the initial factors, then per
+// iteration (Alg. 1 with the dimension tree of Alg. 3, N = 3, S = 2)
+//   T^{1:2} = X_(1:2) H^(3)  over the CTAs' row blocks  -> M^(1) = T x_2 H^(2)
+//   -> update of mode 1 -> M^(2) = T x_1 H^(1) -> update of mode 2
+//   -> M^(3) = X_(1:2)^T (H^(2) . H^(1)) over the CTAs' slabs -> update of
+//   mode 3 and the error identity of Alg. 4 (Sec. A.2) into the history,
+// with the same device code as the per-phase kernels.  Consecutive phases are
+// separated by cluster barriers (release / acquire at cluster scope, so one
+// phase's global writes are visible to the next); no CTA ever waits on
+// another cluster, so the launch needs no flag, no spin and no device-wide
+// barrier.  mode 1 / 2 run only the left / right partial MTTKRP of every
+// assigned instance at the current factors (timed by the schedule tuner;
+// they leave the factors as they are).  sqpart: MC_CS doubles per instance.
+constexpr int PB_MINB = 2;  // CTAs per SM the persistent kernel is compiled for (the update needs ~200 registers)
+
+__device__ __forceinline__ void cluster_sync_all() {
+  cluster_arrive();
+  cluster_wait();
+}
+
+size_t batch_persistent_smem(int hmax) {
+  return std::max(McLayout<float, 32, false>::bytes, bdev::pm_smem_bytes(hmax));
+}
+
+template <int ALG>
+__global__ void __launch_bounds__(MC_NT, PB_MINB)
+batch_solve_kernel(const BatchInst* __restrict__ tab, const int* __restrict__ clist,
+                   const int* __restrict__ coff, int iters, double mu_eps, int pgd_steps,
+                   int sched_l, int sched_r, int mode, double* __restrict__ sqpart,
+                   int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char mc_smem[];
+  __shared__ double sred[MC_NT / 32];
+  // the contractions' staged column and partial sums use the start of the
+  // dynamic area, which no other phase holds while they run
+  float* hcol = reinterpret_cast<float*>(mc_smem);                  // <= 1024 floats
+  float* cpart = reinterpret_cast<float*>(mc_smem + 1024 * sizeof(float));  // MC_NT floats
+  const int q = (int)(blockIdx.x / MC_CS);
+  const int c = (int)cluster_rank();
+  const int t = threadIdx.x;
+  for (int j = coff[q]; j < coff[q + 1]; ++j) {
+    const int bi = clist[j];
+    const BatchInst& b = tab[bi];
+    const int R = b.R;
+    const int64_t L = b.I[0] * b.I[1];
+    const int I3 = (int)b.I[2];
+    // this CTA's left items (row blocks of 2 MC_NT rows) and right items (slabs)
+    const int nyl = (int)((L + 2 * MC_NT - 1) / (2 * MC_NT));
+    const int yl0 = nyl * c / MC_CS, yl1 = nyl * (c + 1) / MC_CS;
+    const int yr0 = I3 * c / MC_CS, yr1 = I3 * (c + 1) / MC_CS;
+    auto item = [bi](int y) { return make_int2(bi, y); };
+    if (mode != 0) {
+      if (mode == 1) bdev::pm_left_run<MC_NT>(tab, item, yl0, yl1, sched_l, mc_smem);
+      else bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem);
+      cluster_sync_all();
+      continue;
+    }
+    {  // alpha: FP64 partial of this CTA's share of the elements, summed in CTA order
+      const int64_t n = L * I3;
+      const int64_t e0 = n * c / MC_CS, e1 = n * (c + 1) / MC_CS;
+      double acc = 0.0;
+#pragma unroll 4
+      for (int64_t e = e0 + t; e < e1; e += MC_NT) {
+        const float x = bdev::ldx(b, e);
+        acc += (double)(x * x);
+      }
+      acc = warp_sum(acc);
+      if ((t & 31) == 0) sred[t >> 5] = acc;
+      __syncthreads();
+      if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < MC_NT / 32; ++w) s += sred[w];
+        sqpart[(size_t)bi * MC_CS + c] = s;
+      }
+    }
+    for (int e = c * MC_NT + t; e < 3 * R * R; e += MC_CS * MC_NT)
+      bdev::initial_gram_entry(b, e / (R * R), e % (R * R));
+    if (c == 0 && t < 32) b.lam[t] = 1.0;  // lambda starts at 1
+    cluster_sync_all();
+    if (c == 0 && t == 0) {  // read next by this thread, in the mode-3 update
+      double s = 0.0;
+      for (int k = 0; k < MC_CS; ++k) s += __ldcg(sqpart + (size_t)bi * MC_CS + k);
+      *b.alpha = s;
+    }
+    for (int it = 0; it < iters; ++it) {
+      for (int n = 0; n < 3; ++n) {
+        if (n == 0) {
+          bdev::pm_left_run<MC_NT>(tab, item, yl0, yl1, sched_l, mc_smem);
+          cluster_sync_all();
+          for (int r = c; r < R; r += MC_CS) bdev::contract_rest_item<MC_NT>(b, r, hcol, cpart);
+        } else if (n == 1) {
+          for (int r = c; r < R; r += MC_CS) bdev::contract_first_item<MC_NT>(b, r, hcol);
+        } else {
+          bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem);
+        }
+        cluster_sync_all();  // M^(n) complete
+        mode_update_body<float, 32, ALG, true>((int)b.I[n], R, 3, n, b.G, b.Gf, b.M, b.H[n], b.lam,
+                                               ALG, mu_eps, pgd_steps, 1e-30, b.inner + 3 * it + n,
+                                               b.alpha, n == 2 ? b.hist + 3 * it : nullptr, err,
+                                               nullptr, 0, 0.0);
+        cluster_sync_all();  // H^(n), G^(n), lambda written
+      }
+    }
+  }
+}
+
+template <int ALG>
+cudaError_t run_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
+                                 int nclusters, int iters, const planc_nls_opts& o, int sched_l,
+                                 int sched_r, int mode, int hmax, double* sqpart, int* err,
+                                 cudaStream_t st) {
+  const size_t smem = batch_persistent_smem(hmax);
+  cudaError_t e = cudaFuncSetAttribute(batch_solve_kernel<ALG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(MC_CS * nclusters), 1, 1);
+  cfg.blockDim = dim3(MC_NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = MC_CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, batch_solve_kernel<ALG>, tab, clist, coff, iters, o.mu_eps,
+                         std::max(1, o.pgd_steps), sched_l, sched_r, mode, sqpart, err);
+  note_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int ALG>
+int max_clusters_persistent(int hmax) {
+  const size_t smem = batch_persistent_smem(hmax);
+  if (cudaFuncSetAttribute(batch_solve_kernel<ALG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(batch_solve_kernel<ALG>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(MC_CS, 1, 1);
+  cfg.blockDim = dim3(MC_NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = MC_CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, batch_solve_kernel<ALG>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 }  // namespace
 
 cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, planc_nls_t alg,
@@ -882,6 +1061,28 @@ cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, pl
 }
 
 int mode_batch_max_rows() { return MC_CS * MC_RPC; }
+
+int batch_persistent_max_clusters(planc_nls_t alg, int hmax) {
+  return alg == PLANC_MU    ? max_clusters_persistent<PLANC_MU>(hmax)
+         : alg == PLANC_PGD ? max_clusters_persistent<PLANC_PGD>(hmax)
+                            : max_clusters_persistent<PLANC_HALS>(hmax);
+}
+
+cudaError_t launch_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
+                                    int nclusters, int iters, planc_nls_t alg,
+                                    const planc_nls_opts& o, int sched_l, int sched_r, int mode,
+                                    int hmax, double* sqpart, int* err, cudaStream_t st) {
+  if (alg == PLANC_MU)
+    return run_batch_persistent<PLANC_MU>(tab, clist, coff, nclusters, iters, o, sched_l, sched_r,
+                                          mode, hmax, sqpart, err, st);
+  if (alg == PLANC_PGD)
+    return run_batch_persistent<PLANC_PGD>(tab, clist, coff, nclusters, iters, o, sched_l, sched_r,
+                                           mode, hmax, sqpart, err, st);
+  if (alg == PLANC_HALS)
+    return run_batch_persistent<PLANC_HALS>(tab, clist, coff, nclusters, iters, o, sched_l,
+                                            sched_r, mode, hmax, sqpart, err, st);
+  return cudaErrorInvalidValue;
+}
 
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64) {
   // the Nesterov and ADMM steps hold four row vectors in registers: FP64 up

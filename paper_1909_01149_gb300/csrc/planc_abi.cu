@@ -217,6 +217,7 @@ planc_solve_opts planc_solve_opts_default(void) {
   o.use_graph = 1;
   o.profile = 0;
   o.nes_accel = 1;
+  o.batch_persistent = 1;
   return o;
 }
 

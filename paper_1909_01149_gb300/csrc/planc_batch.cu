@@ -1,11 +1,16 @@
 // planc_batch_solve: many independent 3-way NNCP instances advanced together.
 //
-// Every phase of an outer iteration is one launch over all instances (work
-// tables of (instance, tile) items built here); with opts.use_graph the whole
-// solve, all outer iterations included, is captured once and launched as one
-// CUDA graph.  The tile shapes of the two partial-MTTKRP launches are picked
-// by timing the candidates on the batch itself the first time a batch of that
-// size and shape sum is seen (the choice is cached for the process).
+// Default (opts.batch_persistent): the whole solve is ONE persistent launch of
+// thread-block clusters, each cluster solving whole instances in turn; the
+// instances are dealt to the clusters longest-first onto the least-loaded
+// cluster (LPT), by an estimate of each instance's work.  Otherwise every
+// phase of an outer iteration is one launch over all instances (work tables
+// of (instance, tile) items built here).  With opts.use_graph the launch
+// sequence (one node, or all phases of all outer iterations) is captured once
+// and launched as a CUDA graph.  The schedule (rank blocking of both partial
+// MTTKRPs; for the per-phase launches also their tile shapes) is picked by
+// timing the candidates on the batch itself the first time a batch of that
+// signature is seen (the choice is cached for the process).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,8 +59,10 @@ struct TuneChoice {
   int tl = 1, nt = 1, sched_left = 2, sched_right = 2;
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, TuneChoice> g_tune;
+std::map<TuneKey, TuneChoice> g_tune;    // per-phase launches
+std::map<TuneKey, TuneChoice> g_tune_p;  // persistent launch (rank blocking only)
 thread_local TuneChoice t_last_choice;
+thread_local bool t_last_persistent = false;
 constexpr int kSchedules = 3;
 
 struct Alloc {
@@ -123,8 +130,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   const int iters = o.iters;
 
   // ---- workspace: per-instance arrays, work tables, instance table
-  std::vector<size_t> offT(count), offM(count), offG(count), offGf(count), offLam(count),
-      offAlpha(count), offHist(count), offInner(count);
+  std::vector<size_t> offT(count), offM(count), offG(count), offGf(count), offAlpha(count);
   size_t bytes = 0;
   for (int b = 0; b < count; ++b) {
     const planc_batch_instance& in = inst[b];
@@ -135,11 +141,14 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     offM[b] = bytes; bytes += align256(maxI * R * 4);
     offG[b] = bytes; bytes += align256(3 * R * R * 8);
     offGf[b] = bytes; bytes += align256(3 * R * R * 4);
-    offLam[b] = bytes; bytes += align256(32 * 8);
     offAlpha[b] = bytes; bytes += 256;
-    offHist[b] = bytes; bytes += align256((size_t)iters * 3 * 8);
-    offInner[b] = bytes; bytes += align256((size_t)iters * 3 * 4);
   }
+  // every instance's error history, inner counts and lambda, contiguous (one
+  // clear and one copy back each)
+  const size_t hist_per = (size_t)iters * 3;
+  const size_t off_hist = bytes; bytes += align256(sizeof(double) * hist_per * count);
+  const size_t off_inner = bytes; bytes += align256(sizeof(int32_t) * hist_per * count);
+  const size_t off_lam = bytes; bytes += align256(sizeof(double) * 32 * count);
   // work tables; the partial-MTTKRP tables list the instances in rank order,
   // so that a CTA's contiguous run of items stays within one rank class
   std::vector<int> by_rank(count);
@@ -191,6 +200,10 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     bytes += align256(sizeof(int64_t) * left_cum[t].size());
   }
   const size_t off_err = bytes; bytes += 256;
+  // persistent launch: alpha partials, and the instances dealt to the clusters
+  const size_t off_sqpart = bytes; bytes += align256(sizeof(double) * kBatchClusterCtas * count);
+  const size_t off_clist = bytes; bytes += align256(sizeof(int) * count);
+  const size_t off_coff = bytes; bytes += align256(sizeof(int) * (count + 1));
 
   Alloc ws;
   if (cudaMalloc(&ws.p, bytes) != cudaSuccess) {
@@ -213,10 +226,10 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     t.M = reinterpret_cast<float*>(base + offM[b]);
     t.G = reinterpret_cast<double*>(base + offG[b]);
     t.Gf = reinterpret_cast<float*>(base + offGf[b]);
-    t.lam = reinterpret_cast<double*>(base + offLam[b]);
+    t.lam = reinterpret_cast<double*>(base + off_lam) + (size_t)32 * b;
     t.alpha = reinterpret_cast<double*>(base + offAlpha[b]);
-    t.hist = reinterpret_cast<double*>(base + offHist[b]);
-    t.inner = reinterpret_cast<int32_t*>(base + offInner[b]);
+    t.hist = reinterpret_cast<double*>(base + off_hist) + hist_per * b;
+    t.inner = reinterpret_cast<int32_t*>(base + off_inner) + hist_per * b;
   }
   const BatchInst* d_tab = reinterpret_cast<const BatchInst*>(base + off_tab);
   const int2* d_sq = reinterpret_cast<const int2*>(base + off_sq);
@@ -240,9 +253,8 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     if (h2d(off_left[t], left_items[t].data(), sizeof(int2) * left_items[t].size()) != cudaSuccess ||
         h2d(off_lcum[t], left_cum[t].data(), sizeof(int64_t) * left_cum[t].size()) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "table upload failed");
-  for (int b = 0; b < count; ++b)
-    if (cudaMemsetAsync(base + offHist[b], 0, (size_t)iters * 3 * 8, st) != cudaSuccess)
-      return bfail(PLANC_E_CUDA, "memset failed");
+  if (cudaMemsetAsync(base + off_hist, 0, sizeof(double) * hist_per * count, st) != cudaSuccess)
+    return bfail(PLANC_E_CUDA, "memset failed");
 
   const int hmax_left = (int)maxC, hmax_right = (int)maxI2;
   if (batch_pm_smem(std::max(hmax_left, hmax_right)) > 227 * 1024)
@@ -252,21 +264,65 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
                         (int)left_items[2].size()};
   const int nright = (int)right_items.size(), nrc = (int)rc_items.size();
 
-  // ---- schedule: every (tile, rank blocking) candidate of each partial
-  // MTTKRP timed on this batch (second of two runs), cached per batch
-  // signature
+  // ---- the persistent launch: clusters that fit at once, instances dealt
+  // longest-first onto the least-loaded cluster.  An instance's estimated
+  // cost per outer iteration is its partial-MTTKRP FMAs (elements x the two
+  // padded ranks, rank classes 8 / 16 / 32) plus a fixed share for the
+  // latency of its phases (about the FMAs of 8e6 at the rate of one cluster).
+  const bool persistent = o.batch_persistent != 0;
+  const int hmax_p = (int)std::max(maxC, maxI2);
+  int nclusters = 0;
+  if (persistent) {
+    nclusters = std::min(count, batch_persistent_max_clusters(o.alg, hmax_p));
+    if (nclusters < 1) return bfail(PLANC_E_CUDA, "the persistent launch does not fit on this GPU");
+    std::vector<double> cost(count);
+    for (int b = 0; b < count; ++b) {
+      const int R = inst[b].R;
+      const double rc = R <= 8 ? 8.0 : R <= 16 ? 16.0 : 32.0;
+      cost[b] = (double)(inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2]) * 2.0 * rc + 8e6;
+    }
+    std::vector<int> order(count);
+    for (int b = 0; b < count; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<int>> lists(nclusters);
+    std::vector<double> load(nclusters, 0.0);
+    for (int b : order) {  // least-loaded cluster, lowest index on ties
+      int q = 0;
+      for (int k = 1; k < nclusters; ++k)
+        if (load[k] < load[q]) q = k;
+      lists[q].push_back(b);
+      load[q] += cost[b];
+    }
+    std::vector<int> clist, coff(1, 0);
+    for (const auto& l : lists) {
+      clist.insert(clist.end(), l.begin(), l.end());
+      coff.push_back((int)clist.size());
+    }
+    if (h2d(off_clist, clist.data(), sizeof(int) * count) != cudaSuccess ||
+        h2d(off_coff, coff.data(), sizeof(int) * (nclusters + 1)) != cudaSuccess)
+      return bfail(PLANC_E_CUDA, "table upload failed");
+  }
+  const int* d_clist = reinterpret_cast<const int*>(base + off_clist);
+  const int* d_coff = reinterpret_cast<const int*>(base + off_coff);
+  double* d_sqpart = reinterpret_cast<double*>(base + off_sqpart);
+
+  // ---- schedule: every candidate of each partial MTTKRP timed on this batch
+  // (second of two runs), cached per batch signature.  Per-phase launches:
+  // (tile, rank blocking) of each kernel; persistent launch: the rank
+  // blocking of each branch (the launch run with only that branch).
   TuneKey key{count, 0, 0, 0};
   for (int b = 0; b < count; ++b) {
     key.elems += inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2];
     key.rank_sum += inst[b].R;
     key.bf16_count += inst[b].x_dtype == PLANC_BF16 ? 1 : 0;
   }
+  std::map<TuneKey, TuneChoice>& cache = persistent ? g_tune_p : g_tune;
   TuneChoice ch;
   bool tuned = false;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune.find(key);
-    if (it != g_tune.end()) {
+    auto it = cache.find(key);
+    if (it != cache.end()) {
       ch = it->second;
       tuned = true;
     }
@@ -293,22 +349,40 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
       }
       return true;
     };
-    for (int t = 0; t < 3; ++t)
+    if (persistent) {
+      ch.tl = 1;  // 128 threads per CTA, two rows each (fixed by the launch)
+      ch.nt = 1;
       for (int sc = 0; sc < kSchedules; ++sc) {
-        const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
-        const int64_t* lcum = reinterpret_cast<const int64_t*>(base + off_lcum[t]);
         float ms = 0.f;
-        if (!time_it([&] { return launch_batch_pm_left(d_tab, items, lcum, nleft[t], kTL[t],
-                                                       hmax_left, sc, sms, st); }, ms))
+        if (!time_it([&] { return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, 1,
+                                                          o.alg, o.nls, sc, sc, 1, hmax_p,
+                                                          d_sqpart, d_err, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
-        if (ms < best_l) { best_l = ms; ch.tl = t; ch.sched_left = sc; }
-        if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, d_rcum, nright, kNT[t],
-                                                        hmax_right, sc, sms, st); }, ms))
+        if (ms < best_l) { best_l = ms; ch.sched_left = sc; }
+        if (!time_it([&] { return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, 1,
+                                                          o.alg, o.nls, sc, sc, 2, hmax_p,
+                                                          d_sqpart, d_err, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
-        if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
+        if (ms < best_r) { best_r = ms; ch.sched_right = sc; }
       }
+    } else {
+      for (int t = 0; t < 3; ++t)
+        for (int sc = 0; sc < kSchedules; ++sc) {
+          const int2* items = reinterpret_cast<const int2*>(base + off_left[t]);
+          const int64_t* lcum = reinterpret_cast<const int64_t*>(base + off_lcum[t]);
+          float ms = 0.f;
+          if (!time_it([&] { return launch_batch_pm_left(d_tab, items, lcum, nleft[t], kTL[t],
+                                                         hmax_left, sc, sms, st); }, ms))
+            return bfail(PLANC_E_CUDA, "tuning launch failed");
+          if (ms < best_l) { best_l = ms; ch.tl = t; ch.sched_left = sc; }
+          if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, d_rcum, nright, kNT[t],
+                                                          hmax_right, sc, sms, st); }, ms))
+            return bfail(PLANC_E_CUDA, "tuning launch failed");
+          if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
+        }
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = ch;
+    cache[key] = ch;
   }
   // PLANC_BATCH_RANK_BLOCKING="l,r" forces the rank blocking of the two
   // kernels (tests compare every schedule; the tile choice stays tuned)
@@ -321,6 +395,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     }
   }
   t_last_choice = ch;
+  t_last_persistent = persistent;
   const int tl_idx = ch.tl;
   const int2* d_left = reinterpret_cast<const int2*>(base + off_left[tl_idx]);
   const int64_t* d_lcum = reinterpret_cast<const int64_t*>(base + off_lcum[tl_idx]);
@@ -329,6 +404,10 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   const long long c_start = launch_count();
   // ---- the solve as a launch sequence
   auto enqueue = [&]() -> cudaError_t {
+    if (persistent)
+      return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, iters, o.alg, o.nls,
+                                     ch.sched_left, ch.sched_right, 0, hmax_p, d_sqpart, d_err,
+                                     st);
     cudaError_t e;
     if ((e = launch_batch_sqnorm(d_tab, count, d_sq, (int)sq_items.size(), d_sqf, d_sqp, sms, st)) != cudaSuccess) return e;
     if ((e = launch_batch_gram(d_tab, count, st)) != cudaSuccess) return e;
@@ -368,22 +447,22 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   }
   const long long launches = launch_count() - c_start;
 
-  // ---- results
+  // ---- results (one copy of every history, one of every lambda)
   int err = 0;
-  std::vector<double> hist((size_t)iters * 3), lam(32);
-  if (cudaMemcpy(&err, d_err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+  std::vector<double> hist(hist_per * count), lam((size_t)32 * count);
+  if (cudaMemcpy(&err, d_err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hist.data(), base + off_hist, hist.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(lam.data(), base + off_lam, lam.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return bfail(PLANC_E_CUDA, "D2H failed");
   double worst = 0.0;
   for (int b = 0; b < count; ++b) {
-    if (cudaMemcpy(hist.data(), tab[b].hist, hist.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(lam.data(), tab[b].lam, 32 * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return bfail(PLANC_E_CUDA, "D2H failed");
-    inst[b].rel_err = hist[3 * (iters - 1)];
+    const double* hb = hist.data() + hist_per * b;
+    inst[b].rel_err = hb[3 * (iters - 1)];
     worst = std::max(worst, inst[b].rel_err);
     if (inst[b].rel_err_hist)
-      for (int i = 0; i < iters; ++i) inst[b].rel_err_hist[i] = hist[3 * i];
+      for (int i = 0; i < iters; ++i) inst[b].rel_err_hist[i] = hb[3 * i];
     if (inst[b].lambda)
-      for (int r = 0; r < inst[b].R; ++r) inst[b].lambda[r] = lam[r];
+      for (int r = 0; r < inst[b].R; ++r) inst[b].lambda[r] = lam[(size_t)32 * b + r];
   }
   if (report) {
     std::memset(report, 0, sizeof *report);
@@ -400,7 +479,7 @@ extern "C" planc_status_t planc_batch_schedule(int* out) {
   if (!out) return PLANC_E_INVALID;
   const planc::TuneChoice& c = planc::t_last_choice;
   out[0] = 2 * planc::kTL[c.tl];  // two rows per thread
-  out[1] = planc::kNT[c.nt];
+  out[1] = planc::kNT[c.nt];      // (the persistent launch: 128 threads per CTA)
   out[2] = c.sched_left;
   out[3] = c.sched_right;
   return PLANC_OK;

@@ -44,7 +44,7 @@ class NlsOpts(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("alg", C.c_int), ("iters", C.c_int), ("tol", C.c_double),
                 ("nls", NlsOpts), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("nes_accel", C.c_int)]
+                ("nes_accel", C.c_int), ("batch_persistent", C.c_int)]
 
 
 class Report(C.Structure):
@@ -391,11 +391,13 @@ class CPLoss(torch.autograd.Function):
 
 
 def batch_solve(Xs, Hs, alg: str = "hals", iters: int = 25, use_graph: bool = True,
-                nls: NlsOpts | None = None, stream=None):
+                nls: NlsOpts | None = None, stream=None, persistent: bool = True):
     """planc_batch_solve over instances (X_b, [H1, H2, H3]_b): X_b a flat device
     tensor (mode 1 fastest, float32 or bfloat16) whose dims come from the
     factors, H_b three float32 device tensors I_n x R updated in place.
-    Returns one dict per instance (lam, rel_err history) and the report."""
+    persistent: one persistent launch for the whole solve (else one launch
+    per phase).  Returns one dict per instance (lam, rel_err history) and the
+    report."""
     if len(Xs) != len(Hs) or not Xs:
         raise ValueError("need one factor triple per tensor")
     arr = (BatchInstance * len(Xs))()
@@ -427,6 +429,7 @@ def batch_solve(Xs, Hs, alg: str = "hals", iters: int = 25, use_graph: bool = Tr
     o.alg = ALGS[alg]
     o.iters = int(iters)
     o.use_graph = 1 if use_graph else 0
+    o.batch_persistent = 1 if persistent else 0
     if nls is not None:
         o.nls = nls
     rep = Report()
