@@ -519,15 +519,27 @@ def run_batch(args):
     import torch
     from paper_1909_01149_gb300 import planc, synth
     torch.cuda.set_device(0)
-    count, iters = 256, 25
+    count, iters = args.count, args.iters or 25
+    only = None if args.batch_path == "both" else args.batch_path == "persistent"
     t0 = time.time()
     insts = synth.batch(count, data_seed=1, noise=0.02)
     log(f"batch of {count} generated in {time.time() - t0:.1f}s")
     H0 = [synth.init_factors(X.shape, R, 2000 + i) for i, (X, _, R) in enumerate(insts)]
     elems = sum(int(np.prod(X.shape)) for X, _, _ in insts)
     peak, peak_kind = measured_peak()
-    out = {"mode": "batch", "workload": "nncp-batch-256x3way-U32..160-R8..32-hals25",
+    out = {"mode": "batch", "workload": "nncp-batch-%dx3way-U32..160-R8..32-hals%d" % (count, iters),
            "instances": count, "outer_iters_each": iters, "tensor_elements": elems}
+    if only is not None:  # one path alone (profiling): FP32 storage, no comparisons
+        Xd = [torch.from_numpy(synth.flat(X)).float().cuda() for X, _, _ in insts]
+        for k in range(max(1, args.warmup) + args.steps):
+            H = [[torch.from_numpy(h).float().cuda() for h in Hi] for Hi in H0]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, rep = planc.batch_solve(Xd, H, "hals", iters, persistent=only)
+            torch.cuda.synchronize()
+            out["f32_" + args.batch_path + "_s"] = round(time.perf_counter() - t0, 5)
+        out["schedule"] = rep["schedule"]
+        return out, 0
     for dtn, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
         Xd = [torch.from_numpy(synth.flat(X)).to(dt).cuda() for X, _, _ in insts]
         es = 4 if dtn == "f32" else 2
@@ -870,6 +882,9 @@ def main():
                          "batch: 256 uneven instances, batched vs per-instance loop; "
                          "ablation: dimension tree vs per-mode MTTKRP; "
                          "algs: every update algorithm on one workload")
+    ap.add_argument("--count", type=int, default=256, help="--mode batch: instances")
+    ap.add_argument("--batch-path", default="both", choices=["both", "persistent", "per-phase"],
+                    help="--mode batch: time one path alone (no comparisons)")
     ap.add_argument("--dims", default=None, help="override dims, e.g. 384,384,384")
     ap.add_argument("--rank", type=int, default=None, help="override R")
     ap.add_argument("--dtype", default=None, choices=["f32", "bf16", "f64"])

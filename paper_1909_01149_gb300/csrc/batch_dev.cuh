@@ -79,10 +79,46 @@ __device__ __forceinline__ void stage_range(uint32_t sdst, const char* xb, int64
   }
 }
 
-// shared-memory bytes of the two partial MTTKRPs: the X ring and a staged
-// factor of at most hmax rows
-__host__ __device__ constexpr size_t pm_smem_bytes(int hmax) {
-  return (size_t)NSTG * SW * 4 + (size_t)hmax * BR * 4;
+// shared-memory bytes of the two partial MTTKRPs: the X ring, a staged factor
+// of at most hmax rows, and (right branch, h1max > 0) the staged H1 of at
+// most h1max rows, transposed (stage_factor_t)
+__host__ __device__ constexpr size_t pm_smem_bytes(int hmax, int h1max = 0) {
+  return (size_t)NSTG * SW * 4 + ((size_t)hmax + (h1max > 0 ? (size_t)h1max + 1 : 0)) * BR * 4;
+}
+
+// a row-major nrow x R factor into shared memory transposed: column r at
+// dst + r * ld, ld = nrow rounded up to even (rows nrow .. ld - 1 and columns
+// R .. BRC - 1 zero), so that lanes reading consecutive row pairs of one
+// column use distinct banks with 8-byte loads
+__device__ __forceinline__ void stage_factor_t(float* dst, const float* H, int nrow, int R,
+                                               int BRC) {
+  const int ld = nrow + (nrow & 1);
+  for (int e = threadIdx.x; e < ld * BRC; e += blockDim.x) {
+    const int r = e / ld, i = e - (e / ld) * ld;
+    dst[e] = (r < R && i < nrow) ? __ldcg(H + (int64_t)i * R + r) : 0.f;
+  }
+}
+
+// The left branch's chunk: nk columns k0 .. k0 + nk - 1 of the item's row
+// block, column kk the nb bytes from element l0 + L (k0 + kk), each copied as
+// its 16-byte-aligned range into slot kk (SB bytes).  The CTA's threads take
+// the chunk's 16-byte pieces in turn (piece idx: column idx / CPC, offset
+// idx % CPC), so that no thread loops over columns it copies nothing of.
+template <int ES, int RB, int NT>
+__device__ __forceinline__ void left_copies(uint32_t dst, const char* xb, int64_t l0, int64_t L,
+                                            int k0, int nk, int nb, int tid) {
+  constexpr int SB = RB * ES + 16;
+  constexpr int CPC = SB / 16;  // pieces per column (RB * ES is a multiple of 16)
+  const int total = nk * CPC;
+  for (int idx = tid; idx < total; idx += NT) {
+    const int kk = idx / CPC, off = (idx - kk * CPC) * 16;
+    const int64_t byte0 = (int64_t)ES * (l0 + L * (k0 + kk));
+    const int64_t a0 = byte0 & ~(int64_t)15;
+    const int lim = (int)(byte0 + nb - a0);
+    if (off < lim)
+      cp_async16(dst + (uint32_t)(kk * SB + off), xb + a0 + off,
+                 lim - off >= 16 ? 16u : (uint32_t)(lim - off));
+  }
 }
 
 // ---- T^{1:2}[l, r] = sum_k X[l, k] H3[k, r]: items (b, block of 2 NT rows l) ------------
@@ -98,39 +134,32 @@ struct LeftGeom {
   __device__ __forceinline__ static int kc(int es) { return min(32, 4 * SW / sb(es)); }
 };
 
+// nk columns of a staged chunk into the thread's two rows: column kk's first
+// element sits sh_kk elements into its copy, sh_0 = sh0 and sh_{kk+1} =
+// (sh_kk + Lm) mod (16 / ES) with Lm = L mod (16 / ES) (consecutive columns
+// start L elements apart); H3's row k0 + kk is read as broadcast 16-byte loads
 template <int NT, int BRC, bool BF16>
-__device__ __forceinline__ void left_chunk(const unsigned char* stage, const float* hs, int64_t l0,
-                                           int64_t L, int k0, int nk, float* a0, float* a1) {
+__device__ __forceinline__ void left_chunk(const unsigned char* stage, const float* hs, int sh0,
+                                           int Lm, int k0, int nk, float* a0, float* a1) {
   constexpr int ES = BF16 ? 2 : 4;
   constexpr int SB = LeftGeom<NT>::RB * ES + 16;
-  const int t2 = 2 * (int)threadIdx.x;
-#pragma unroll 2
-  for (int kk = 0; kk < nk; ++kk) {
-    // first element of the column within its copy (X starts on 16 bytes)
-    const int sh = (int)((l0 + L * (k0 + kk)) & (16 / ES - 1));
+  constexpr int MASK = 16 / ES - 1;
+  const unsigned char* xs = stage + 2 * (int)threadIdx.x * ES;
+  const float4* h = reinterpret_cast<const float4*>(hs + k0 * BRC);
+  int sh = sh0;
+#pragma unroll 4
+  for (int kk = 0; kk < nk; ++kk, xs += SB, h += BRC / 4) {
     float x0, x1;
     if (BF16) {
-      const __nv_bfloat16* xs = reinterpret_cast<const __nv_bfloat16*>(stage + kk * SB) + sh + t2;
-      if ((sh & 1) == 0) {
-        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(xs);
-        x0 = __low2float(v);
-        x1 = __high2float(v);
-      } else {
-        x0 = __bfloat162float(xs[0]);
-        x1 = __bfloat162float(xs[1]);
-      }
+      const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(xs) + sh;
+      x0 = __bfloat162float(p[0]);
+      x1 = __bfloat162float(p[1]);
     } else {
-      const float* xs = reinterpret_cast<const float*>(stage + kk * SB) + sh + t2;
-      if ((sh & 1) == 0) {
-        const float2 v = *reinterpret_cast<const float2*>(xs);
-        x0 = v.x;
-        x1 = v.y;
-      } else {
-        x0 = xs[0];
-        x1 = xs[1];
-      }
+      const float* p = reinterpret_cast<const float*>(xs) + sh;
+      x0 = p[0];
+      x1 = p[1];
     }
-    const float4* h = reinterpret_cast<const float4*>(hs + (k0 + kk) * BRC);
+    sh = (sh + Lm) & MASK;
 #pragma unroll
     for (int q = 0; q < BRC / 4; ++q) {
       const float4 hv = h[q];
@@ -167,13 +196,11 @@ __device__ __forceinline__ void pm_left_run(const BatchInst* __restrict__ tab, I
       const int es = b.xbf16 ? 2 : 4;
       const int64_t l0 = (int64_t)itm.y * G::RB;
       const int64_t nb = (int64_t)es * min((int64_t)G::RB, L - l0);
-      const int sb = G::sb(es);
       const int nk = min(G::kc(es), C - pk);
       const char* xb = reinterpret_cast<const char*>(b.X);
-      for (int kk = 0; kk < nk; ++kk) {
-        const int64_t byte0 = (int64_t)es * (l0 + L * (pk + kk));
-        stage_range(stg + (uint32_t)(slot * SW * 4 + kk * sb), xb, byte0, byte0 + nb, tid, NT);
-      }
+      const uint32_t dst = stg + (uint32_t)(slot * SW * 4);
+      if (es == 4) left_copies<4, G::RB, NT>(dst, xb, l0, L, pk, nk, (int)nb, tid);
+      else left_copies<2, G::RB, NT>(dst, xb, l0, L, pk, nk, (int)nb, tid);
       pk += nk;
       if (pk >= C) {
         ++pit;
@@ -213,15 +240,18 @@ __device__ __forceinline__ void pm_left_run(const BatchInst* __restrict__ tab, I
       }
     }
     const unsigned char* stage = bsm + (size_t)(k % NSTG) * SW * 4;
+    // the chunk's first element within its copy (X starts on 16 bytes)
+    const int mask = bf ? 7 : 3;
+    const int sh0 = (int)((l0 + L * ck) & mask), Lm = (int)(L & mask);
     if (cls == 8) {
-      if (bf) left_chunk<NT, 8, true>(stage, hs, l0, L, ck, nk, a0, a1);
-      else left_chunk<NT, 8, false>(stage, hs, l0, L, ck, nk, a0, a1);
+      if (bf) left_chunk<NT, 8, true>(stage, hs, sh0, Lm, ck, nk, a0, a1);
+      else left_chunk<NT, 8, false>(stage, hs, sh0, Lm, ck, nk, a0, a1);
     } else if (cls == 16) {
-      if (bf) left_chunk<NT, 16, true>(stage, hs, l0, L, ck, nk, a0, a1);
-      else left_chunk<NT, 16, false>(stage, hs, l0, L, ck, nk, a0, a1);
+      if (bf) left_chunk<NT, 16, true>(stage, hs, sh0, Lm, ck, nk, a0, a1);
+      else left_chunk<NT, 16, false>(stage, hs, sh0, Lm, ck, nk, a0, a1);
     } else {
-      if (bf) left_chunk<NT, 32, true>(stage, hs, l0, L, ck, nk, a0, a1);
-      else left_chunk<NT, 32, false>(stage, hs, l0, L, ck, nk, a0, a1);
+      if (bf) left_chunk<NT, 32, true>(stage, hs, sh0, Lm, ck, nk, a0, a1);
+      else left_chunk<NT, 32, false>(stage, hs, sh0, Lm, ck, nk, a0, a1);
     }
     ck += nk;
     if (ck >= C) {  // the item's rows are complete
@@ -277,17 +307,22 @@ __device__ __forceinline__ float ldstage(const unsigned char* stage, int q) {
 }
 
 // inner sums of the unit (rows i, i + 1 when live1; columns jj = g, g + ng,
-// ... below nj of the chunk whose first column is j0) into in0, in1
+// ... below nj of the chunk whose first column is j0) into in0, in1.  Row
+// i + 1 is read even when it is not live (it stays inside the stage) and
+// weighted by zero.
 template <int BRC, bool BF16>
 __device__ __forceinline__ void right_sums(const unsigned char* stage, int sh, const float* hs,
                                            int I1, int i, bool live1, int g, int ng, int j0,
                                            int nj, float* in0, float* in1) {
-#pragma unroll 2
-  for (int jj = g; jj < nj; jj += ng) {
-    const int q = sh + jj * I1 + i;
+  int q = sh + g * I1 + i;
+  const int qs = ng * I1;
+  const float4* h = reinterpret_cast<const float4*>(hs + (j0 + g) * BRC);
+  const int hs4 = ng * (BRC / 4);
+#pragma unroll 4
+  for (int jj = g; jj < nj; jj += ng, q += qs, h += hs4) {
     const float x0 = ldstage<BF16>(stage, q);
-    const float x1 = live1 ? ldstage<BF16>(stage, q + 1) : 0.f;
-    const float4* h = reinterpret_cast<const float4*>(hs + (j0 + jj) * BRC);
+    const float v1 = ldstage<BF16>(stage, q + 1);
+    const float x1 = live1 ? v1 : 0.f;
 #pragma unroll
     for (int qq = 0; qq < BRC / 4; ++qq) {
       const float4 hv = h[qq];
@@ -307,8 +342,8 @@ __device__ __forceinline__ void right_sums(const unsigned char* stage, int sh, c
 // weighted by H1[i, r] into acc
 template <int NT, int BRC, bool BF16>
 __device__ __forceinline__ void right_rows(const unsigned char* stage, int sh, const float* hs,
-                                           const float* H1, int I1, int R, int j0, int nj,
-                                           float* acc) {
+                                           const float* H1, const float* h1s, int I1, int R,
+                                           int j0, int nj, float* acc) {
   for (int i = threadIdx.x; i < I1; i += NT) {
     float t[BRC];
 #pragma unroll
@@ -326,10 +361,16 @@ __device__ __forceinline__ void right_rows(const unsigned char* stage, int sh, c
         t[4 * qq + 3] = fmaf(x, hv.w, t[4 * qq + 3]);
       }
     }
-    const float* h1 = H1 + (int64_t)i * R;
+    if (h1s) {  // H1 staged in shared memory, transposed (column stride I1 rounded to even)
+      const int ld = I1 + (I1 & 1);
 #pragma unroll
-    for (int r = 0; r < BRC; ++r)
-      if (r < R) acc[r] = fmaf(t[r], __ldcg(h1 + r), acc[r]);
+      for (int r = 0; r < BRC; ++r) acc[r] = fmaf(t[r], h1s[r * ld + i], acc[r]);
+    } else {
+      const float* h1 = H1 + (int64_t)i * R;
+#pragma unroll
+      for (int r = 0; r < BRC; ++r)
+        if (r < R) acc[r] = fmaf(t[r], __ldcg(h1 + r), acc[r]);
+    }
   }
 }
 
@@ -337,8 +378,8 @@ __device__ __forceinline__ void right_rows(const unsigned char* stage, int sh, c
 // weighted sums (long first modes)
 template <int NT, int BRC, bool BF16>
 __device__ __forceinline__ void right_chunk(const unsigned char* stage, int sh, const float* hs,
-                                            const float* H1, int I1, int R, int j0, int nj,
-                                            float* in0, float* in1) {
+                                            const float* H1, const float* h1s, int I1, int R,
+                                            int j0, int nj, float* in0, float* in1) {
   const int P = (I1 + 1) >> 1;
   if (P <= NT) {
     const int ng = NT / P;
@@ -348,17 +389,22 @@ __device__ __forceinline__ void right_chunk(const unsigned char* stage, int sh, 
       right_sums<BRC, BF16>(stage, sh, hs, I1, i, i + 1 < I1, u / P, ng, j0, nj, in0, in1);
     }
   } else {
-    right_rows<NT, BRC, BF16>(stage, sh, hs, H1, I1, R, j0, nj, in0);
+    right_rows<NT, BRC, BF16>(stage, sh, hs, H1, h1s, I1, R, j0, nj, in0);
   }
 }
 
 // The CTA's contiguous run of right items i0 .. i1 - 1; item(i) gives
-// (instance, slab c).  bsm as for pm_left_run (the staged factor is H2).
+// (instance, slab c).  bsm: the X ring, the staged H2 (room for hcap rows)
+// and, for instances with I1 <= h1cap, the staged H1 (pm_smem_bytes(hcap,
+// h1cap)); H1 is read from global memory otherwise.
 template <int NT, typename ItemFn>
 __device__ __forceinline__ void pm_right_run(const BatchInst* __restrict__ tab, ItemFn item,
-                                             int i0, int i1, int sched, unsigned char* bsm) {
+                                             int i0, int i1, int sched, unsigned char* bsm,
+                                             int hcap, int h1cap) {
   __shared__ float red[NT / 32][BR];
   float* hs = reinterpret_cast<float*>(bsm + (size_t)NSTG * SW * 4);
+  float* hs1 = hs + (size_t)hcap * BR;
+  const float* h1s = nullptr;
   const uint32_t stg = (uint32_t)__cvta_generic_to_shared(bsm);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -406,9 +452,11 @@ __device__ __forceinline__ void pm_right_run(const BatchInst* __restrict__ tab, 
     const bool bf = b.xbf16 != 0;
     const int es = bf ? 2 : 4;
     const int nj = min(right_kc(I1, es), I2 - cj);
-    if (cj == 0 && bi != cur) {  // H2 of a new instance (the old one is no longer read)
+    if (cj == 0 && bi != cur) {  // H2 (and H1) of a new instance (the old ones are no longer read)
       cls = rank_class(R, sched);
       stage_factor(hs, b.H[1], I2, R, cls);
+      h1s = I1 <= h1cap ? hs1 : nullptr;
+      if (h1s) stage_factor_t(hs1, b.H[0], I1, R, cls);
       __syncthreads();
       cur = bi;
     }
@@ -416,14 +464,14 @@ __device__ __forceinline__ void pm_right_run(const BatchInst* __restrict__ tab, 
     const int sh = (int)((L * itm.y + (int64_t)I1 * cj) & (16 / es - 1));
     const unsigned char* stage = bsm + (size_t)(k % NSTG) * SW * 4;
     if (cls == 8) {
-      if (bf) right_chunk<NT, 8, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
-      else right_chunk<NT, 8, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      if (bf) right_chunk<NT, 8, true>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 8, false>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
     } else if (cls == 16) {
-      if (bf) right_chunk<NT, 16, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
-      else right_chunk<NT, 16, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      if (bf) right_chunk<NT, 16, true>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 16, false>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
     } else {
-      if (bf) right_chunk<NT, 32, true>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
-      else right_chunk<NT, 32, false>(stage, sh, hs, b.H[0], I1, R, cj, nj, in0, in1);
+      if (bf) right_chunk<NT, 32, true>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
+      else right_chunk<NT, 32, false>(stage, sh, hs, b.H[0], h1s, I1, R, cj, nj, in0, in1);
     }
     cj += nj;
     if (cj >= I2) {  // the item's sums are complete
@@ -432,13 +480,27 @@ __device__ __forceinline__ void pm_right_run(const BatchInst* __restrict__ tab, 
         const int ng = NT / P;
         const int i = 2 * (tid % P);
         const bool live = tid < P * ng, live1 = live && i + 1 < I1;
-        const float* h1 = b.H[0] + (int64_t)i * R;
+        if (h1s) {  // staged rows i, i + 1 of every column (transposed; padding is zero)
+          const int ld = I1 + (I1 & 1);
 #pragma unroll
-        for (int r = 0; r < BR; ++r) {
-          float v = 0.f;
-          if (live && r < R) v = in0[r] * __ldcg(h1 + r);
-          if (live1 && r < R) v = fmaf(in1[r], __ldcg(h1 + R + r), v);
-          in0[r] = v;
+          for (int r = 0; r < BR; ++r) {
+            float v = 0.f;
+            if (live && r < cls) {
+              const float2 w = *reinterpret_cast<const float2*>(h1s + r * ld + i);
+              v = in0[r] * w.x;
+              if (live1) v = fmaf(in1[r], w.y, v);
+            }
+            in0[r] = v;
+          }
+        } else {
+          const float* h1 = b.H[0] + (int64_t)i * R;
+#pragma unroll
+          for (int r = 0; r < BR; ++r) {
+            float v = 0.f;
+            if (live && r < R) v = in0[r] * __ldcg(h1 + r);
+            if (live1 && r < R) v = fmaf(in1[r], __ldcg(h1 + R + r), v);
+            in0[r] = v;
+          }
         }
       }
       const float v = reduce_scatter32(in0, lane);

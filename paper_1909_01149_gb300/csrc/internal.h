@@ -215,13 +215,16 @@ int mode_batch_max_rows();
 // thread-block clusters, cluster q solving the instances clist[coff[q]] ..
 // clist[coff[q + 1] - 1] in turn (alg MU, HALS or PGD); mode 1 / 2 runs only
 // the left / right partial MTTKRPs (schedule timing).  hmax: the longest
-// second or third mode of the batch; sqpart: 8 doubles per instance.
+// second or third mode of the batch; h1max: the longest first mode when the
+// right branch stages H1 in shared memory, else 0; sqpart: 8 doubles per
+// instance.
 cudaError_t launch_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
                                     int nclusters, int iters, planc_nls_t alg,
                                     const planc_nls_opts& o, int sched_l, int sched_r, int mode,
-                                    int hmax, double* sqpart, int* err, cudaStream_t st);
+                                    int hmax, int h1max, double* sqpart, int* err,
+                                    cudaStream_t st);
 // clusters of the persistent launch that fit on the device at once (0 if none)
-int batch_persistent_max_clusters(planc_nls_t alg, int hmax);
+int batch_persistent_max_clusters(planc_nls_t alg, int hmax, int h1max);
 constexpr int kBatchClusterCtas = 8;  // CTAs per cluster of the persistent launch
 bool mode_fused_eligible(planc_nls_t alg, int64_t rows, int R, bool f64);
 // the per-iteration history record (error triple and inner counts at index

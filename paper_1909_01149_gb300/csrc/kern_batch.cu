@@ -96,7 +96,7 @@ __device__ __forceinline__ void work_run(const int64_t* cumw, int nitems, int& i
 template <int NT>
 __global__ void __launch_bounds__(NT)
 batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                     const int64_t* __restrict__ cumw, int nitems, int sched) {
+                     const int64_t* __restrict__ cumw, int nitems, int sched, int, int) {
   extern __shared__ __align__(16) unsigned char bsm[];
   int i0, i1;
   work_run(cumw, nitems, i0, i1);
@@ -104,14 +104,17 @@ batch_pm_left_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__
 }
 
 // ---- M^(3) = X_(1:2)^T (H^(2) . H^(1)): items (b, c) -------------------------------------
+// hcap: rows of the staged H2; h1cap: rows of the staged H1 (0: H1 is read
+// from global memory)
 template <int NT>
 __global__ void __launch_bounds__(NT)
 batch_pm_right_kernel(const BatchInst* __restrict__ tab, const int2* __restrict__ items,
-                      const int64_t* __restrict__ cumw, int nitems, int sched) {
+                      const int64_t* __restrict__ cumw, int nitems, int sched, int hcap,
+                      int h1cap) {
   extern __shared__ __align__(16) unsigned char bsm[];
   int i0, i1;
   work_run(cumw, nitems, i0, i1);
-  pm_right_run<NT>(tab, [items](int i) { return items[i]; }, i0, i1, sched, bsm);
+  pm_right_run<NT>(tab, [items](int i) { return items[i]; }, i0, i1, sched, bsm, hcap, h1cap);
 }
 
 // ---- M^(1) and M^(2) from T^{1:2}: items (b, r) ----------------------------------------
@@ -150,7 +153,7 @@ cudaError_t launch_batch_gram(const BatchInst* tab, int count, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-size_t batch_pm_smem(int hmax) { return pm_smem_bytes(hmax); }
+size_t batch_pm_smem(int hmax, int h1max) { return pm_smem_bytes(hmax, h1max); }
 
 namespace {
 // a persistent grid: as many CTAs as fit on the device at once (at least one
@@ -158,7 +161,7 @@ namespace {
 template <typename K>
 cudaError_t launch_staged(K kern, int nt, size_t smem, int sm_count, const BatchInst* tab,
                           const int2* items, const int64_t* cumw, int nitems, int sched,
-                          cudaStream_t st) {
+                          int hcap, int h1cap, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // the whole unified L1 as shared memory, so that every CTA of the grid is
   // resident at once (the default carveout may hold fewer)
@@ -170,7 +173,7 @@ cudaError_t launch_staged(K kern, int nt, size_t smem, int sm_count, const Batch
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sm_count));
-  kern<<<grid, nt, smem, st>>>(tab, items, cumw, nitems, sched);
+  kern<<<grid, nt, smem, st>>>(tab, items, cumw, nitems, sched, hcap, h1cap);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -181,25 +184,26 @@ cudaError_t launch_staged(K kern, int nt, size_t smem, int sm_count, const Batch
 cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, const int64_t* cumw,
                                  int nitems, int tl, int hmax, int sched, int sm_count,
                                  cudaStream_t st) {
-  const size_t smem = batch_pm_smem(hmax);
+  const size_t smem = batch_pm_smem(hmax, 0);
   switch (tl) {
-    case 64: return launch_staged(batch_pm_left_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, st);
-    case 128: return launch_staged(batch_pm_left_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, st);
-    case 256: return launch_staged(batch_pm_left_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 64: return launch_staged(batch_pm_left_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, hmax, 0, st);
+    case 128: return launch_staged(batch_pm_left_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, hmax, 0, st);
+    case 256: return launch_staged(batch_pm_left_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, hmax, 0, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // nt: threads per CTA (64, 128 or 256); hmax: longest second mode of the
-// batch; sched: rank-class schedule (see rank_class)
+// batch; h1max: longest first mode when H1 is staged too, else 0; sched:
+// rank-class schedule (see rank_class)
 cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, const int64_t* cumw,
-                                  int nitems, int nt, int hmax, int sched, int sm_count,
+                                  int nitems, int nt, int hmax, int h1max, int sched, int sm_count,
                                   cudaStream_t st) {
-  const size_t smem = batch_pm_smem(hmax);
+  const size_t smem = batch_pm_smem(hmax, h1max);
   switch (nt) {
-    case 64: return launch_staged(batch_pm_right_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, st);
-    case 128: return launch_staged(batch_pm_right_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, st);
-    case 256: return launch_staged(batch_pm_right_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, st);
+    case 64: return launch_staged(batch_pm_right_kernel<64>, 64, smem, sm_count, tab, items, cumw, nitems, sched, hmax, h1max, st);
+    case 128: return launch_staged(batch_pm_right_kernel<128>, 128, smem, sm_count, tab, items, cumw, nitems, sched, hmax, h1max, st);
+    case 256: return launch_staged(batch_pm_right_kernel<256>, 256, smem, sm_count, tab, items, cumw, nitems, sched, hmax, h1max, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -893,16 +893,16 @@ __device__ __forceinline__ void cluster_sync_all() {
   cluster_wait();
 }
 
-size_t batch_persistent_smem(int hmax) {
-  return std::max(McLayout<float, 32, false>::bytes, bdev::pm_smem_bytes(hmax));
+size_t batch_persistent_smem(int hmax, int h1max) {
+  return std::max(McLayout<float, 32, false>::bytes, bdev::pm_smem_bytes(hmax, h1max));
 }
 
 template <int ALG>
 __global__ void __launch_bounds__(MC_NT, PB_MINB)
 batch_solve_kernel(const BatchInst* __restrict__ tab, const int* __restrict__ clist,
                    const int* __restrict__ coff, int iters, double mu_eps, int pgd_steps,
-                   int sched_l, int sched_r, int mode, double* __restrict__ sqpart,
-                   int* __restrict__ err) {
+                   int sched_l, int sched_r, int mode, int hcap, int h1cap,
+                   double* __restrict__ sqpart, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char mc_smem[];
   __shared__ double sred[MC_NT / 32];
   // the contractions' staged column and partial sums use the start of the
@@ -925,7 +925,7 @@ batch_solve_kernel(const BatchInst* __restrict__ tab, const int* __restrict__ cl
     auto item = [bi](int y) { return make_int2(bi, y); };
     if (mode != 0) {
       if (mode == 1) bdev::pm_left_run<MC_NT>(tab, item, yl0, yl1, sched_l, mc_smem);
-      else bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem);
+      else bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem, hcap, h1cap);
       cluster_sync_all();
       continue;
     }
@@ -965,7 +965,7 @@ batch_solve_kernel(const BatchInst* __restrict__ tab, const int* __restrict__ cl
         } else if (n == 1) {
           for (int r = c; r < R; r += MC_CS) bdev::contract_first_item<MC_NT>(b, r, hcol);
         } else {
-          bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem);
+          bdev::pm_right_run<MC_NT>(tab, item, yr0, yr1, sched_r, mc_smem, hcap, h1cap);
         }
         cluster_sync_all();  // M^(n) complete
         mode_update_body<float, 32, ALG, true>((int)b.I[n], R, 3, n, b.G, b.Gf, b.M, b.H[n], b.lam,
@@ -981,9 +981,9 @@ batch_solve_kernel(const BatchInst* __restrict__ tab, const int* __restrict__ cl
 template <int ALG>
 cudaError_t run_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
                                  int nclusters, int iters, const planc_nls_opts& o, int sched_l,
-                                 int sched_r, int mode, int hmax, double* sqpart, int* err,
-                                 cudaStream_t st) {
-  const size_t smem = batch_persistent_smem(hmax);
+                                 int sched_r, int mode, int hmax, int h1max, double* sqpart,
+                                 int* err, cudaStream_t st) {
+  const size_t smem = batch_persistent_smem(hmax, h1max);
   cudaError_t e = cudaFuncSetAttribute(batch_solve_kernel<ALG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1000,14 +1000,15 @@ cudaError_t run_batch_persistent(const BatchInst* tab, const int* clist, const i
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, batch_solve_kernel<ALG>, tab, clist, coff, iters, o.mu_eps,
-                         std::max(1, o.pgd_steps), sched_l, sched_r, mode, sqpart, err);
+                         std::max(1, o.pgd_steps), sched_l, sched_r, mode, hmax, h1max, sqpart,
+                         err);
   note_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int ALG>
-int max_clusters_persistent(int hmax) {
-  const size_t smem = batch_persistent_smem(hmax);
+int max_clusters_persistent(int hmax, int h1max) {
+  const size_t smem = batch_persistent_smem(hmax, h1max);
   if (cudaFuncSetAttribute(batch_solve_kernel<ALG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(batch_solve_kernel<ALG>,
@@ -1062,25 +1063,26 @@ cudaError_t launch_mode_batch(const BatchInst* tab, int count, int n, int it, pl
 
 int mode_batch_max_rows() { return MC_CS * MC_RPC; }
 
-int batch_persistent_max_clusters(planc_nls_t alg, int hmax) {
-  return alg == PLANC_MU    ? max_clusters_persistent<PLANC_MU>(hmax)
-         : alg == PLANC_PGD ? max_clusters_persistent<PLANC_PGD>(hmax)
-                            : max_clusters_persistent<PLANC_HALS>(hmax);
+int batch_persistent_max_clusters(planc_nls_t alg, int hmax, int h1max) {
+  return alg == PLANC_MU    ? max_clusters_persistent<PLANC_MU>(hmax, h1max)
+         : alg == PLANC_PGD ? max_clusters_persistent<PLANC_PGD>(hmax, h1max)
+                            : max_clusters_persistent<PLANC_HALS>(hmax, h1max);
 }
 
 cudaError_t launch_batch_persistent(const BatchInst* tab, const int* clist, const int* coff,
                                     int nclusters, int iters, planc_nls_t alg,
                                     const planc_nls_opts& o, int sched_l, int sched_r, int mode,
-                                    int hmax, double* sqpart, int* err, cudaStream_t st) {
+                                    int hmax, int h1max, double* sqpart, int* err,
+                                    cudaStream_t st) {
   if (alg == PLANC_MU)
     return run_batch_persistent<PLANC_MU>(tab, clist, coff, nclusters, iters, o, sched_l, sched_r,
-                                          mode, hmax, sqpart, err, st);
+                                          mode, hmax, h1max, sqpart, err, st);
   if (alg == PLANC_PGD)
     return run_batch_persistent<PLANC_PGD>(tab, clist, coff, nclusters, iters, o, sched_l, sched_r,
-                                           mode, hmax, sqpart, err, st);
+                                           mode, hmax, h1max, sqpart, err, st);
   if (alg == PLANC_HALS)
     return run_batch_persistent<PLANC_HALS>(tab, clist, coff, nclusters, iters, o, sched_l,
-                                            sched_r, mode, hmax, sqpart, err, st);
+                                            sched_r, mode, hmax, h1max, sqpart, err, st);
   return cudaErrorInvalidValue;
 }
 

@@ -33,9 +33,9 @@ cudaError_t launch_batch_pm_left(const BatchInst* tab, const int2* items, const 
                                  int nitems, int tl, int hmax, int sched, int sm_count,
                                  cudaStream_t st);
 cudaError_t launch_batch_pm_right(const BatchInst* tab, const int2* items, const int64_t* cumw,
-                                  int nitems, int nt, int hmax, int sched, int sm_count,
+                                  int nitems, int nt, int hmax, int h1max, int sched, int sm_count,
                                   cudaStream_t st);
-size_t batch_pm_smem(int hmax);
+size_t batch_pm_smem(int hmax, int h1max);
 cudaError_t launch_batch_contract(const BatchInst* tab, const int2* items, int nitems, bool rest,
                                   int sm_count, cudaStream_t st);
 
@@ -96,7 +96,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   if (o.alg != PLANC_MU && o.alg != PLANC_HALS && o.alg != PLANC_PGD)
     return bfail(PLANC_E_UNSUPPORTED, "batched solve supports MU, HALS and PGD");
   const int maxrows = mode_batch_max_rows();
-  int64_t maxC = 1, maxI2 = 1;
+  int64_t maxC = 1, maxI2 = 1, maxI1 = 1;
   for (int b = 0; b < count; ++b) {
     const planc_batch_instance& in = inst[b];
     if (!in.X || !in.H[0] || !in.H[1] || !in.H[2]) return bfail(PLANC_E_INVALID, "NULL pointer");
@@ -109,6 +109,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
       return bfail(PLANC_E_INVALID, "X must start on a 16-byte boundary");
     maxC = std::max(maxC, in.dims[2]);
     maxI2 = std::max(maxI2, in.dims[1]);
+    maxI1 = std::max(maxI1, in.dims[0]);
   }
   // graph capture needs a stream other than the legacy default stream
   struct OwnStream {
@@ -257,8 +258,12 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     return bfail(PLANC_E_CUDA, "memset failed");
 
   const int hmax_left = (int)maxC, hmax_right = (int)maxI2;
-  if (batch_pm_smem(std::max(hmax_left, hmax_right)) > 227 * 1024)
+  if (batch_pm_smem(std::max(hmax_left, hmax_right), 0) > 227 * 1024)
     return bfail(PLANC_E_SHAPE, "a mode is too long for the staged factor");
+  // the right branch also stages H1 when it fits next to H2 (otherwise its
+  // epilogue reads H1 from global memory)
+  constexpr size_t kStageBudget = 160 * 1024;
+  const int h1max_right = batch_pm_smem(hmax_right, (int)maxI1) <= kStageBudget ? (int)maxI1 : 0;
   const int64_t* d_rcum = reinterpret_cast<const int64_t*>(base + off_rcum);
   const int nleft[3] = {(int)left_items[0].size(), (int)left_items[1].size(),
                         (int)left_items[2].size()};
@@ -271,9 +276,10 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   // latency of its phases (about the FMAs of 8e6 at the rate of one cluster).
   const bool persistent = o.batch_persistent != 0;
   const int hmax_p = (int)std::max(maxC, maxI2);
+  const int h1max_p = batch_pm_smem(hmax_p, (int)maxI1) <= kStageBudget ? (int)maxI1 : 0;
   int nclusters = 0;
   if (persistent) {
-    nclusters = std::min(count, batch_persistent_max_clusters(o.alg, hmax_p));
+    nclusters = std::min(count, batch_persistent_max_clusters(o.alg, hmax_p, h1max_p));
     if (nclusters < 1) return bfail(PLANC_E_CUDA, "the persistent launch does not fit on this GPU");
     std::vector<double> cost(count);
     for (int b = 0; b < count; ++b) {
@@ -356,12 +362,12 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
         float ms = 0.f;
         if (!time_it([&] { return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, 1,
                                                           o.alg, o.nls, sc, sc, 1, hmax_p,
-                                                          d_sqpart, d_err, st); }, ms))
+                                                          h1max_p, d_sqpart, d_err, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
         if (ms < best_l) { best_l = ms; ch.sched_left = sc; }
         if (!time_it([&] { return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, 1,
                                                           o.alg, o.nls, sc, sc, 2, hmax_p,
-                                                          d_sqpart, d_err, st); }, ms))
+                                                          h1max_p, d_sqpart, d_err, st); }, ms))
           return bfail(PLANC_E_CUDA, "tuning launch failed");
         if (ms < best_r) { best_r = ms; ch.sched_right = sc; }
       }
@@ -376,7 +382,8 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
             return bfail(PLANC_E_CUDA, "tuning launch failed");
           if (ms < best_l) { best_l = ms; ch.tl = t; ch.sched_left = sc; }
           if (!time_it([&] { return launch_batch_pm_right(d_tab, d_right, d_rcum, nright, kNT[t],
-                                                          hmax_right, sc, sms, st); }, ms))
+                                                          hmax_right, h1max_right, sc, sms,
+                                                          st); }, ms))
             return bfail(PLANC_E_CUDA, "tuning launch failed");
           if (ms < best_r) { best_r = ms; ch.nt = t; ch.sched_right = sc; }
         }
@@ -406,8 +413,8 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   auto enqueue = [&]() -> cudaError_t {
     if (persistent)
       return launch_batch_persistent(d_tab, d_clist, d_coff, nclusters, iters, o.alg, o.nls,
-                                     ch.sched_left, ch.sched_right, 0, hmax_p, d_sqpart, d_err,
-                                     st);
+                                     ch.sched_left, ch.sched_right, 0, hmax_p, h1max_p, d_sqpart,
+                                     d_err, st);
     cudaError_t e;
     if ((e = launch_batch_sqnorm(d_tab, count, d_sq, (int)sq_items.size(), d_sqf, d_sqp, sms, st)) != cudaSuccess) return e;
     if ((e = launch_batch_gram(d_tab, count, st)) != cudaSuccess) return e;
@@ -417,7 +424,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
       if ((e = launch_mode_batch(d_tab, count, 0, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
       if ((e = launch_batch_contract(d_tab, d_rc, nrc, false, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 1, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
-      if ((e = launch_batch_pm_right(d_tab, d_right, d_rcum, nright, nt, hmax_right, ch.sched_right, sms, st)) != cudaSuccess) return e;
+      if ((e = launch_batch_pm_right(d_tab, d_right, d_rcum, nright, nt, hmax_right, h1max_right, ch.sched_right, sms, st)) != cudaSuccess) return e;
       if ((e = launch_mode_batch(d_tab, count, 2, it, o.alg, o.nls, d_err, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
