@@ -633,7 +633,8 @@ def run_mixed(args):
     """BF16 storage vs FP32 on the 4-way mouse-like workload (BPP, 30 outer
     iterations from the same initial factors).  Arms: 'bf16'; 'fp32_same_values'
     (the BF16-rounded tensor stored in FP32: the identical problem with FP32
-    streaming); 'fp32' (the unrounded tensor).  Each arm: outer iterations/s
+    streaming); 'fp32' (the unrounded tensor); 'fp16' (FP16 storage, its own
+    rounding).  Each arm: outer iterations/s
     (median of timed solves) and the event-timed partial-MTTKRP roofline, with
     the clocks sampled during the timed solves.  'seeds': BF16 vs FP32 on the
     unrounded tensor for data seeds 1-3, both final errors, and the speed at
@@ -648,7 +649,8 @@ def run_mixed(args):
     flat = synth.flat(X)
     Xb = torch.from_numpy(flat).to(torch.bfloat16).cuda()
     arms = (("bf16", Xb, 2), ("fp32_same_values", Xb.float(), 4),
-            ("fp32", torch.from_numpy(flat).cuda(), 4))
+            ("fp32", torch.from_numpy(flat).cuda(), 4),
+            ("fp16", torch.from_numpy(flat).to(torch.float16).cuda(), 2))
     out = {"workload": cfg["workload"], "alg": cfg["alg"], "iters": iters}
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
@@ -698,6 +700,7 @@ def run_mixed(args):
                                           out["fp32_same_values"]["rel_err"])
     out["speedup_bf16_over_fp32"] = round(out["bf16"]["iter_s"] /
                                           out["fp32_same_values"]["iter_s"], 3)
+    out["speedup_fp16_over_fp32"] = round(out["fp16"]["iter_s"] / out["fp32"]["iter_s"], 3)
     del Xb, arms
     torch.cuda.empty_cache()
     # seeds: BF16 storage vs FP32 on the unrounded tensor, matched error

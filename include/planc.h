@@ -163,8 +163,12 @@ planc_status_t planc_plan_split(int N, const int64_t* dims, int* split);
  * The partial MTTKRPs run on the tcgen05 tensor cores when the shape allows
  * (BF16 or FP32 X, R <= 64, TMA-compatible strides, X 16-byte aligned; the
  * resident-operand kernel when its factor image fits in shared memory, the
- * streamed-operand kernel otherwise) and on the CUDA-core kernels
- * otherwise (planc_pm_tensor_cores reports which).
+ * streamed-operand kernel otherwise; BF16 X with R <= 32 and FP16 X with
+ * R <= 32 as one GEMM against the split Khatri-Rao image, which needs the
+ * row stride of X_(1:S) a multiple of 16 bytes) and on the CUDA-core
+ * kernels otherwise (planc_pm_tensor_cores reports which).  PLANC_PM_KRP=0
+ * (read at context creation and at each launch) turns the Khatri-Rao GEMM
+ * form off (BF16 then uses the weighted-row kernels, FP16 the CUDA cores).
  * Environment switches: PLANC_PM_PATH=simt (read here) forces the CUDA-core
  * partial MTTKRPs; PLANC_FUSED_MODES=0 (read here) keeps the per-mode update
  * on the multi-launch path; PLANC_TC_STREAMED_KRP (set; read at each launch)

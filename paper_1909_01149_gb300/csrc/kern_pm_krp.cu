@@ -1,5 +1,6 @@
-// The partial MTTKRPs of both root branches for BF16 X as one tcgen05 GEMM
-// each (Alg. 3: T^{1:S} = X_(1:S) K^{S+1:N} and T^{S+1:N} = X_(1:S)^T K^{1:S}):
+// The partial MTTKRPs of both root branches for BF16 (and FP16) X as one
+// tcgen05 GEMM each (Alg. 3: T^{1:S} = X_(1:S) K^{S+1:N} and T^{S+1:N} =
+// X_(1:S)^T K^{1:S}):
 //
 //   right: D[c, r] = sum_k X[k + L c] K[k, r]   (k over the L leading entries)
 //   left:  D[l, r] = sum_k X[l + L k] K[k, r]   (k over the C trailing entries)
@@ -23,8 +24,18 @@
 // partial 128 x R' block per tile it touches, and krp_reduce_kernel sums a
 // tile's partials in CTA order (fixed order: results do not depend on
 // scheduling).
+//
+// FP16 X: the MMA takes both operands in one type, so the image is split into
+// three FP16 terms instead.  FP16's exponent range is narrow (normal values
+// from 6e-5): each column r of K is first scaled by 2^s_r, s_r chosen from
+// the column's largest magnitude so that it lands in [2^14, 2^15) (a first
+// kernel finds the maxima), and the fixed-order reduction multiplies the
+// column's sums by 2^-s_r (exact).  Terms far below a column's maximum lose
+// their last split terms to FP16 subnormals; their error relative to the
+// column's largest product stays near 2^-33.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -68,34 +79,76 @@ struct KrpParams {
   int* err;
 };
 
-// ---- B image: K^T split into hi | mid | lo, 3 RB rows of Kp BF16 ----------------------
+// ---- B image: K^T split into hi | mid | lo, 3 RB rows of Kp 16-bit values --------------
 // K[k, r] = H_0[i_0, r] * H_1[i_1, r] * ..., k = i_0 + dim_0 (i_1 + dim_1 (...)),
 // zero for k >= L or r >= R
+__device__ __forceinline__ float krp_entry(const KrpDev& kd, int R, int64_t k, int r) {
+  int64_t rest = k;
+  const int64_t i0 = rest % kd.dim[0];
+  rest /= kd.dim[0];
+  float v = kd.H[0][i0 * R + r];
+  for (int m = 1; m < kd.nm; ++m) {
+    const int64_t im = rest % kd.dim[m];
+    rest /= kd.dim[m];
+    v *= kd.H[m][im * R + r];
+  }
+  return v;
+}
+
+// FP16 image: the power-of-two exponent s_r of column r from its largest
+// magnitude (bits of a non-negative float: integer order is float order)
+__device__ __forceinline__ int f16_col_shift(unsigned maxbits) {
+  const float mx = __uint_as_float(maxbits);
+  if (!(mx > 0.f) || !(mx < 3.0e38f)) return 0;
+  int e;
+  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  return 15 - e;   // mx 2^s in [2^14, 2^15)
+}
+
+// cmax[r] = bits of max_k |K[k, r]| (cmax zeroed beforehand); a warp's 32
+// consecutive indices share one r (Kp is a multiple of 64)
+__global__ void krp_colmax_kernel(KrpDev kd, int R, int RB, int64_t L, int64_t Kp,
+                                  unsigned* __restrict__ cmax) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = idx < Kp * RB;
+  const int64_t k = in ? idx % Kp : 0;
+  const int r = in ? (int)(idx / Kp) : 0;
+  const float v = (in && k < L && r < R) ? fabsf(krp_entry(kd, R, k, r)) : 0.f;
+  unsigned b = __float_as_uint(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+  if ((threadIdx.x & 31) == 0 && in && b != 0u) atomicMax(cmax + r, b);
+}
+
+template <bool F16>
 __global__ void krp_image_kernel(KrpDev kd, int R, int RB, int64_t L, int64_t Kp,
-                                 __nv_bfloat16* __restrict__ Bt) {
+                                 void* __restrict__ Bt, const unsigned* __restrict__ cmax) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Kp * RB) return;
   const int64_t k = idx % Kp;
   const int r = (int)(idx / Kp);
   float v = 0.f;
-  if (k < L && r < R) {
-    int64_t rest = k;
-    const int64_t i0 = rest % kd.dim[0];
-    rest /= kd.dim[0];
-    v = kd.H[0][i0 * R + r];
-    for (int m = 1; m < kd.nm; ++m) {
-      const int64_t im = rest % kd.dim[m];
-      rest /= kd.dim[m];
-      v *= kd.H[m][im * R + r];
-    }
+  if (k < L && r < R) v = krp_entry(kd, R, k, r);
+  if (F16) {
+    v = ldexpf(v, f16_col_shift(cmax[r]));
+    const __half hi = __float2half_rn(v);
+    const float r1 = v - __half2float(hi);
+    const __half mid = __float2half_rn(r1);
+    const __half lo = __float2half_rn(r1 - __half2float(mid));
+    __half* B = static_cast<__half*>(Bt);
+    B[(int64_t)r * Kp + k] = hi;
+    B[(int64_t)(RB + r) * Kp + k] = mid;
+    B[(int64_t)(2 * RB + r) * Kp + k] = lo;
+  } else {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    __nv_bfloat16* B = static_cast<__nv_bfloat16*>(Bt);
+    B[(int64_t)r * Kp + k] = hi;
+    B[(int64_t)(RB + r) * Kp + k] = mid;
+    B[(int64_t)(2 * RB + r) * Kp + k] = lo;
   }
-  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  const float r1 = v - __bfloat162float(hi);
-  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-  const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-  Bt[(int64_t)r * Kp + k] = hi;
-  Bt[(int64_t)(RB + r) * Kp + k] = mid;
-  Bt[(int64_t)(2 * RB + r) * Kp + k] = lo;
 }
 
 // first unit of CTA g (of G) over U units
@@ -104,9 +157,10 @@ __host__ __device__ __forceinline__ int64_t unit0(int64_t U, int g, int G) {
 }
 
 // ---- sum of a tile's partials over the CTAs that touched it, in CTA order ------------
+// cmax (FP16 image): the column scales to undo, else NULL
 __global__ void krp_reduce_kernel(const float* __restrict__ part, int64_t C, int R, int RB,
                                   int64_t U, int ks, int G, int tmax, float* __restrict__ out,
-                                  int rowmajor) {
+                                  int rowmajor, const unsigned* __restrict__ cmax) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= C * R) return;
   const int64_t c = idx / R;
@@ -126,12 +180,14 @@ __global__ void krp_reduce_kernel(const float* __restrict__ part, int64_t C, int
     const int64_t slot = t - u0 / ks;
     s += part[(((int64_t)g * tmax + slot) * KR_BM + m) * RB + r];
   }
+  if (cmax) s = ldexpf(s, -f16_col_shift(cmax[r]));
   if (rowmajor) out[c * R + r] = s;
   else out[c + C * r] = s;
 }
 
 // ---- the GEMM: persistent, stream-K over (tile, k-step) units ------------------------
-template <int RB, bool LEFT>
+// F16: X and the image in FP16 (else BF16)
+template <int RB, bool LEFT, bool F16 = false>
 __global__ void __launch_bounds__(KR_THREADS, 1)
 pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
               const __grid_constant__ KrpParams p) {
@@ -238,7 +294,7 @@ pm_krp_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CU
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(1u, LEFT, false, KR_BM, N);
+      const uint32_t idesc = instr_desc(F16 ? 0u : 1u, LEFT, false, KR_BM, N);  // A, B: f16 / bf16
       int s = 0, buf = 0;
       uint32_t ph = 0, eph = 0;
       bool ok = true, issued = false;
@@ -707,7 +763,7 @@ pm_krp32_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ 
 namespace {
 
 struct KrpPlan {
-  bool ok = false, f32 = false;
+  bool ok = false, f32 = false, f16 = false;
   int RB = 16;
   int64_t Kp = 0, U = 0;
   int ks = 0, grid = 0, tmax = 0, stages = 0, aslots = 4;
@@ -715,10 +771,13 @@ struct KrpPlan {
 };
 
 // Mdim: output rows (C right, L left); Kdim: the reduction (L right, C left);
-// f32: FP32 X (converter kernel; 32-element stages)
-KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count, bool f32 = false) {
+// f32: FP32 X (converter kernel; 32-element stages); f16: FP16 X (the image
+// in FP16, with its column maxima after it)
+KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count, bool f32 = false,
+                 bool f16 = false) {
   KrpPlan pl;
   pl.f32 = f32;
+  pl.f16 = f16 && !f32;
   if (R < 1 || R > (f32 ? 64 : 32) || Mdim < 1 || Kdim < 1) return pl;
   pl.RB = R <= 16 ? 16 : R <= 32 ? 32 : 64;
   const int bk = f32 ? K3_BK : KR_BK;
@@ -745,6 +804,7 @@ KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count, bool f32 = fal
   } else {
     if (pl.RB > 32) return pl;
     pl.img_bytes = ((size_t)3 * pl.RB * pl.Kp * 2 + 255) / 256 * 256;
+    if (pl.f16) pl.cs_bytes = 256;  // the column maxima (RB <= 32 words)
     const size_t st_bytes = (size_t)KR_BM * KR_BK * 2 + (size_t)3 * pl.RB * KR_BK * 2;
     const size_t fixed = 1024 + 8 * (2 * KR_MAX_STAGES + 2 * 4 + 1) + 16;
     pl.stages = (int)std::min<size_t>(KR_MAX_STAGES, (227 * 1024 - fixed) / st_bytes);
@@ -755,8 +815,8 @@ KrpPlan krp_plan(int64_t Mdim, int64_t Kdim, int R, int sm_count, bool f32 = fal
 }
 
 KrpPlan krp_plan_for(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R, int sm_count) {
-  const bool f32 = xdt == PLANC_F32;
-  return left ? krp_plan(L, C, R, sm_count, f32) : krp_plan(C, L, R, sm_count, f32);
+  const bool f32 = xdt == PLANC_F32, f16 = xdt == PLANC_F16;
+  return left ? krp_plan(L, C, R, sm_count, f32, f16) : krp_plan(C, L, R, sm_count, f32, f16);
 }
 
 // PLANC_PM_KRP=0 keeps both BF16 branches on the weighted-row kernels (read
@@ -772,8 +832,8 @@ bool pm_krp_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                      const KrpHost& kh) {
   if (!krp_enabled() || kh.nm < 1 || kh.nm > PLANC_MAX_N) return false;
   if (L >= (1LL << 31) || C >= (1LL << 31)) return false;
-  if (xdt == PLANC_BF16) {
-    // TMA: the row stride of X (L BF16 elements) a multiple of 16 bytes
+  if (xdt == PLANC_BF16 || xdt == PLANC_F16) {
+    // TMA: the row stride of X (L 16-bit elements) a multiple of 16 bytes
     if (R < 1 || R > 32 || L % 8 != 0) return false;
   } else if (xdt == PLANC_F32) {
     // the right branch only (the left one's converters already set its pace),
@@ -797,10 +857,10 @@ size_t pm_krp_workspace_bytes(planc_dtype_t xdt, bool left, int64_t L, int64_t C
 cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C, bool left,
                           const KrpHost& kh, int R, void* out, bool out_rowmajor, void* work,
                           size_t work_bytes, int* err_flag, int sm_count, cudaStream_t st) {
-  const bool f32 = xdt == PLANC_F32;
+  const bool f32 = xdt == PLANC_F32, f16 = xdt == PLANC_F16;
   if (f32 && left) return cudaErrorInvalidValue;
   const int64_t Mdim = left ? L : C, Kdim = left ? C : L;
-  const KrpPlan pl = krp_plan(Mdim, Kdim, R, sm_count, f32);
+  const KrpPlan pl = krp_plan(Mdim, Kdim, R, sm_count, f32, f16);
   if (!pl.ok || work_bytes < pl.img_bytes + pl.cs_bytes + pl.part_bytes) return cudaErrorInvalidValue;
   if (((uintptr_t)X & 15) != 0 || ((uintptr_t)work & 255) != 0) return cudaErrorInvalidValue;
   char* wb = static_cast<char*>(work);
@@ -815,12 +875,22 @@ cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C
   }
   {
     const int64_t n = pl.Kp * pl.RB;
-    if (f32)
+    unsigned* cmax = reinterpret_cast<unsigned*>(cs);  // FP16: the column maxima
+    if (f32) {
       krp32_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
           kd, R, pl.RB, Kdim, pl.Kp, reinterpret_cast<float*>(wb), cs);
-    else
-      krp_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-          kd, R, pl.RB, Kdim, pl.Kp, reinterpret_cast<__nv_bfloat16*>(wb));
+    } else if (f16) {
+      const cudaError_t me = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * pl.RB, st);
+      if (me != cudaSuccess) return me;
+      krp_colmax_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim, pl.Kp,
+                                                                      cmax);
+      krp_image_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim,
+                                                                          pl.Kp, wb, cmax);
+      note_launches(1);
+    } else {
+      krp_image_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          kd, R, pl.RB, Kdim, pl.Kp, wb, nullptr);
+    }
     note_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -828,7 +898,9 @@ cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C
   // tensor maps: A = X as L x C (L contiguous; right: rows c, boxes of one
   // 128-byte row of k by 128 rows; left: rows l, two 64 x 64 boxes per
   // stage), B = the image, K-major
-  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapDataType dt = f32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t es = f32 ? 4 : 2;
   const cuuint32_t bk = f32 ? K3_BK : KR_BK;
   const int nrows_b = (f32 ? 2 : 3) * pl.RB;
@@ -881,8 +953,10 @@ cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C
     p.tmax = pl.tmax;
     p.part = part;
     p.err = err_flag;
-    auto k = pl.RB == 16 ? (left ? pm_krp_kernel<16, true> : pm_krp_kernel<16, false>)
-                         : (left ? pm_krp_kernel<32, true> : pm_krp_kernel<32, false>);
+    auto k = f16 ? (pl.RB == 16 ? (left ? pm_krp_kernel<16, true, true> : pm_krp_kernel<16, false, true>)
+                                : (left ? pm_krp_kernel<32, true, true> : pm_krp_kernel<32, false, true>))
+                 : (pl.RB == 16 ? (left ? pm_krp_kernel<16, true> : pm_krp_kernel<16, false>)
+                                : (left ? pm_krp_kernel<32, true> : pm_krp_kernel<32, false>));
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k, dim3(pl.grid), dim3(KR_THREADS), pl.smem, st, tA, tB, p);
@@ -893,7 +967,7 @@ cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C
   const int64_t n = Mdim * R;
   krp_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
       part, Mdim, R, pl.RB, pl.U, pl.ks, pl.grid, pl.tmax, static_cast<float*>(out),
-      out_rowmajor ? 1 : 0);
+      out_rowmajor ? 1 : 0, f16 ? reinterpret_cast<const unsigned*>(cs) : nullptr);
   note_launches(1);
   return cudaGetLastError();
 }

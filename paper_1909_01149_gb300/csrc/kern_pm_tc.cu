@@ -1701,6 +1701,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
 
 bool pm_tc_eligible(planc_dtype_t xdt, bool left, int64_t L, int64_t C, int R,
                     const KrpHost& kh) {
+  // FP16 X: only the Khatri-Rao GEMM form (an FP16 image; the other
+  // tensor-core kernels take BF16 or FP32)
+  if (xdt == PLANC_F16) return pm_krp_eligible(xdt, left, L, C, R, kh);
   if (xdt != PLANC_BF16 && xdt != PLANC_F32) return false;
   if (R < 1 || R > 64) return false;
   if (kh.nm < 1 || kh.nm > TC_MAXM) return false;
@@ -1861,6 +1864,7 @@ cudaError_t launch_pm_tc(planc_dtype_t xdt, const void* X, int64_t L, int64_t C,
       work_bytes >= pm_krp_workspace_bytes(xdt, left, L, C, R, sm_count))
     return launch_pm_krp(xdt, X, L, C, left, kh, R, out, out_rowmajor, work, work_bytes,
                          err_flag, sm_count, st);
+  if (xdt == PLANC_F16) return cudaErrorNotSupported;
   {
     const TcrPlan pl = tcr_plan(xdt, left, L, C, R, kh, sm_count);
     if (pl.ok && getenv("PLANC_TC_STREAMED_KRP") == nullptr)
