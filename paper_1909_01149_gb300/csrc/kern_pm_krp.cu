@@ -29,7 +29,8 @@
 // three FP16 terms instead.  FP16's exponent range is narrow (normal values
 // from 6e-5): each column r of K is first scaled by 2^s_r, s_r chosen from
 // the column's largest magnitude so that it lands in [2^14, 2^15) (a first
-// kernel finds the maxima), and the fixed-order reduction multiplies the
+// kernel finds the maxima from the factors' column maxima), and the
+// fixed-order reduction multiplies the
 // column's sums by 2^-s_r (exact).  Terms far below a column's maximum lose
 // their last split terms to FP16 subnormals; their error relative to the
 // column's largest product stays near 2^-33.
@@ -105,19 +106,28 @@ __device__ __forceinline__ int f16_col_shift(unsigned maxbits) {
   return 15 - e;   // mx 2^s in [2^14, 2^15)
 }
 
-// cmax[r] = bits of max_k |K[k, r]| (cmax zeroed beforehand); a warp's 32
-// consecutive indices share one r (Kp is a multiple of 64)
-__global__ void krp_colmax_kernel(KrpDev kd, int R, int RB, int64_t L, int64_t Kp,
-                                  unsigned* __restrict__ cmax) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = idx < Kp * RB;
-  const int64_t k = in ? idx % Kp : 0;
-  const int r = in ? (int)(idx / Kp) : 0;
-  const float v = (in && k < L && r < R) ? fabsf(krp_entry(kd, R, k, r)) : 0.f;
-  unsigned b = __float_as_uint(v);
+// cmax[r] = bits of max_k |K[k, r]| = prod_m max_i |H_m[i, r]| (the maximum
+// of a product over independent indices; multiplied in the order
+// krp_entry uses, so it equals the largest entry the image kernel forms):
+// one block per column r < RB (zero past R)
+__global__ void __launch_bounds__(256)
+krp_colmax_kernel(KrpDev kd, int R, unsigned* __restrict__ cmax) {
+  __shared__ float wmax[8];
+  const int r = blockIdx.x, t = threadIdx.x;
+  float prod = r < R ? 1.f : 0.f;
+  for (int m = 0; m < kd.nm && r < R; ++m) {
+    float mx = 0.f;
+    for (int64_t i = t; i < kd.dim[m]; i += blockDim.x) mx = fmaxf(mx, fabsf(kd.H[m][i * R + r]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
-  if ((threadIdx.x & 31) == 0 && in && b != 0u) atomicMax(cmax + r, b);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((t & 31) == 0) wmax[t >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, wmax[w]);
+    __syncthreads();
+    prod = m == 0 ? mx : prod * mx;
+  }
+  if (t == 0) cmax[r] = __float_as_uint(prod);
 }
 
 template <bool F16>
@@ -880,10 +890,7 @@ cudaError_t launch_pm_krp(planc_dtype_t xdt, const void* X, int64_t L, int64_t C
       krp32_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
           kd, R, pl.RB, Kdim, pl.Kp, reinterpret_cast<float*>(wb), cs);
     } else if (f16) {
-      const cudaError_t me = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * pl.RB, st);
-      if (me != cudaSuccess) return me;
-      krp_colmax_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim, pl.Kp,
-                                                                      cmax);
+      krp_colmax_kernel<<<(unsigned)pl.RB, 256, 0, st>>>(kd, R, cmax);
       krp_image_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kd, R, pl.RB, Kdim,
                                                                           pl.Kp, wb, cmax);
       note_launches(1);
