@@ -493,14 +493,26 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
   float* wf = df + 64;
 
   // S x for the full vector in zs: rows j0, j1
+  // (four partial sums per row: a single chain of R dependent FP64 FMAs is
+  // the latency of every refinement step on this GPU's narrow FP64 pipe)
   auto sx = [&](double& s0, double& s1) {
-    s0 = 0.0;
-    s1 = 0.0;
-    for (int k = 0; k < R; ++k) {
-      const double xk = zs[k];
-      if (v0) s0 = fma(Ss[j0 * LD + k], xk, s0);
-      if (v1) s1 = fma(Ss[j1 * LD + k], xk, s1);
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = 0;
+    for (; k + 4 <= R; k += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double xk = zs[k + u];
+        if (v0) a[u] = fma(Ss[j0 * LD + k + u], xk, a[u]);
+        if (v1) b[u] = fma(Ss[j1 * LD + k + u], xk, b[u]);
+      }
     }
+    for (; k < R; ++k) {
+      const double xk = zs[k];
+      if (v0) a[0] = fma(Ss[j0 * LD + k], xk, a[0]);
+      if (v1) b[0] = fma(Ss[j1 * LD + k], xk, b[0]);
+    }
+    s0 = (a[0] + a[1]) + (a[2] + a[3]);
+    s1 = (b[0] + b[1]) + (b[2] + b[3]);
   };
   // wf := (L L^T)^{-1} wf with the FP32 factor (positions 0..f-1)
   auto solve32 = [&](int f) {
@@ -593,13 +605,15 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
       const float dw = __shfl_sync(0xffffffffu, w, p0 & 31);
       const double d = in0 ? (double)dw : 0.0;
       x0 += d;
-      double dm = fabs(d), xm = fabs(x0);
+      // the stop test's maxima in FP32 (a ratio of 1e-9 is well inside its
+      // range; FP64 shuffles cost twice as many and the FP64 pipe is narrow)
+      float dm = fabsf((float)d), xm = fabsf((float)x0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
       }
-      if (st > 0 && dm <= 1e-9 * xm) return true;
+      if (st > 0 && dm <= 1e-9f * xm) return true;
       if (st == 6) return false;
       // FP64 residual m_F - S_FF x_F
       if (v0) zs[j0] = x0;
