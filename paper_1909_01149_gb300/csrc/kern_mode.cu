@@ -887,6 +887,7 @@ cudaError_t run_mc(int rows, int R, int N, int n, double* G, float* Gf, const vo
 // assigned instance at the current factors (timed by the schedule tuner;
 // they leave the factors as they are).  sqpart: MC_CS doubles per instance.
 constexpr int PB_MINB = 2;  // CTAs per SM the persistent kernel is compiled for (the update needs ~200 registers)
+static_assert(kBatchClusterCtas == MC_CS, "the host sizes the alpha partials for this cluster size");
 
 __device__ __forceinline__ void cluster_sync_all() {
   cluster_arrive();
