@@ -605,16 +605,18 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
       const float dw = __shfl_sync(0xffffffffu, w, p0 & 31);
       const double d = in0 ? (double)dw : 0.0;
       x0 += d;
-      // the stop test's maxima in FP32 (a ratio of 1e-9 is well inside its
-      // range; FP64 shuffles cost twice as many and the FP64 pipe is narrow)
-      float dm = fabsf((float)d), xm = fabsf((float)x0);
+      if (st > 0) {  // (the first solve is never the last)
+        // the stop test's maxima in FP32 (a ratio of 1e-9 is well inside its
+        // range; FP64 shuffles cost twice as many and the FP64 pipe is narrow)
+        float dm = fabsf((float)d), xm = fabsf((float)x0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        for (int o = 16; o > 0; o >>= 1) {
+          dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+          xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        }
+        if (dm <= 1e-9f * xm) return true;
+        if (st == 6) return false;
       }
-      if (st > 0 && dm <= 1e-9f * xm) return true;
-      if (st == 6) return false;
       // FP64 residual m_F - S_FF x_F
       if (v0) zs[j0] = x0;
       __syncwarp();

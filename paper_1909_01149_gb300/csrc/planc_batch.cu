@@ -62,7 +62,6 @@ std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;    // per-phase launches
 std::map<TuneKey, TuneChoice> g_tune_p;  // persistent launch (rank blocking only)
 thread_local TuneChoice t_last_choice;
-thread_local bool t_last_persistent = false;
 constexpr int kSchedules = 3;
 
 struct Alloc {
@@ -402,7 +401,6 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     }
   }
   t_last_choice = ch;
-  t_last_persistent = persistent;
   const int tl_idx = ch.tl;
   const int2* d_left = reinterpret_cast<const int2*>(base + off_left[tl_idx]);
   const int64_t* d_lcum = reinterpret_cast<const int64_t*>(base + off_lcum[tl_idx]);
