@@ -575,33 +575,52 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
       }
     }
     if (!good) return false;
-    // L by rows into shared memory for the transposed solve
+    // Y = L^{-1} by rows (lane p holds row p): forward substitution on the
+    // identity, every column at once.  Each solve below is then two short
+    // matrix-vector products instead of two chains of f dependent
+    // substitution steps (every refinement step solves once more).
+    float li[RM];
+#pragma unroll
+    for (int j = 0; j < RM; ++j) li[j] = (j == lane) ? 1.f : 0.f;
+#pragma unroll
+    for (int c = 0; c < RM; ++c) {
+      if (c < f) {
+        const float sc = lane == c ? inv[c] : 1.f;  // row c is final once scaled
+#pragma unroll
+        for (int j = 0; j <= c; ++j) li[j] *= sc;
+#pragma unroll
+        for (int j = 0; j <= c; ++j) {
+          const float ycj = __shfl_sync(0xffffffffu, li[j], c);
+          if (lane > c) li[j] = fmaf(-a[c], ycj, li[j]);  // a[c] = L[lane][c]
+        }
+      }
+    }
+    // rows of Y into shared memory (the transposed product reads columns)
 #pragma unroll
     for (int q = 0; q < RM; ++q)
-      if (live && q <= lane && q < f) Af[lane * LD + q] = a[q];
+      if (live && q <= lane && q < f) Af[lane * LD + q] = li[q];
     __syncwarp();
     x0 = 0.0;
     double r0 = in0 ? m0 : 0.0;  // residual on F (x = 0)
     for (int st = 0; st <= 6; ++st) {
-      // right-hand side to the position lanes, then L z = r, L^T d = z
+      // right-hand side to the position lanes, then z = Y r, d = Y^T z
       float w = __shfl_sync(0xffffffffu, (float)r0, myi);
       if (!live) w = 0.f;
+      float z4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int c = 0; c < RM; ++c) {
-        if (c < f) {
-          const float zc = __shfl_sync(0xffffffffu, w, c) * inv[c];
-          if (lane > c) w = fmaf(-a[c], zc, w);
-          else if (lane == c) w = zc;
-        }
+      for (int j = 0; j < RM; ++j) {
+        const float wj = __shfl_sync(0xffffffffu, w, j);
+        z4[j & 3] = fmaf(li[j], wj, z4[j & 3]);  // li[j] = 0 past the diagonal
       }
+      const float z = live ? (z4[0] + z4[1]) + (z4[2] + z4[3]) : 0.f;
+      float d4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int c = RM - 1; c >= 0; --c) {
-        if (c < f) {
-          const float xc = __shfl_sync(0xffffffffu, w, c) * inv[c];
-          if (lane < c) w = fmaf(-Af[c * LD + lane], xc, w);
-          else if (lane == c) w = xc;
-        }
+      for (int j = 0; j < RM; ++j) {
+        const float zj = __shfl_sync(0xffffffffu, z, j);
+        const float yji = (live && j >= lane && j < f) ? Af[j * LD + lane] : 0.f;
+        d4[j & 3] = fmaf(yji, zj, d4[j & 3]);
       }
+      w = (d4[0] + d4[1]) + (d4[2] + d4[3]);
       const float dw = __shfl_sync(0xffffffffu, w, p0 & 31);
       const double d = in0 ? (double)dw : 0.0;
       x0 += d;
