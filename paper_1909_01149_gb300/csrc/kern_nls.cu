@@ -548,79 +548,55 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
     for (int q = 0; q < RM; ++q) a[q] = (live && q < f) ? (float)Ss[myi * LD + tbl[q]] : 0.f;
     const float d0 = (float)Ss[myi * LD + myi];
     __syncwarp();  // tbl read by all lanes before xs is reused
-    // Cholesky: after step c, lane i >= c holds L[i][c] in a[c]
-    float inv[RM];
+    // Gauss-Jordan inversion of S_FF in registers (symmetric positive
+    // definite: no pivoting), lane p holding row p: step c scales row c by
+    // the reciprocal of its pivot (the Schur complement's diagonal, the
+    // square of the Cholesky pivot) and removes column c from every other
+    // row.  Afterwards a[] holds row p of S_FF^{-1}, so a solve is one
+    // matrix-vector product.  One chain of f steps (a Cholesky factor and
+    // two triangular solves per refinement step were three); a pivot below
+    // 1e-5 of its diagonal entry hands the system to the FP64 path as before.
     int good = 1;
 #pragma unroll
     for (int c = 0; c < RM; ++c) {
-      inv[c] = 0.f;
       if (c < f) {
-        float piv = __shfl_sync(0xffffffffu, a[c], c);
-        const float dc = __shfl_sync(0xffffffffu, d0, c);
-        if (!(piv > 1e-5f * dc)) {
-          good = 0;
-          piv = 1.f;
-        }
-        const float ic = rsqrtf(piv);
-        inv[c] = ic;
-        const float lic = a[c] * ic;
-        if (lane >= c) a[c] = lic;
-#pragma unroll
-        for (int j = c + 1; j < RM; ++j) {
-          if (j < f) {
-            const float ljc = __shfl_sync(0xffffffffu, lic, j);
-            if (lane >= j) a[j] = fmaf(-lic, ljc, a[j]);
+        const float fct = a[c];  // A[lane][c]; at lane c the pivot
+        float ip = 1.f;
+        if (lane == c) {
+          float piv = fct;
+          if (!(piv > 1e-5f * d0)) {
+            good = 0;
+            piv = 1.f;
           }
+          ip = __frcp_rn(piv);
+          a[c] = 1.f;
+        }
+#pragma unroll
+        for (int q = 0; q < RM; ++q) a[q] *= ip;  // row c scaled (ip = 1 elsewhere)
+        float rq[RM];
+#pragma unroll
+        for (int q = 0; q < RM; ++q) rq[q] = q < f ? __shfl_sync(0xffffffffu, a[q], c) : 0.f;
+        if (lane != c) {
+          a[c] = 0.f;
+#pragma unroll
+          for (int q = 0; q < RM; ++q) a[q] = fmaf(-fct, rq[q], a[q]);
         }
       }
     }
-    if (!good) return false;
-    // Y = L^{-1} by rows (lane p holds row p): forward substitution on the
-    // identity, every column at once.  Each solve below is then two short
-    // matrix-vector products instead of two chains of f dependent
-    // substitution steps (every refinement step solves once more).
-    float li[RM];
-#pragma unroll
-    for (int j = 0; j < RM; ++j) li[j] = (j == lane) ? 1.f : 0.f;
-#pragma unroll
-    for (int c = 0; c < RM; ++c) {
-      if (c < f) {
-        const float sc = lane == c ? inv[c] : 1.f;  // row c is final once scaled
-#pragma unroll
-        for (int j = 0; j <= c; ++j) li[j] *= sc;
-#pragma unroll
-        for (int j = 0; j <= c; ++j) {
-          const float ycj = __shfl_sync(0xffffffffu, li[j], c);
-          if (lane > c) li[j] = fmaf(-a[c], ycj, li[j]);  // a[c] = L[lane][c]
-        }
-      }
-    }
-    // rows of Y into shared memory (the transposed product reads columns)
-#pragma unroll
-    for (int q = 0; q < RM; ++q)
-      if (live && q <= lane && q < f) Af[lane * LD + q] = li[q];
-    __syncwarp();
+    if (!__all_sync(0xffffffffu, good)) return false;
     x0 = 0.0;
     double r0 = in0 ? m0 : 0.0;  // residual on F (x = 0)
     for (int st = 0; st <= 6; ++st) {
-      // right-hand side to the position lanes, then z = Y r, d = Y^T z
+      // right-hand side to the position lanes, then d = S_FF^{-1} r
       float w = __shfl_sync(0xffffffffu, (float)r0, myi);
       if (!live) w = 0.f;
-      float z4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < RM; ++j) {
-        const float wj = __shfl_sync(0xffffffffu, w, j);
-        z4[j & 3] = fmaf(li[j], wj, z4[j & 3]);  // li[j] = 0 past the diagonal
-      }
-      const float z = live ? (z4[0] + z4[1]) + (z4[2] + z4[3]) : 0.f;
       float d4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < RM; ++j) {
-        const float zj = __shfl_sync(0xffffffffu, z, j);
-        const float yji = (live && j >= lane && j < f) ? Af[j * LD + lane] : 0.f;
-        d4[j & 3] = fmaf(yji, zj, d4[j & 3]);
+        const float wj = __shfl_sync(0xffffffffu, w, j);
+        d4[j & 3] = fmaf(a[j], wj, d4[j & 3]);  // a[j] = 0 for j >= f
       }
-      w = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+      w = live ? (d4[0] + d4[1]) + (d4[2] + d4[3]) : 0.f;
       const float dw = __shfl_sync(0xffffffffu, w, p0 & 31);
       const double d = in0 ? (double)dw : 0.0;
       x0 += d;
