@@ -407,10 +407,10 @@ __device__ __forceinline__ uint64_t ballot64(bool lo, bool hi) {
   return a | (b << 32);
 }
 
-// RMAX > 0 (FP32 storage, R <= RMAX <= 32): the passive systems are factored
-// and solved in registers (lane p holds row p of S_FF and of its Cholesky
-// factor; pivots and factor entries travel by warp shuffles), without a
-// shared-memory round trip per elimination step.
+// RMAX > 0 (FP32 storage, R <= RMAX <= 32): the passive systems are inverted
+// and solved in registers (lane p holds row p of S_FF and then of its
+// inverse; pivot rows travel by warp shuffles), without a shared-memory
+// round trip per elimination step.
 template <typename TA, int RMAX>
 __global__ void __launch_bounds__(32 * BPP_WARPS, 1)
 nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __restrict__ M,
@@ -480,8 +480,9 @@ nls_bpp_kernel(int64_t rows, int R, const double* __restrict__ S, const TA* __re
   double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
   int bad = 0;
 
-  // The passive system S_FF x_F = m_F is factored in FP32 (this GPU's FP64
-  // pipe is narrow, and the factorisation is a chain of dependent steps) and
+  // The passive system S_FF x_F = m_F is factored (register path: inverted)
+  // in FP32 (this GPU's FP64 pipe is narrow, and the elimination is a chain
+  // of dependent steps) and
   // x_F refined with FP64 residuals m_F - S_FF x_F until the correction is
   // below 1e-11 of x (mixed-precision iterative refinement: the result is the
   // FP64 solution to that accuracy; 1e-9 on the register path, whose results
