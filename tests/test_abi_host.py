@@ -99,6 +99,7 @@ def test_option_defaults_cross_the_abi():
             n.nes_max_inner, n.nes_tol) == (1e-16, 5, 1e-2, 0, 1, 20, 1e-3)
     s = planc.lib.planc_solve_opts_default()
     assert (s.alg, s.iters, s.tol, s.use_graph, s.profile, s.nes_accel) == (1, 10, 0.0, 1, 0, 1)
+    assert s.batch_persistent == 1  # the batched solve as one persistent launch by default
     assert s.nls.nes_max_inner == 20 and s.nls.nes_tol == 1e-3
     assert planc.ALGS["nes"] == 6 and planc.ALGS["ucp"] == 5
 
