@@ -368,6 +368,22 @@ planc_status_t planc_batch_solve(planc_batch_instance* inst, int count,
                                  const planc_solve_opts* opts, void* cuda_stream,
                                  planc_report* report);
 
+/* How the persistent launch of planc_batch_solve deals `count` instances to
+ * `nclusters` thread-block clusters (host-only; the device pointers in inst
+ * are not read).  Each instance's estimated cost per outer iteration is its
+ * partial-MTTKRP FMAs (elements times both ranks padded to the classes 8, 16
+ * or 32) plus a fixed share for the latency of its phases; instances are
+ * taken longest-first (ties in index order), each onto the least-loaded
+ * cluster (lowest index on ties).  Out: clist (count ints) lists cluster q's
+ * instances at clist[coff[q]] .. clist[coff[q + 1] - 1], in the order it
+ * solves them; coff (nclusters + 1 ints); load (nclusters doubles, or NULL)
+ * the clusters' summed costs.  planc_batch_solve uses the clusters that fit
+ * on the GPU at once, at most count.  Errors: PLANC_E_INVALID (NULL
+ * argument, count < 1, nclusters outside 1..count), PLANC_E_SHAPE (dims or
+ * R below 1). */
+planc_status_t planc_batch_plan(const planc_batch_instance* inst, int count, int nclusters,
+                                int* clist, int* coff, double* load);
+
 /* The schedule the most recent planc_batch_solve on the calling thread used
  * for its two partial MTTKRPs, as chosen by timing every candidate on the
  * first call for a batch signature: out[0] rows per left-branch work item

@@ -73,6 +73,43 @@ struct Alloc {
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// The persistent launch's deal of the instances to its clusters.  An
+// instance's estimated cost per outer iteration is its partial-MTTKRP FMAs
+// (elements x the two padded ranks, rank classes 8 / 16 / 32) plus a fixed
+// share for the latency of its phases (about the FMAs of 8e6 at the rate of
+// one cluster); instances are taken longest-first (ties in index order), each
+// onto the least-loaded cluster (the lowest index on ties).  clist: count
+// entries, cluster q's instances clist[coff[q]] .. clist[coff[q + 1] - 1];
+// coff: nclusters + 1 entries; load (optional): the clusters' summed costs.
+void batch_deal(const planc_batch_instance* inst, int count, int nclusters, int* clist, int* coff,
+                double* load_out) {
+  std::vector<double> cost(count);
+  for (int b = 0; b < count; ++b) {
+    const int R = inst[b].R;
+    const double rc = R <= 8 ? 8.0 : R <= 16 ? 16.0 : 32.0;
+    cost[b] = (double)(inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2]) * 2.0 * rc + 8e6;
+  }
+  std::vector<int> order(count);
+  for (int b = 0; b < count; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<std::vector<int>> lists(nclusters);
+  std::vector<double> load(nclusters, 0.0);
+  for (int b : order) {
+    int q = 0;
+    for (int k = 1; k < nclusters; ++k)
+      if (load[k] < load[q]) q = k;
+    lists[q].push_back(b);
+    load[q] += cost[b];
+  }
+  int n = 0;
+  coff[0] = 0;
+  for (int q = 0; q < nclusters; ++q) {
+    for (int b : lists[q]) clist[n++] = b;
+    coff[q + 1] = n;
+    if (load_out) load_out[q] = load[q];
+  }
+}
+
 planc_status_t bfail(planc_status_t st, const char* msg) {
   char buf[256];
   std::snprintf(buf, sizeof buf, "planc_batch_solve: %s", msg);
@@ -269,10 +306,7 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   const int nright = (int)right_items.size(), nrc = (int)rc_items.size();
 
   // ---- the persistent launch: clusters that fit at once, instances dealt
-  // longest-first onto the least-loaded cluster.  An instance's estimated
-  // cost per outer iteration is its partial-MTTKRP FMAs (elements x the two
-  // padded ranks, rank classes 8 / 16 / 32) plus a fixed share for the
-  // latency of its phases (about the FMAs of 8e6 at the rate of one cluster).
+  // longest-first onto the least-loaded cluster (batch_deal)
   const bool persistent = o.batch_persistent != 0;
   const int hmax_p = (int)std::max(maxC, maxI2);
   const int h1max_p = batch_pm_smem(hmax_p, (int)maxI1) <= kStageBudget ? (int)maxI1 : 0;
@@ -280,29 +314,8 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
   if (persistent) {
     nclusters = std::min(count, batch_persistent_max_clusters(o.alg, hmax_p, h1max_p));
     if (nclusters < 1) return bfail(PLANC_E_CUDA, "the persistent launch does not fit on this GPU");
-    std::vector<double> cost(count);
-    for (int b = 0; b < count; ++b) {
-      const int R = inst[b].R;
-      const double rc = R <= 8 ? 8.0 : R <= 16 ? 16.0 : 32.0;
-      cost[b] = (double)(inst[b].dims[0] * inst[b].dims[1] * inst[b].dims[2]) * 2.0 * rc + 8e6;
-    }
-    std::vector<int> order(count);
-    for (int b = 0; b < count; ++b) order[b] = b;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<std::vector<int>> lists(nclusters);
-    std::vector<double> load(nclusters, 0.0);
-    for (int b : order) {  // least-loaded cluster, lowest index on ties
-      int q = 0;
-      for (int k = 1; k < nclusters; ++k)
-        if (load[k] < load[q]) q = k;
-      lists[q].push_back(b);
-      load[q] += cost[b];
-    }
-    std::vector<int> clist, coff(1, 0);
-    for (const auto& l : lists) {
-      clist.insert(clist.end(), l.begin(), l.end());
-      coff.push_back((int)clist.size());
-    }
+    std::vector<int> clist(count), coff(nclusters + 1);
+    batch_deal(inst, count, nclusters, clist.data(), coff.data(), nullptr);
     if (h2d(off_clist, clist.data(), sizeof(int) * count) != cudaSuccess ||
         h2d(off_coff, coff.data(), sizeof(int) * (nclusters + 1)) != cudaSuccess)
       return bfail(PLANC_E_CUDA, "table upload failed");
@@ -477,6 +490,19 @@ extern "C" planc_status_t planc_batch_solve(planc_batch_instance* inst, int coun
     report->launches = launches;
   }
   if (err != 0) return bfail(PLANC_E_TIMEOUT, "a bounded wait in the mode update gave up");
+  return PLANC_OK;
+}
+
+extern "C" planc_status_t planc_batch_plan(const planc_batch_instance* inst, int count,
+                                           int nclusters, int* clist, int* coff, double* load) {
+  if (!inst || !clist || !coff || count < 1) return bfail(PLANC_E_INVALID, "bad arguments");
+  if (nclusters < 1 || nclusters > count) return bfail(PLANC_E_INVALID, "nclusters must be 1..count");
+  for (int b = 0; b < count; ++b) {
+    if (inst[b].R < 1) return bfail(PLANC_E_SHAPE, "R must be >= 1");
+    for (int n = 0; n < 3; ++n)
+      if (inst[b].dims[n] < 1) return bfail(PLANC_E_SHAPE, "dims must be >= 1");
+  }
+  planc::batch_deal(inst, count, nclusters, clist, coff, load);
   return PLANC_OK;
 }
 

@@ -97,6 +97,8 @@ def _load():
         "planc_batch_solve": (I, [C.POINTER(BatchInstance), I, C.POINTER(SolveOpts), P,
                                   C.POINTER(Report)]),
         "planc_batch_schedule": (I, [C.POINTER(I)]),
+        "planc_batch_plan": (I, [C.POINTER(BatchInstance), I, I, C.POINTER(I), C.POINTER(I),
+                                 C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -388,6 +390,29 @@ class CPLoss(torch.autograd.Function):
         if float(g) == 1.0:
             return (None,) + tuple(dH)
         return (None,) + tuple(d * g.to(d.dtype) for d in dH)
+
+
+def batch_plan(shapes, nclusters: int):
+    """planc_batch_plan (host-only): how the persistent batched launch deals
+    instances, given as ((I1, I2, I3), R) pairs, to `nclusters` clusters.
+    Returns (lists, loads): each cluster's instance indices in the order it
+    solves them, and its summed estimated cost."""
+    count = len(shapes)
+    if count < 1:
+        raise ValueError("need at least one instance")
+    arr = (BatchInstance * count)()
+    for b, (dims, R) in enumerate(shapes):
+        for k in range(3):
+            arr[b].dims[k] = int(dims[k])
+        arr[b].R = int(R)
+    clist = (C.c_int * count)()
+    coff = (C.c_int * (nclusters + 1))()
+    load = (C.c_double * nclusters)()
+    st = lib.planc_batch_plan(arr, count, int(nclusters), clist, coff, load)
+    if st != 0:
+        raise PlancError(st, lib.planc_last_error(None).decode())
+    lists = [list(clist[coff[q]:coff[q + 1]]) for q in range(nclusters)]
+    return lists, list(load)
 
 
 def batch_solve(Xs, Hs, alg: str = "hals", iters: int = 25, use_graph: bool = True,

@@ -6,6 +6,7 @@ with the paper (Fig. DT) and with the oracle's statement of the split rule.
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle as o
@@ -194,7 +195,7 @@ def test_every_computational_entry_point_cites_the_paper():
             uncited[name] = comment
     helpers = {"planc_status_str", "planc_last_error", "planc_nls_opts_default",
                "planc_solve_opts_default", "planc_destroy", "planc_get_split",
-               "planc_pm_tensor_cores", "planc_batch_schedule"}
+               "planc_pm_tensor_cores", "planc_batch_schedule", "planc_batch_plan"}
     extensions = {"planc_sqnorm_noalloc"}
     assert set(uncited) <= helpers | extensions, sorted(set(uncited) - helpers - extensions)
     for name in extensions:
@@ -205,3 +206,44 @@ def test_every_computational_entry_point_cites_the_paper():
                  "planc_batch_solve", "planc_plan_split", "planc_describe"):
         assert name in cited, name
     assert cited | set(uncited) == set(_planc().header_functions())
+
+
+def test_batch_plan_deals_every_instance_longest_first():
+    """The persistent batched launch's deal (host-only): every instance in
+    exactly one cluster; each cluster's list in non-increasing estimated cost
+    (the order it solves them); the estimate is elements x 2 x the padded
+    rank class + 8e6; the greedy rule (longest first onto the least-loaded
+    cluster) keeps every cluster within one instance's cost of the least
+    loaded; the same input gives the same deal."""
+    planc = _planc()
+    rng = np.random.default_rng(5)
+    shapes = [(tuple(int(v) for v in rng.integers(32, 161, 3)), int(rng.integers(8, 33)))
+              for _ in range(256)]
+
+    def cost(dims, R):
+        rc = 8 if R <= 8 else 16 if R <= 16 else 32
+        return dims[0] * dims[1] * dims[2] * 2.0 * rc + 8e6
+
+    for ncl in (1, 7, 38, 256):
+        lists, loads = planc.batch_plan(shapes, ncl)
+        assert len(lists) == ncl
+        assert sorted(b for l in lists for b in l) == list(range(len(shapes)))
+        costs = [cost(*s) for s in shapes]
+        for l, ld in zip(lists, loads):
+            assert all(costs[a] >= costs[b] for a, b in zip(l, l[1:]))
+            assert ld == pytest.approx(sum(costs[b] for b in l), rel=1e-12)
+        assert max(loads) - min(loads) <= max(costs) + 1e-6 * max(loads)
+        assert planc.batch_plan(shapes, ncl) == (lists, loads)
+    # the benchmark batch's deal is within 3 % of perfect balance
+    _, loads = planc.batch_plan(shapes, 38)
+    assert max(loads) <= 1.03 * (sum(loads) / len(loads))
+
+
+def test_batch_plan_rejects_bad_arguments():
+    planc = _planc()
+    with pytest.raises(planc.PlancError):
+        planc.batch_plan([((4, 5, 6), 3)], 2)      # more clusters than instances
+    with pytest.raises(planc.PlancError):
+        planc.batch_plan([((4, 0, 6), 3)], 1)      # an empty mode
+    with pytest.raises(planc.PlancError):
+        planc.batch_plan([((4, 5, 6), 0)], 1)      # rank 0
